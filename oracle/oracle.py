@@ -1,0 +1,192 @@
+"""ctypes wrapper of the plain FP64 CPU oracle (``fmm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference legs are the only callers.  The CUDA
+library never imports this module and this module never imports it.
+
+The shared library is compiled on first use with the system C compiler
+(``build()``), into ``oracle/_build/``.
+"""
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fmm_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+NCELL = 512
+NCOMP = 20
+
+
+def build(force=False):
+    """Compile the oracle with gcc (OpenMP over target cells, IEEE FP64)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            lib.oracle_upward.argtypes = [P, I64, P, P, P, P]
+            lib.oracle_m2l.argtypes = [P, I64, P, P, P, P, P, P, P, I64, ctypes.c_int]
+            lib.oracle_sources.argtypes = [P, I64, P, I64, ctypes.c_int, P, P, I64]
+            lib.oracle_sources.restype = I64
+            lib.oracle_coverage.argtypes = [P, I64, P, P, P]
+            lib.oracle_downward.argtypes = [P, I64, P, P, P, P, P, P]
+            lib.oracle_forces.argtypes = [P, I64, P, P, P, P, P, P, P]
+            lib.oracle_pair_m2l.argtypes = [ctypes.c_double, P, P, P, P, ctypes.c_int, P, P]
+            lib.oracle_dtensors.argtypes = [P, P, P, P, P, P]
+            _LIB = lib
+        return _LIB
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _cfg(theta, G, box_lo, box_size):
+    return np.array([theta, G, box_lo[0], box_lo[1], box_lo[2], box_size],
+                    dtype=np.float64)
+
+
+def n_trees(desc):
+    return int(desc[:, 13].max()) + 1
+
+
+class Tree:
+    """A node-descriptor array plus the solve parameters (theta, G, box)."""
+
+    def __init__(self, desc, theta, G=1.0, box_lo=(0.0, 0.0, 0.0), box_size=1.0):
+        self.desc = np.ascontiguousarray(desc, dtype=np.int32)
+        self.n = len(self.desc)
+        self.cfg = _cfg(theta, G, box_lo, box_size)
+        self.n_leaf = int((self.desc[:, 5] < 0).sum())
+        self.n_trees = n_trees(self.desc)
+
+    @classmethod
+    def from_config(cls, c):
+        return cls(c["desc"], c["theta"], c["G"], c["box_lo"], c["box_size"])
+
+
+def upward(tree, rho):
+    """Returns (M [n,20,512], com [n,3,512])."""
+    rho = _f64(rho)
+    M = np.empty((tree.n, NCOMP, NCELL))
+    com = np.empty((tree.n, 3, NCELL))
+    _lib().oracle_upward(_p(tree.desc), tree.n, _p(tree.cfg), _p(rho), _p(M), _p(com))
+    return M, com
+
+
+def m2l(tree, M, com, targets=None, n_threads=0):
+    """Returns (L [n,20,512], dL1 [n,3,512], counts[4]).
+
+    With ``targets`` (int64 node*512+cell), only those cells are computed and
+    the rest of L / dL1 is zero.  counts = (mp<-mp, mp<-mono, mono<-mono,
+    mono<-mp) evaluated pairs.
+    """
+    M = _f64(M)
+    com = _f64(com)
+    L = np.zeros((tree.n, NCOMP, NCELL))
+    dL1 = np.zeros((tree.n, 3, NCELL))
+    counts = np.zeros(4, dtype=np.int64)
+    if targets is None:
+        tp, nt = None, 0
+    else:
+        targets = np.ascontiguousarray(targets, dtype=np.int64)
+        tp, nt = _p(targets), len(targets)
+    _lib().oracle_m2l(_p(tree.desc), tree.n, _p(tree.cfg), _p(M), _p(com), _p(L),
+                      _p(dL1), _p(counts), tp, nt, int(n_threads))
+    return L, dL1, counts
+
+
+def sources(tree, node, cell, max_out=4096):
+    """Offsets (k,3) and flags (k,) of the sources evaluated for one cell."""
+    off = np.zeros((max_out, 3), dtype=np.int32)
+    flg = np.zeros(max_out, dtype=np.int32)
+    k = _lib().oracle_sources(_p(tree.desc), tree.n, _p(tree.cfg), int(node), int(cell),
+                              _p(off), _p(flg), max_out)
+    if k > max_out:
+        return sources(tree, node, cell, max_out=int(k))
+    return off[:k], flg[:k]
+
+
+def coverage(tree, w):
+    w = _f64(w)
+    out = np.zeros_like(w)
+    _lib().oracle_coverage(_p(tree.desc), tree.n, _p(tree.cfg), _p(w), _p(out))
+    return out
+
+
+def downward(tree, com, L, dL1):
+    """Returns (L64 [n,20,512], dL1acc [n,3,512])."""
+    L64 = np.empty((tree.n, NCOMP, NCELL))
+    acc = np.empty((tree.n, 3, NCELL))
+    _lib().oracle_downward(_p(tree.desc), tree.n, _p(tree.cfg), _p(_f64(com)),
+                           _p(_f64(L)), _p(_f64(dL1)), _p(L64), _p(acc))
+    return L64, acc
+
+
+def forces(tree, L64, dL1acc, rho):
+    """Returns (phi [n_leaf,512], g [n_leaf,3,512], totals [n_trees,8])."""
+    phi = np.empty((tree.n_leaf, NCELL))
+    g = np.empty((tree.n_leaf, 3, NCELL))
+    tot = np.empty((tree.n_trees, 8))
+    _lib().oracle_forces(_p(tree.desc), tree.n, _p(tree.cfg), _p(_f64(L64)),
+                         _p(_f64(dL1acc)), _p(_f64(rho)), _p(phi), _p(g), _p(tot))
+    return phi, g, tot
+
+
+def solve(tree, rho, n_threads=0):
+    """The whole solve; returns a dict of every stage's output."""
+    M, com = upward(tree, rho)
+    L, dL1, counts = m2l(tree, M, com, n_threads=n_threads)
+    L64, acc = downward(tree, com, L, dL1)
+    phi, g, tot = forces(tree, L64, acc, rho)
+    return dict(M=M, com=com, L=L, dL1=dL1, counts=counts, L64=L64, dL1acc=acc,
+                phi=phi, g=g, totals=tot)
+
+
+def pair_m2l(MA, XA, MB, XB, a_leaf, G=1.0):
+    """One interaction A <- B: returns (L20, dL1)."""
+    L = np.zeros(NCOMP)
+    d = np.zeros(3)
+    _lib().oracle_pair_m2l(float(G), _p(_f64(MA)), _p(_f64(XA)), _p(_f64(MB)),
+                           _p(_f64(XB)), int(bool(a_leaf)), _p(L), _p(d))
+    return L, d
+
+
+def dtensors(R):
+    """Full derivative tensors of 1/|R|: (D0, D1[3], D2[3,3], D3[3,3,3], D4[3]*4).
+
+    Flat index i + 3j + 9k + 27l is returned in numpy order [l, k, j, i]
+    reshaped so that D2[i, j] etc. read naturally (tensors are symmetric).
+    """
+    R = _f64(R)
+    D = [np.zeros(1), np.zeros(3), np.zeros(9), np.zeros(27), np.zeros(81)]
+    _lib().oracle_dtensors(_p(R), *(_p(x) for x in D))
+    return (D[0][0], D[1], D[2].reshape(3, 3), D[3].reshape(3, 3, 3),
+            D[4].reshape(3, 3, 3, 3))

@@ -1,0 +1,231 @@
+/*
+ * fmm_gb300.h -- C ABI of the GB300 (sm_103a) cell-based FMM gravity solve.
+ *
+ * The method is the FMM of Octo-Tiger (arXiv 1908.03121, Sec. 4.3 "The FMM
+ * hotspot"): an adaptive octree whose nodes are 8x8x8-cell sub-grids; an
+ * upward pass computing each cell's multipole moments and centre of mass from
+ * the leaf densities; a same-level pass in which each cell collects Taylor
+ * coefficients from the cells picked by the opening criterion (four kinds of
+ * interaction by node refinement, Sec. 4.3); and a downward pass that hands
+ * each parent's Taylor expansion to its children and accumulates it.  The
+ * gravity solver also conserves angular momentum (Sec. 2, Sec. 4.2), through a
+ * correction to the force coefficient that is carried down the tree.
+ *
+ * Conventions shared by every call
+ *   - Expansion order 3: 20 packed symmetric-tensor components per cell,
+ *     ordered  0 | x y z | xx xy xz yy yz zz | xxx xxy xxz xyy xyz xzz yyy
+ *     yyz yzz zzz.  Moments are central moments about the cell's centre of
+ *     mass, so the three dipole slots are always zero.
+ *   - Cells inside a node are numbered x + 8 y + 64 z; per-node arrays are
+ *     node-major, [node][component][cell], nodes in descriptor order.
+ *   - Leaf rows (density, potential, field) follow the order in which leaf
+ *     nodes appear in the descriptor array.
+ *   - Cell width at level l (root = 1): h_l = box_size / (8 * 2^(l-1)).
+ *   - Opening rule: cells at integer offset o (in cell widths) are well
+ *     separated iff theta^2 |o|^2 > 1; a same-level pair is a candidate iff
+ *     its parent cells are not well separated (all pairs on the root level);
+ *     a candidate is evaluated iff it is well separated or either cell is a
+ *     leaf cell.  theta must lie in (0.25, 1/sqrt(3)] so that sources stay in
+ *     the 26 neighbour nodes and every leaf pair is evaluated exactly once.
+ *
+ * Memory and streams
+ *   - The caller owns every data buffer (device memory, raw pointers).  The
+ *     library owns only what fmm_build_tree allocates (tree tables on the
+ *     device and a fixed workspace), released by fmm_destroy_tree.
+ *   - fmm_upward / fmm_m2l / fmm_downward / fmm_forces only enqueue work on
+ *     the given stream (a cudaStream_t; NULL = legacy default stream).  They
+ *     do not allocate, free or synchronise.  A tree's workspace is shared by
+ *     its calls, so calls on one tree must not overlap in time (serialise
+ *     them on one stream).
+ *   - Buffer sizes in bytes are reported by fmm_get_sizes.
+ *
+ * Errors: every int-returning call gives 0 or a negative FMM_ERR_* code;
+ * fmm_last_error() returns a message for the calling thread's last failure.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_tree_s *fmm_tree_t;
+typedef void *fmm_stream_t;          /* cudaStream_t */
+
+enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID_ARG = -1,        /* null pointer, bad config, host-only tree */
+    FMM_ERR_TREE = -2,               /* descriptors do not form a valid octree */
+    FMM_ERR_CUDA = -3,               /* a CUDA call or launch failed */
+    FMM_ERR_TIMEOUT = -4,            /* reserved: a device wait exceeded its budget */
+    FMM_ERR_NOMEM = -5               /* device or host allocation failed */
+};
+
+enum { FMM_FP64 = 0, FMM_MIXED = 1 };
+
+enum {
+    FMM_FLAG_HOST_ONLY = 1           /* plan on the host only; no CUDA calls */
+};
+
+typedef struct {
+    double theta;                    /* opening angle, (0.25, 1/sqrt(3)] */
+    double G;                        /* gravitational constant */
+    double box_lo[3];                /* lower corner of every tree's domain */
+    double box_size;                 /* edge of the cubic domain */
+    int32_t precision;               /* FMM_FP64 or FMM_MIXED (same-level pass) */
+    int32_t max_level;               /* deepest level allowed (1..20) */
+    int32_t flags;                   /* FMM_FLAG_* */
+    int32_t reserved;
+} fmm_config;
+
+/* One octree node.  child[k] covers octant (k&1, (k>>1)&1, (k>>2)&1) of the
+ * node; either all eight children are -1 (leaf) or all are valid.  The root
+ * of each tree is level 1 at (0,0,0) with parent -1.  tree_id groups nodes
+ * of independent trees solved together (nodes of different trees never
+ * interact). */
+typedef struct {
+    int32_t level, ix, iy, iz;
+    int32_t parent;
+    int32_t child[8];
+    int32_t tree_id;
+} fmm_node_desc;
+
+typedef struct {
+    int64_t n_nodes, n_leaf, n_refined, n_trees;
+    int32_t max_level, precision;
+    /* required buffer sizes in bytes */
+    int64_t rho_bytes;               /* double [n_leaf][512] */
+    int64_t M_bytes;                 /* double [n_nodes][20][512] */
+    int64_t com_bytes;               /* double [n_nodes][3][512] */
+    int64_t L_bytes;                 /* double or float [n_nodes][20][512] */
+    int64_t Lcomp_bytes;             /* float [n_nodes][20][512] (mixed), else 0 */
+    int64_t dL1_bytes;               /* double [n_nodes][3][512] */
+    int64_t L64_bytes;               /* double [n_nodes][20][512] */
+    int64_t phi_bytes;               /* double [n_leaf][512] */
+    int64_t g_bytes;                 /* double [n_leaf][3][512] */
+    int64_t totals_bytes;            /* double [n_trees][8] */
+    int64_t workspace_bytes;         /* device memory the tree itself holds */
+} fmm_sizes;
+
+typedef struct {
+    /* evaluated directed cell pairs of each kind, in the order
+     * multipole<-multipole, multipole<-monopole, monopole<-monopole,
+     * monopole<-multipole (target <- source) */
+    int64_t interactions[4];
+    int64_t stencil_far;             /* well-separated offsets per parity */
+    int64_t stencil_near;            /* near offsets per parity */
+    int64_t stencil_union;           /* distinct offsets over the 8 parities */
+    double flops_per_interaction[4]; /* operation count of one interaction */
+    int64_t work_items[4];           /* nodes handled by each same-level kernel:
+                                        multipole, monopole, monopole<-multipole, root */
+    int32_t reach;                   /* largest per-axis stencil offset */
+    int32_t launches_m2l;            /* kernel launches per fmm_m2l call */
+    int32_t launches_step;           /* kernel launches per upward+m2l+downward+forces */
+    int32_t reserved;
+} fmm_stats;
+
+/*
+ * Validate descriptors and plan the solve (Sec. 4.2: octree of N^3 sub-grids;
+ * Sec. 4.3: per-level stencil of constant size).  Host work, then one upload
+ * of the tables and one workspace allocation on the current device (none with
+ * FMM_FLAG_HOST_ONLY).  Synchronous.
+ *   nodes: host array of n_nodes descriptors (copied; the caller keeps it).
+ *   cfg:   host config (copied).
+ *   out:   receives the tree handle on success, NULL on failure.
+ * Errors: FMM_ERR_INVALID_ARG (null pointers, n_nodes < 1, theta or box or
+ * precision out of range), FMM_ERR_TREE (broken parent/child links, bad
+ * levels or coordinates, duplicates, a refined node with a missing in-domain
+ * neighbour, levels above cfg->max_level), FMM_ERR_NOMEM, FMM_ERR_CUDA.
+ */
+int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes,
+                   const fmm_config *cfg, fmm_tree_t *out);
+
+/* Buffer sizes for this tree (host, immediate). */
+int fmm_get_sizes(fmm_tree_t tree, fmm_sizes *out);
+
+/* Interaction counts of the opening rule, stencil sizes, the operation-count
+ * model (Sec. 4.3 quotes 455 and 12 operations for its two main kernels;
+ * this library reports its own counts) and launch counts (host, immediate). */
+int fmm_get_stats(fmm_tree_t tree, fmm_stats *out);
+
+/*
+ * Upward pass (Sec. 4.3, first step).  Leaf cells: mass m = rho h^3 placed at
+ * the cell centre (locally homogeneous density, Sec. 3 and Sec. 4.3).
+ * Refined cells: mass, centre of mass and central moments of their eight
+ * child cells, combined in FP64, deepest level first.
+ *   rho: device double [n_leaf][512], read.
+ *   M:   device double [n_nodes][20][512], written.  For leaf nodes only
+ *        component 0 (the cell mass) is written; their other components are
+ *        zero by definition and are not touched.
+ *   com: device double [n_nodes][3][512], written for refined nodes only
+ *        (a leaf cell's centre of mass is its centre by definition).
+ */
+int fmm_upward(fmm_tree_t tree, const double *rho, double *M, double *com,
+               fmm_stream_t stream);
+
+/*
+ * Same-level pass (Sec. 4.3, second step; Sec. 5.1 runs it on the GPU).
+ * Every cell A gathers, from every source cell B the opening rule selects,
+ *   L^(n)_A += -G sum_{m: n+m<=3} ((-1)^m/m!) M_B^(m) . D^(n+m)(X_A - X_B),
+ * D^(k) the k-th derivative tensor of 1/|R|, plus the angular-momentum
+ * correction
+ *   dL1_A,i += (G/6) sum_jkl D^(4)_ijkl(X_A - X_B) [M_B^(3) - (M_B^(0)/M_A^(0)) M_A^(3)]_jkl.
+ * Leaf targets only get orders 0 and 1 (nothing below them needs more).
+ *   M, com: as written by fmm_upward (read).
+ *   L:      device [n_nodes][20][512], written: double (FMM_FP64) or the
+ *           float high part (FMM_MIXED).  Values are in level units: lengths
+ *           in cell widths of the target's level and G factored out, i.e.
+ *           L_physical^(n) = G h^-(n+1) L^(n).  Orders 2-3 of leaf nodes are
+ *           not written.
+ *   L_comp: FMM_MIXED: device float [n_nodes][20][512], the compensation
+ *           (low) part, L = L + L_comp; FMM_FP64: ignored, may be NULL.
+ *   dL1:    device double [n_nodes][3][512], written, level units
+ *           (dL1_physical = G h^-2 dL1).
+ * Precision: FMM_FP64 evaluates in double; FMM_MIXED forms the offsets in
+ * double, contracts in float with two-sum compensated accumulation, and
+ * finishes the correction in double.
+ */
+int fmm_m2l(fmm_tree_t tree, const double *M, const double *com, void *L,
+            float *L_comp, double *dL1, fmm_stream_t stream);
+
+/*
+ * Downward pass (Sec. 4.3, third step), root level first, in FP64:
+ *   L64^(n)_child = L^(n)_child + sum_{k=0}^{3-n} (1/k!) L64^(n+k)_parent . d^k,
+ *   d = X_child - X_parent,   dL1_acc_child = dL1_child + dL1_acc_parent.
+ *   L, L_comp, dL1: as written by fmm_m2l (read; level units).
+ *   com:     as written by fmm_upward (read).
+ *   L64:     device double [n_nodes][20][512], written, physical units; for
+ *            leaf nodes only components 0-3 are written.
+ *   dL1_acc: device double [n_nodes][3][512], written, physical units.  It
+ *            may be the same buffer as dL1.
+ */
+int fmm_downward(fmm_tree_t tree, const void *L, const float *L_comp,
+                 const double *dL1, const double *com, double *L64,
+                 double *dL1_acc, fmm_stream_t stream);
+
+/*
+ * Potential and field at leaf cells and the conservation sums, in FP64:
+ *   phi = L64^(0), g = -(L64^(1) + dL1_acc), f = m g with m = rho h^3.
+ *   phi:    device double [n_leaf][512], written.
+ *   g:      device double [n_leaf][3][512], written.
+ *   totals: device double [n_trees][8], written: sum f (3), sum x cross f
+ *           (3), sum |f|, sum |x cross f|, x measured from the box centre.
+ *           Summation order is fixed, so results are deterministic.
+ */
+int fmm_forces(fmm_tree_t tree, const double *L64, const double *dL1_acc,
+               const double *rho, double *phi, double *g, double *totals,
+               fmm_stream_t stream);
+
+/* Release the tree's host and device memory (synchronises the device first). */
+void fmm_destroy_tree(fmm_tree_t tree);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *fmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_GB300_H */

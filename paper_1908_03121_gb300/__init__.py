@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) cell-based FMM gravity solve (Octo-Tiger, arXiv 1908.03121).
+
+The solve lives in the CUDA library built from ``csrc/`` (C ABI:
+``include/fmm_gb300.h``); ``fmm`` is its Python binding.
+"""
+
+from .fmm import (FmmError, Solver, Tree, fmm_build_tree, fmm_get_sizes, fmm_get_stats,
+                  fmm_upward, fmm_m2l, fmm_downward, fmm_forces, fmm_destroy_tree,
+                  fmm_last_error, load, library_path, FMM_FP64, FMM_MIXED)
+
+__all__ = ["FmmError", "Solver", "Tree", "fmm_build_tree", "fmm_get_sizes", "fmm_get_stats",
+           "fmm_upward", "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_destroy_tree",
+           "fmm_last_error", "load", "library_path", "FMM_FP64", "FMM_MIXED"]

@@ -1,0 +1,631 @@
+// Host side of the C ABI: descriptor validation, planning (neighbour tables,
+// per-parity stencils of the opening rule, level schedules, cost-sorted work
+// lists, exact interaction counts), device upload and launch sequencing.
+//
+// Method: Octo-Tiger's cell-based FMM (arXiv 1908.03121, Sec. 4.3).  The
+// opening rule gives every cell of a level the same set of same-level
+// partners ("constant on each level", Sec. 4.3), which is why it can be
+// tabulated once per child parity and applied as a stencil.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <unordered_map>
+
+#include "fmm_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(FMM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+inline int64_t floordiv2(int64_t v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+
+// node key inside one tree
+inline uint64_t node_key(int level, int64_t ix, int64_t iy, int64_t iz)
+{
+    return (uint64_t(level) << 60) | (uint64_t(ix) << 40) | (uint64_t(iy) << 20) | uint64_t(iz);
+}
+
+bool well_separated(double theta, int64_t ox, int64_t oy, int64_t oz)
+{
+    double o2 = double(ox * ox + oy * oy + oz * oz);
+    return theta * theta * o2 > 1.0;
+}
+
+// pad a pitch up to the next value congruent to want (mod 32)
+int pad_to(int min_value, int want)
+{
+    int v = min_value;
+    while (((v % 32) + 32) % 32 != want) ++v;
+    return v;
+}
+
+// Monopole-monopole coefficients of one offset o (target minus source
+// position is -o cell widths): L0 += c0 m, L1 += c1 m in level units.
+void mono_coef(int ox, int oy, int oz, double c[4])
+{
+    double r2 = double(ox * ox + oy * oy + oz * oz);
+    double r = std::sqrt(r2);
+    double ir3 = 1.0 / (r2 * r);
+    c[0] = -1.0 / r;
+    c[1] = -ox * ir3;
+    c[2] = -oy * ir3;
+    c[3] = -oz * ir3;
+}
+
+}  // namespace
+
+namespace fmm {
+
+int sm_count_of_current_device()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace fmm
+
+using namespace fmm;
+
+static int validate_config(const fmm_config *cfg)
+{
+    if (!(cfg->theta > 0.25 && cfg->theta <= 1.0 / std::sqrt(3.0) + 1e-12))
+        return fail(FMM_ERR_INVALID_ARG,
+                    "theta must lie in (0.25, 1/sqrt(3)]: sources within the 26 neighbour "
+                    "nodes and each leaf pair evaluated once");
+    if (!(cfg->box_size > 0.0) || !std::isfinite(cfg->box_size))
+        return fail(FMM_ERR_INVALID_ARG, "box_size must be positive and finite");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(cfg->box_lo[a])) return fail(FMM_ERR_INVALID_ARG, "box_lo not finite");
+    if (!std::isfinite(cfg->G)) return fail(FMM_ERR_INVALID_ARG, "G not finite");
+    if (cfg->precision != FMM_FP64 && cfg->precision != FMM_MIXED)
+        return fail(FMM_ERR_INVALID_ARG, "precision must be FMM_FP64 or FMM_MIXED");
+    if (cfg->max_level < 1 || cfg->max_level > 20)
+        return fail(FMM_ERR_INVALID_ARG, "max_level must lie in 1..20");
+    return FMM_OK;
+}
+
+// ------------------------------------------------------------ validation
+static int validate_nodes(const fmm_node_desc *d, int64_t n, const fmm_config *cfg,
+                          fmm_tree_s *t, std::vector<std::unordered_map<uint64_t, int32_t>> &maps)
+{
+    int32_t max_tree = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        const fmm_node_desc &x = d[i];
+        if (x.level < 1 || x.level > cfg->max_level)
+            return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": level outside 1..max_level");
+        int64_t side = int64_t(1) << (x.level - 1);
+        if (x.ix < 0 || x.iy < 0 || x.iz < 0 || x.ix >= side || x.iy >= side || x.iz >= side)
+            return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": coordinates outside its level");
+        if (x.tree_id < 0 || x.tree_id >= n)
+            return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": tree_id out of range");
+        max_tree = std::max(max_tree, x.tree_id);
+    }
+    t->n_trees = max_tree + 1;
+    maps.assign(size_t(t->n_trees), {});
+    std::vector<int> roots(size_t(t->n_trees), 0);
+    for (int64_t i = 0; i < n; ++i) {
+        const fmm_node_desc &x = d[i];
+        auto &m = maps[size_t(x.tree_id)];
+        auto ins = m.emplace(node_key(x.level, x.ix, x.iy, x.iz), int32_t(i));
+        if (!ins.second)
+            return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": duplicate of node " +
+                                          std::to_string(ins.first->second));
+        if (x.level == 1) {
+            if (x.parent != -1) return fail(FMM_ERR_TREE, "root node with a parent");
+            roots[size_t(x.tree_id)]++;
+        } else {
+            if (x.parent < 0 || x.parent >= n)
+                return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": parent out of range");
+            const fmm_node_desc &p = d[x.parent];
+            if (p.level != x.level - 1 || p.tree_id != x.tree_id)
+                return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": parent level/tree mismatch");
+            if (p.ix != x.ix / 2 || p.iy != x.iy / 2 || p.iz != x.iz / 2)
+                return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": not inside its parent");
+            int k = (x.ix & 1) + 2 * (x.iy & 1) + 4 * (x.iz & 1);
+            if (p.child[k] != i)
+                return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": parent does not list it");
+        }
+        int nchild = 0;
+        for (int k = 0; k < 8; ++k) nchild += x.child[k] >= 0;
+        if (nchild != 0 && nchild != 8)
+            return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": partially refined");
+        for (int k = 0; k < 8 && nchild; ++k) {
+            int32_t c = x.child[k];
+            if (c >= n) return fail(FMM_ERR_TREE, "child index out of range");
+            const fmm_node_desc &ch = d[c];
+            if (ch.parent != i || ch.level != x.level + 1 || ch.ix != 2 * x.ix + (k & 1) ||
+                ch.iy != 2 * x.iy + ((k >> 1) & 1) || ch.iz != 2 * x.iz + ((k >> 2) & 1))
+                return fail(FMM_ERR_TREE, "node " + std::to_string(i) + ": inconsistent child " +
+                                              std::to_string(k));
+        }
+    }
+    for (int32_t tr = 0; tr < t->n_trees; ++tr)
+        if (roots[size_t(tr)] != 1)
+            return fail(FMM_ERR_TREE, "tree " + std::to_string(tr) + " does not have exactly one root");
+    return FMM_OK;
+}
+
+// ------------------------------------------------------------- stencils
+// Per child parity p: all offsets o whose parent offset floor((p+o)/2) is
+// not well separated, split into well-separated (far) and near offsets.
+static void build_stencils(fmm_tree_s *t)
+{
+    Plan &P = t->plan;
+    double theta = t->cfg.theta;
+    int R = 2 * int(std::floor(1.0 / theta)) + 1;
+    P.reach = R;
+    P.sub = 4 + R;
+    P.py = pad_to(P.sub, 12);
+    P.pz = pad_to(P.sub * P.py, 16);
+    P.sub_stride = P.sub * P.pz;
+    std::vector<char> in_union(size_t(2 * R + 1) * (2 * R + 1) * (2 * R + 1), 0);
+    std::vector<StencilEntry> lists[8];
+    for (int p = 0; p < 8; ++p) {
+        int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
+        std::vector<StencilEntry> far, nearv;
+        for (int oz = -R; oz <= R; ++oz)
+            for (int oy = -R; oy <= R; ++oy)
+                for (int ox = -R; ox <= R; ++ox) {
+                    if (!ox && !oy && !oz) continue;
+                    int o[3] = {ox, oy, oz};
+                    int64_t po[3];
+                    for (int a = 0; a < 3; ++a) po[a] = floordiv2(pp[a] + o[a]);
+                    if (well_separated(theta, po[0], po[1], po[2])) continue;
+                    // window offset of the source relative to the lane base
+                    int u[3], q = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        u[a] = pp[a] + o[a] + R;       // >= 0
+                        q |= (u[a] & 1) << a;
+                    }
+                    int woff = q * P.sub_stride + (u[0] >> 1) + P.py * (u[1] >> 1) + P.pz * (u[2] >> 1);
+                    StencilEntry e{ox, oy, oz, woff};
+                    (well_separated(theta, ox, oy, oz) ? far : nearv).push_back(e);
+                    in_union[size_t((oz + R) * (2 * R + 1) + (oy + R)) * (2 * R + 1) + (ox + R)] = 1;
+                }
+        P.n_far[p] = int(far.size());
+        P.n_near[p] = int(nearv.size());
+        lists[p] = far;
+        lists[p].insert(lists[p].end(), nearv.begin(), nearv.end());
+    }
+    // the kernels rely on every parity having the same far/near counts
+    // (a reflection maps one parity's stencil onto another's)
+    for (int p = 1; p < 8; ++p)
+        if (P.n_far[p] != P.n_far[0] || P.n_near[p] != P.n_near[0]) std::abort();
+    int stride = 0;
+    for (int p = 0; p < 8; ++p) stride = std::max(stride, int(lists[p].size()));
+    P.ent_stride = (stride + 3) & ~3;
+    t->stencil.assign(size_t(8) * P.ent_stride, StencilEntry{0, 0, 0, 0});
+    t->coef32.assign(size_t(8) * P.ent_stride * 4, 0.f);
+    t->coef64.assign(size_t(8) * P.ent_stride * 4, 0.0);
+    for (int p = 0; p < 8; ++p)
+        for (size_t k = 0; k < lists[p].size(); ++k) {
+            const StencilEntry &e = lists[p][k];
+            size_t idx = size_t(p) * P.ent_stride + k;
+            t->stencil[idx] = e;
+            double c[4];
+            mono_coef(e.ox, e.oy, e.oz, c);
+            for (int j = 0; j < 4; ++j) {
+                t->coef64[idx * 4 + j] = c[j];
+                t->coef32[idx * 4 + j] = float(c[j]);
+            }
+        }
+    P.stencil_union = 0;
+    for (char c : in_union) P.stencil_union += c;
+}
+
+// --------------------------------------------------- interaction counting
+// For every parity, far/near list and neighbour slot, the number of
+// (target cell, entry) pairs whose source falls into that slot.
+static void slot_tables(const fmm_tree_s *t, std::vector<int64_t> &tab)
+{
+    const Plan &P = t->plan;
+    tab.assign(size_t(8) * 2 * 27, 0);
+    for (int p = 0; p < 8; ++p) {
+        int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
+        for (int e = 0; e < P.n_far[p] + P.n_near[p]; ++e) {
+            const StencilEntry &s = t->stencil[size_t(p) * P.ent_stride + e];
+            int o[3] = {s.ox, s.oy, s.oz};
+            int64_t cnt[3][3] = {{0}};
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 4; ++c) {
+                    int b = 2 * c + pp[a] + o[a];
+                    int slot = (b + 8) / 8;   // b in [-7, 14]
+                    cnt[a][slot]++;
+                }
+            int fn = e < P.n_far[p] ? 0 : 1;
+            for (int sz = 0; sz < 3; ++sz)
+                for (int sy = 0; sy < 3; ++sy)
+                    for (int sx = 0; sx < 3; ++sx)
+                        tab[(size_t(p) * 2 + fn) * 27 + sx + 3 * sy + 9 * sz] +=
+                            cnt[0][sx] * cnt[1][sy] * cnt[2][sz];
+        }
+    }
+}
+
+// flop model: operation count of one interaction of each kind as the kernels
+// evaluate it (fused multiply-add = 2), excluding compensation.
+static const double kFlops[4] = {
+    /* mp<-mp   */ 376.0,
+    /* mp<-mono */ 376.0,
+    /* mono<-mono */ 8.0,
+    /* mono<-mp */ 240.0,
+};
+
+static void plan_work(fmm_tree_s *t)
+{
+    Plan &P = t->plan;
+    std::vector<int64_t> tab;
+    slot_tables(t, tab);
+    const int64_t n = t->n;
+    std::vector<int64_t> cost(size_t(n), 0);
+    std::vector<char> has_refined_nbr(size_t(n), 0);
+    for (int k = 0; k < 4; ++k) P.interactions[k] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const NodeInfo &x = t->info[size_t(i)];
+        bool leaf = x.leaf_row >= 0;
+        if (x.level == 1) {
+            // root level: every pair of the one node is a candidate
+            int64_t far = 0, nearc = 0;
+            for (int a = 0; a < NCELL; ++a)
+                for (int b = 0; b < NCELL; ++b) {
+                    if (a == b) continue;
+                    int ox = (b & 7) - (a & 7), oy = ((b >> 3) & 7) - ((a >> 3) & 7),
+                        oz = (b >> 6) - (a >> 6);
+                    (well_separated(t->cfg.theta, ox, oy, oz) ? far : nearc)++;
+                }
+            if (leaf) P.interactions[2] += far + nearc;
+            else P.interactions[0] += far;
+            cost[size_t(i)] = leaf ? (far + nearc) : far * 40;
+            continue;
+        }
+        const int32_t *nb = &t->nbr[size_t(i) * 27];
+        int64_t c[4] = {0, 0, 0, 0};
+        for (int s = 0; s < 27; ++s) {
+            if (nb[s] < 0) continue;
+            bool src_leaf = t->info[size_t(nb[s])].leaf_row >= 0;
+            if (!src_leaf && s != 13) has_refined_nbr[size_t(i)] = 1;
+            for (int p = 0; p < 8; ++p) {
+                int64_t fa = tab[(size_t(p) * 2 + 0) * 27 + s];
+                int64_t ne = tab[(size_t(p) * 2 + 1) * 27 + s];
+                if (!leaf) {
+                    if (src_leaf) c[1] += fa + ne;
+                    else c[0] += fa;
+                } else {
+                    if (src_leaf) c[2] += fa + ne;
+                    else c[3] += fa + ne;
+                }
+            }
+        }
+        for (int k = 0; k < 4; ++k) P.interactions[k] += c[k];
+        cost[size_t(i)] = leaf ? c[2] + 30 * c[3] : 45 * (c[0] + c[1]);
+    }
+    // node lists
+    std::vector<int32_t> &L = t->lists;
+    L.clear();
+    auto push_range = [&](const std::vector<int32_t> &v) {
+        ListRange r;
+        r.off = int64_t(L.size());
+        r.count = int64_t(v.size());
+        L.insert(L.end(), v.begin(), v.end());
+        return r;
+    };
+    auto by_cost = [&](std::vector<int32_t> &v) {
+        std::stable_sort(v.begin(), v.end(),
+                         [&](int32_t a, int32_t b) { return cost[size_t(a)] > cost[size_t(b)]; });
+    };
+    std::vector<int32_t> leaves, mp, mono, mx, roots;
+    for (int64_t i = 0; i < n; ++i) {
+        const NodeInfo &x = t->info[size_t(i)];
+        bool leaf = x.leaf_row >= 0;
+        if (leaf) leaves.push_back(int32_t(i));
+        if (x.level == 1) { roots.push_back(int32_t(i)); continue; }
+        if (!leaf) mp.push_back(int32_t(i));
+        else {
+            mono.push_back(int32_t(i));
+            if (has_refined_nbr[size_t(i)]) mx.push_back(int32_t(i));
+        }
+    }
+    by_cost(mp);
+    by_cost(mono);
+    by_cost(mx);
+    P.leaves = push_range(leaves);
+    P.work_mp = push_range(mp);
+    P.work_mono = push_range(mono);
+    P.work_mx = push_range(mx);
+    P.roots = push_range(roots);
+    P.refined_at.assign(size_t(t->max_level) + 2, {});
+    P.nodes_at.assign(size_t(t->max_level) + 2, {});
+    for (int lev = 1; lev <= t->max_level; ++lev) {
+        std::vector<int32_t> ref, all;
+        for (int64_t i = 0; i < n; ++i) {
+            const NodeInfo &x = t->info[size_t(i)];
+            if (x.level != lev) continue;
+            all.push_back(int32_t(i));
+            if (x.leaf_row < 0) ref.push_back(int32_t(i));
+        }
+        P.refined_at[size_t(lev)] = push_range(ref);
+        P.nodes_at[size_t(lev)] = push_range(all);
+    }
+}
+
+// ------------------------------------------------------------- upload
+template <typename T>
+static int upload(T **dst, const std::vector<T> &src)
+{
+    if (src.empty()) { *dst = nullptr; return FMM_OK; }
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), src.size() * sizeof(T));
+    if (e != cudaSuccess) return fail(FMM_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    return FMM_OK;
+}
+
+static void free_device(fmm_tree_s *t)
+{
+    DeviceTables &d = t->dev;
+    void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64,
+                    d.tree_leaf_off, d.tree_leaf_rows, d.mass, d.mp, d.counters, d.partials};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    d = DeviceTables{};
+}
+
+static int upload_tree(fmm_tree_s *t)
+{
+    DeviceTables &d = t->dev;
+    int rc;
+    if ((rc = upload(&d.info, t->info)) || (rc = upload(&d.children, t->children)) ||
+        (rc = upload(&d.nbr, t->nbr)) || (rc = upload(&d.lists, t->lists)) ||
+        (rc = upload(&d.stencil, t->stencil)) || (rc = upload(&d.coef32, t->coef32)) ||
+        (rc = upload(&d.coef64, t->coef64)) || (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||
+        (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)))
+        return rc;
+    size_t es = t->cfg.precision == FMM_MIXED ? sizeof(float) : sizeof(double);
+    size_t mass_b = size_t(t->n) * NCELL * es;
+    size_t mp_b = size_t(std::max<int64_t>(t->n_refined, 1)) * NMP * NCELL * es;
+    size_t part_b = size_t(std::max<int64_t>(t->n_leaf, 1)) * 8 * sizeof(double);
+    cudaError_t e;
+    if ((e = cudaMalloc(&d.mass, mass_b)) != cudaSuccess ||
+        (e = cudaMalloc(&d.mp, mp_b)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void **>(&d.counters), 64 * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void **>(&d.partials), part_b)) != cudaSuccess)
+        return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+    d.workspace_bytes = mass_b + mp_b + part_b + 64 * sizeof(int32_t);
+    return FMM_OK;
+}
+
+// ================================================================ C ABI
+extern "C" {
+
+int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config *cfg,
+                   fmm_tree_t *out)
+{
+    if (!out) return fail(FMM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!nodes || !cfg) return fail(FMM_ERR_INVALID_ARG, "nodes or cfg is NULL");
+    if (n_nodes < 1 || n_nodes > (int64_t(1) << 30))
+        return fail(FMM_ERR_INVALID_ARG, "n_nodes must lie in 1..2^30");
+    int rc = validate_config(cfg);
+    if (rc) return rc;
+    fmm_tree_s *t = new (std::nothrow) fmm_tree_s();
+    if (!t) return fail(FMM_ERR_NOMEM, "host allocation failed");
+    t->cfg = *cfg;
+    t->n = n_nodes;
+    t->host_only = (cfg->flags & FMM_FLAG_HOST_ONLY) != 0;
+    std::vector<std::unordered_map<uint64_t, int32_t>> maps;
+    rc = validate_nodes(nodes, n_nodes, cfg, t, maps);
+    if (rc) { delete t; return rc; }
+    // node table
+    t->info.resize(size_t(n_nodes));
+    t->children.assign(size_t(n_nodes) * 8, -1);
+    int64_t leaf_rows = 0, mp_rows = 0;
+    for (int64_t i = 0; i < n_nodes; ++i) {
+        const fmm_node_desc &x = nodes[i];
+        bool leaf = x.child[0] < 0;
+        t->info[size_t(i)] = NodeInfo{x.level, x.ix, x.iy, x.iz, x.parent,
+                                      leaf ? int32_t(leaf_rows++) : -1,
+                                      leaf ? -1 : int32_t(mp_rows++), x.tree_id};
+        for (int k = 0; k < 8; ++k) t->children[size_t(i) * 8 + k] = x.child[k];
+        t->max_level = std::max(t->max_level, x.level);
+    }
+    t->n_leaf = leaf_rows;
+    t->n_refined = mp_rows;
+    // neighbours, and the nesting rule for refined nodes
+    t->nbr.assign(size_t(n_nodes) * 27, -1);
+    for (int64_t i = 0; i < n_nodes; ++i) {
+        const fmm_node_desc &x = nodes[i];
+        int64_t side = int64_t(1) << (x.level - 1);
+        auto &m = maps[size_t(x.tree_id)];
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t jx = x.ix + dx, jy = x.iy + dy, jz = x.iz + dz;
+                    if (jx < 0 || jy < 0 || jz < 0 || jx >= side || jy >= side || jz >= side) continue;
+                    auto it = m.find(node_key(x.level, jx, jy, jz));
+                    int s = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                    if (it != m.end()) t->nbr[size_t(i) * 27 + s] = it->second;
+                    else if (x.child[0] >= 0) {
+                        delete t;
+                        return fail(FMM_ERR_TREE, "node " + std::to_string(i) +
+                                                      " is refined but an in-domain neighbour is missing");
+                    }
+                }
+    }
+    // leaf rows grouped per tree (fixed-order reductions)
+    t->tree_leaf_off.assign(size_t(t->n_trees) + 1, 0);
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (t->info[size_t(i)].leaf_row >= 0) t->tree_leaf_off[size_t(t->info[size_t(i)].tree) + 1]++;
+    for (int32_t k = 0; k < t->n_trees; ++k) t->tree_leaf_off[size_t(k) + 1] += t->tree_leaf_off[size_t(k)];
+    t->tree_leaf_rows.assign(size_t(t->n_leaf), 0);
+    {
+        std::vector<int32_t> fill(t->tree_leaf_off.begin(), t->tree_leaf_off.end() - 1);
+        for (int64_t i = 0; i < n_nodes; ++i) {
+            const NodeInfo &x = t->info[size_t(i)];
+            if (x.leaf_row >= 0) t->tree_leaf_rows[size_t(fill[size_t(x.tree)]++)] = x.leaf_row;
+        }
+    }
+    build_stencils(t);
+    plan_work(t);
+    if (!t->host_only) {
+        if (cudaGetDevice(&t->device) != cudaSuccess) {
+            delete t;
+            return fail(FMM_ERR_CUDA, "no CUDA device available (use FMM_FLAG_HOST_ONLY to plan only)");
+        }
+        rc = upload_tree(t);
+        if (rc) { free_device(t); delete t; return rc; }
+    }
+    *out = t;
+    return FMM_OK;
+}
+
+int fmm_get_sizes(fmm_tree_t t, fmm_sizes *o)
+{
+    if (!t || !o) return fail(FMM_ERR_INVALID_ARG, "NULL argument");
+    std::memset(o, 0, sizeof *o);
+    o->n_nodes = t->n;
+    o->n_leaf = t->n_leaf;
+    o->n_refined = t->n_refined;
+    o->n_trees = t->n_trees;
+    o->max_level = t->max_level;
+    o->precision = t->cfg.precision;
+    int64_t per = int64_t(NCELL) * 8;
+    bool mixed = t->cfg.precision == FMM_MIXED;
+    o->rho_bytes = t->n_leaf * per;
+    o->M_bytes = t->n * NCOMP * per;
+    o->com_bytes = t->n * 3 * per;
+    o->L_bytes = t->n * NCOMP * NCELL * (mixed ? 4 : 8);
+    o->Lcomp_bytes = mixed ? t->n * NCOMP * NCELL * 4 : 0;
+    o->dL1_bytes = t->n * 3 * per;
+    o->L64_bytes = t->n * NCOMP * per;
+    o->phi_bytes = t->n_leaf * per;
+    o->g_bytes = t->n_leaf * 3 * per;
+    o->totals_bytes = int64_t(t->n_trees) * 8 * 8;
+    o->workspace_bytes = int64_t(t->dev.workspace_bytes);
+    return FMM_OK;
+}
+
+int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
+{
+    if (!t || !o) return fail(FMM_ERR_INVALID_ARG, "NULL argument");
+    std::memset(o, 0, sizeof *o);
+    const Plan &P = t->plan;
+    for (int k = 0; k < 4; ++k) {
+        o->interactions[k] = P.interactions[k];
+        o->flops_per_interaction[k] = kFlops[k];
+    }
+    o->stencil_far = P.n_far[0];
+    o->stencil_near = P.n_near[0];
+    o->stencil_union = P.stencil_union;
+    o->work_items[0] = P.work_mp.count;
+    o->work_items[1] = P.work_mono.count;
+    o->work_items[2] = P.work_mx.count;
+    o->work_items[3] = P.roots.count;
+    o->reach = P.reach;
+    int m2l = 1 /*pack*/ + (P.roots.count > 0) + (P.work_mp.count > 0) + (P.work_mono.count > 0) +
+              (P.work_mx.count > 0);
+    int up = 1;
+    for (int lev = 1; lev < t->max_level; ++lev) up += P.refined_at[size_t(lev)].count > 0;
+    int down = 0;
+    for (int lev = 1; lev <= t->max_level; ++lev) down += P.nodes_at[size_t(lev)].count > 0;
+    o->launches_m2l = m2l;
+    o->launches_step = up + m2l + down + 2;
+    return FMM_OK;
+}
+
+static int check_device_tree(fmm_tree_t t)
+{
+    if (!t) return fail(FMM_ERR_INVALID_ARG, "tree is NULL");
+    if (t->host_only) return fail(FMM_ERR_INVALID_ARG, "tree was planned with FMM_FLAG_HOST_ONLY");
+    return FMM_OK;
+}
+
+int fmm_upward(fmm_tree_t t, const double *rho, double *M, double *com, fmm_stream_t stream)
+{
+    int rc = check_device_tree(t);
+    if (rc) return rc;
+    if (!rho || !M || !com) return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_p2m(t, rho, M, s);
+    if (e != cudaSuccess) return cuda_fail(e, "p2m launch");
+    for (int lev = t->max_level - 1; lev >= 1; --lev) {
+        if (t->plan.refined_at[size_t(lev)].count == 0) continue;
+        e = launch_m2m_level(t, lev, M, com, s);
+        if (e != cudaSuccess) return cuda_fail(e, "m2m launch");
+    }
+    return FMM_OK;
+}
+
+int fmm_m2l(fmm_tree_t t, const double *M, const double *com, void *L, float *L_comp,
+            double *dL1, fmm_stream_t stream)
+{
+    int rc = check_device_tree(t);
+    if (rc) return rc;
+    if (!M || !com || !L || !dL1) return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
+    if (t->cfg.precision == FMM_MIXED && !L_comp)
+        return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_pack(t, M, com, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+    int nl = 0;
+    e = launch_m2l(t, L, L_comp, dL1, s, &nl);
+    if (e != cudaSuccess) return cuda_fail(e, "m2l launch");
+    return FMM_OK;
+}
+
+int fmm_downward(fmm_tree_t t, const void *L, const float *L_comp, const double *dL1,
+                 const double *com, double *L64, double *dL1_acc, fmm_stream_t stream)
+{
+    int rc = check_device_tree(t);
+    if (rc) return rc;
+    if (!L || !dL1 || !com || !L64 || !dL1_acc) return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
+    if (t->cfg.precision == FMM_MIXED && !L_comp)
+        return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int lev = 1; lev <= t->max_level; ++lev) {
+        if (t->plan.nodes_at[size_t(lev)].count == 0) continue;
+        cudaError_t e = launch_l2l_level(t, lev, L, L_comp, dL1, com, L64, dL1_acc, s);
+        if (e != cudaSuccess) return cuda_fail(e, "l2l launch");
+    }
+    return FMM_OK;
+}
+
+int fmm_forces(fmm_tree_t t, const double *L64, const double *dL1_acc, const double *rho,
+               double *phi, double *g, double *totals, fmm_stream_t stream)
+{
+    int rc = check_device_tree(t);
+    if (rc) return rc;
+    if (!L64 || !dL1_acc || !rho || !phi || !g || !totals)
+        return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
+    cudaError_t e = launch_forces(t, L64, dL1_acc, rho, phi, g, totals,
+                                  static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "forces launch");
+    return FMM_OK;
+}
+
+void fmm_destroy_tree(fmm_tree_t t)
+{
+    if (!t) return;
+    if (!t->host_only) {
+        cudaDeviceSynchronize();
+        free_device(t);
+    }
+    delete t;
+}
+
+const char *fmm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

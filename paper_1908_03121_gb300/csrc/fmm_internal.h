@@ -1,0 +1,126 @@
+// Internal declarations of the GB300 FMM library (not part of the C ABI).
+//
+// Layouts used inside the library, beyond the caller-visible ones described
+// in include/fmm_gb300.h:
+//   - "parity-split" cell order inside a node: cell (x,y,z) sits at
+//       ((x&1) + 2(y&1) + 4(z&1)) * 64 + (x>>1) + 4(y>>1) + 16(z>>1),
+//     so the 64 cells of one parity class (which share one stencil) are
+//     contiguous;
+//   - packed same-level source data (workspace), in level units:
+//       mass[node][512]          cell mass (all nodes)
+//       mp[mp_row][19][512]      refined nodes only: centre-of-mass offset
+//                                from the cell centre in cell widths (3),
+//                                A2 = mult * M2 / (2 h^2) (6),
+//                                A3 = mult * M3 / (6 h^3) (10)
+//     where mult is the number of index permutations of a symmetric
+//     component (so full-tensor contractions become plain dot products).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fmm_gb300.h"
+
+namespace fmm {
+
+constexpr int NSIDE = 8;
+constexpr int NCELL = 512;
+constexpr int NCOMP = 20;
+constexpr int NMP = 19;          // packed multipole fields per refined cell
+
+// per-node table row (device and host)
+struct NodeInfo {
+    int32_t level, ix, iy, iz;
+    int32_t parent;
+    int32_t leaf_row;    // density / potential row, -1 for refined nodes
+    int32_t mp_row;      // row in the packed multipole workspace, -1 for leaves
+    int32_t tree;
+};
+
+// stencil entry of one parity class; far entries come first
+struct StencilEntry {
+    int32_t ox, oy, oz;  // source offset in cell widths
+    int32_t woff;        // offset inside the parity-split halo window
+};
+
+struct DeviceTables {
+    NodeInfo *info = nullptr;        // [n]
+    int32_t *children = nullptr;     // [n][8]
+    int32_t *nbr = nullptr;          // [n][27], slot (dx+1)+3(dy+1)+9(dz+1)
+    int32_t *lists = nullptr;        // all node-index lists, see Plan offsets
+    StencilEntry *stencil = nullptr; // [8][ent_stride]
+    float *coef32 = nullptr;         // [8][ent_stride][4] monopole coefficients
+    double *coef64 = nullptr;        // [8][ent_stride][4]
+    int32_t *tree_leaf_off = nullptr;   // [n_trees + 1]
+    int32_t *tree_leaf_rows = nullptr;  // [n_leaf]
+    // workspace
+    void *mass = nullptr;            // [n][512] float or double
+    void *mp = nullptr;              // [n_refined][19][512] float or double
+    int32_t *counters = nullptr;     // work-queue heads
+    double *partials = nullptr;      // [n_leaf][8]
+    size_t workspace_bytes = 0;
+};
+
+// offsets of the node lists inside DeviceTables::lists
+struct ListRange {
+    int64_t off = 0, count = 0;
+};
+
+struct Plan {
+    // window geometry
+    int reach = 5;                   // largest per-axis offset
+    int sub = 9;                     // parity sub-window edge = 4 + reach
+    int py = 12, pz = 112;           // padded pitches of a sub-window
+    int sub_stride = 1008;           // elements per sub-window
+    int n_far[8] = {0}, n_near[8] = {0};
+    int ent_stride = 0;              // entries reserved per parity
+    int64_t stencil_union = 0;
+    // node lists
+    ListRange leaves;                // all leaf nodes (P2M, forces)
+    std::vector<ListRange> refined_at;   // [level] refined nodes (M2M)
+    std::vector<ListRange> nodes_at;     // [level] all nodes (L2L)
+    ListRange work_mp, work_mono, work_mx, roots;
+    int64_t interactions[4] = {0, 0, 0, 0};
+};
+
+}  // namespace fmm
+
+struct fmm_tree_s {
+    fmm_config cfg;
+    int64_t n = 0, n_leaf = 0, n_refined = 0;
+    int32_t n_trees = 0, max_level = 0;
+    std::vector<fmm::NodeInfo> info;
+    std::vector<int32_t> children, nbr, lists;
+    std::vector<fmm::StencilEntry> stencil;
+    std::vector<float> coef32;
+    std::vector<double> coef64;
+    std::vector<int32_t> tree_leaf_off, tree_leaf_rows;
+    fmm::Plan plan;
+    bool host_only = false;
+    int device = -1;
+    fmm::DeviceTables dev;
+};
+
+namespace fmm {
+
+// kernels (each returns a cudaError_t from the launch)
+cudaError_t launch_p2m(const fmm_tree_s *t, const double *rho, double *M, cudaStream_t s);
+cudaError_t launch_m2m_level(const fmm_tree_s *t, int level, double *M, double *com,
+                             cudaStream_t s);
+cudaError_t launch_pack(const fmm_tree_s *t, const double *M, const double *com,
+                        cudaStream_t s);
+cudaError_t launch_m2l(const fmm_tree_s *t, void *L, float *Lc, double *dL1,
+                       cudaStream_t s, int *n_launches);
+cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L,
+                             const float *Lc, const double *dL1, const double *com,
+                             double *L64, double *dacc, cudaStream_t s);
+cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *dacc,
+                          const double *rho, double *phi, double *g, double *totals,
+                          cudaStream_t s);
+
+int sm_count_of_current_device();
+
+}  // namespace fmm

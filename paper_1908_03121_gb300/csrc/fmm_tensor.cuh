@@ -1,0 +1,121 @@
+// Device helpers: symmetric-tensor index maps and the derivative tensors of
+// 1/|R| used by the same-level interactions (Sec. 4.3: Taylor coefficients of
+// a cell's potential from the multipole moments of its partners).
+//
+// Symmetric components are stored once each:
+//   rank 2 (6):  xx xy xz yy yz zz
+//   rank 3 (10): xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+//   rank 4 (15): xxxx xxxy xxxz xxyy xxyz xxzz xyyy xyyz xyzz xzzz
+//                yyyy yyyz yyzz yzzz zzzz
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fmm {
+
+// number of index orderings of each symmetric component
+__host__ __device__ constexpr int mult2(int q) { return (q == 1 || q == 2 || q == 4) ? 2 : 1; }
+__host__ __device__ constexpr int mult3(int q)
+{
+    return q == 0 || q == 6 || q == 9 ? 1 : (q == 4 ? 6 : 3);
+}
+
+// rank-3 component (i, q2) for i in 0..2 and q2 a rank-2 component
+__host__ __device__ constexpr int r3_of(int i, int q)
+{
+    constexpr int t[3][6] = {{0, 1, 2, 3, 4, 5}, {1, 3, 4, 6, 7, 8}, {2, 4, 5, 7, 8, 9}};
+    return t[i][q];
+}
+// rank-4 component (i, q3) for i in 0..2 and q3 a rank-3 component
+__host__ __device__ constexpr int r4_of(int i, int q)
+{
+    constexpr int t[3][10] = {{0, 1, 2, 3, 4, 5, 6, 7, 8, 9},
+                              {1, 3, 4, 6, 7, 8, 10, 11, 12, 13},
+                              {2, 4, 5, 7, 8, 9, 11, 12, 13, 14}};
+    return t[i][q];
+}
+// rank-2 component (i, j)
+__host__ __device__ constexpr int r2_of(int i, int j)
+{
+    constexpr int t[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    return t[i][j];
+}
+// rank-3 component (i, j, k)
+__host__ __device__ constexpr int r3_ijk(int i, int j, int k) { return r3_of(i, r2_of(j, k)); }
+
+template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
+
+// Derivative tensors of 1/|R| (Cartesian closed forms):
+//   D1_i = d1 R_i,  D2_ij = d2 R_i R_j + d1 delta_ij,
+//   D3_ijk = d3 R_i R_j R_k + d2 (R_i delta_jk + R_j delta_ik + R_k delta_ij),
+//   D4_ijkl = d4 R_i R_j R_k R_l + d3 (sum of the six R R delta terms)
+//             + d2 (delta_ij delta_kl + delta_ik delta_jl + delta_il delta_jk),
+// with d0 = 1/r, d1 = -1/r^3, d2 = 3/r^5, d3 = -15/r^7, d4 = 105/r^9.
+template <typename T, bool WITH_D4>
+struct DTensors {
+    T D0, D1[3], D2[6], D3[10], D4[15];
+
+    __device__ __forceinline__ void eval(T x, T y, T z)
+    {
+        T r2 = x * x + y * y + z * z;
+        T ri = rsqrt_t<T>(r2);
+        T ri2 = ri * ri;
+        T d0 = ri;
+        T d1 = -d0 * ri2;
+        T d2 = T(-3) * d1 * ri2;
+        T d3 = T(-5) * d2 * ri2;
+        D0 = d0;
+        D1[0] = d1 * x; D1[1] = d1 * y; D1[2] = d1 * z;
+        T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+        D2[0] = d2 * xx + d1; D2[1] = d2 * xy; D2[2] = d2 * xz;
+        D2[3] = d2 * yy + d1; D2[4] = d2 * yz; D2[5] = d2 * zz + d1;
+        T d3x = d3 * x, d3y = d3 * y, d3z = d3 * z;
+        D3[0] = d3x * xx + T(3) * d2 * x;
+        D3[1] = d3x * xy + d2 * y;
+        D3[2] = d3x * xz + d2 * z;
+        D3[3] = d3x * yy + d2 * x;
+        D3[4] = d3x * yz;
+        D3[5] = d3x * zz + d2 * x;
+        D3[6] = d3y * yy + T(3) * d2 * y;
+        D3[7] = d3y * yz + d2 * z;
+        D3[8] = d3y * zz + d2 * y;
+        D3[9] = d3z * zz + T(3) * d2 * z;
+        if (WITH_D4) {
+            T d4 = T(-7) * d3 * ri2;
+            T d4xx = d4 * xx, d4yy = d4 * yy, d4xy = d4 * xy, d4xz = d4 * xz, d4yz = d4 * yz;
+            D4[0] = d4xx * xx + T(6) * d3 * xx + T(3) * d2;
+            D4[1] = d4xx * xy + T(3) * d3 * xy;
+            D4[2] = d4xx * xz + T(3) * d3 * xz;
+            D4[3] = d4xx * yy + d3 * (xx + yy) + d2;
+            D4[4] = d4xx * yz + d3 * yz;
+            D4[5] = d4xx * zz + d3 * (xx + zz) + d2;
+            D4[6] = d4xy * yy + T(3) * d3 * xy;
+            D4[7] = d4xy * yz + d3 * xz;
+            D4[8] = d4xy * zz + d3 * xy;
+            D4[9] = d4xz * zz + T(3) * d3 * xz;
+            D4[10] = d4yy * yy + T(6) * d3 * yy + T(3) * d2;
+            D4[11] = d4yy * yz + T(3) * d3 * yz;
+            D4[12] = d4yy * zz + d3 * (yy + zz) + d2;
+            D4[13] = d4yz * zz + T(3) * d3 * yz;
+            D4[14] = d4 * zz * zz + T(6) * d3 * zz + T(3) * d2;
+        }
+    }
+};
+
+// cell (x,y,z) of a node -> parity-split position
+__host__ __device__ __forceinline__ int parity_index(int x, int y, int z)
+{
+    return ((x & 1) + 2 * (y & 1) + 4 * (z & 1)) * 64 + (x >> 1) + 4 * (y >> 1) + 16 * (z >> 1);
+}
+
+// TwoSum (Knuth): s + e == a + b exactly, s = fl(a + b)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+}  // namespace fmm

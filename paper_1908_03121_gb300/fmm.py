@@ -1,0 +1,285 @@
+"""ctypes binding of ``libfmm_gb300.so`` (C ABI in ``include/fmm_gb300.h``).
+
+The functions keep the C names and only marshal arguments: torch CUDA tensors
+(or raw device addresses as ints) become pointers, the current torch stream
+becomes the ``cudaStream_t``.  Every step of the solve runs in the library's
+CUDA kernels; nothing here computes, and there is no CPU fallback: if the
+library cannot be built or loaded, the first call raises.
+"""
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import _build
+
+FMM_OK = 0
+FMM_ERR_INVALID_ARG = -1
+FMM_ERR_TREE = -2
+FMM_ERR_CUDA = -3
+FMM_ERR_TIMEOUT = -4
+FMM_ERR_NOMEM = -5
+FMM_FP64 = 0
+FMM_MIXED = 1
+FMM_FLAG_HOST_ONLY = 1
+
+EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
+            "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_destroy_tree",
+            "fmm_last_error")
+
+NCELL = 512
+NCOMP = 20
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class FmmConfig(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("G", ctypes.c_double),
+                ("box_lo", ctypes.c_double * 3), ("box_size", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("max_level", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class FmmSizes(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_leaf", ctypes.c_int64),
+                ("n_refined", ctypes.c_int64), ("n_trees", ctypes.c_int64),
+                ("max_level", ctypes.c_int32), ("precision", ctypes.c_int32)] + [
+        (k, ctypes.c_int64) for k in (
+            "rho_bytes", "M_bytes", "com_bytes", "L_bytes", "Lcomp_bytes", "dL1_bytes",
+            "L64_bytes", "phi_bytes", "g_bytes", "totals_bytes", "workspace_bytes")]
+
+
+class FmmStats(ctypes.Structure):
+    _fields_ = [("interactions", ctypes.c_int64 * 4), ("stencil_far", ctypes.c_int64),
+                ("stencil_near", ctypes.c_int64), ("stencil_union", ctypes.c_int64),
+                ("flops_per_interaction", ctypes.c_double * 4),
+                ("work_items", ctypes.c_int64 * 4), ("reach", ctypes.c_int32),
+                ("launches_m2l", ctypes.c_int32), ("launches_step", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build=True):
+    """Build (if stale) and load the CUDA library; raises if impossible."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = _build.build() if build else _build.LIB
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        lib.fmm_build_tree.argtypes = [P, ctypes.c_int64, ctypes.POINTER(FmmConfig),
+                                       ctypes.POINTER(P)]
+        lib.fmm_get_sizes.argtypes = [P, ctypes.POINTER(FmmSizes)]
+        lib.fmm_get_stats.argtypes = [P, ctypes.POINTER(FmmStats)]
+        lib.fmm_upward.argtypes = [P, P, P, P, P]
+        lib.fmm_m2l.argtypes = [P, P, P, P, P, P, P]
+        lib.fmm_downward.argtypes = [P, P, P, P, P, P, P, P]
+        lib.fmm_forces.argtypes = [P, P, P, P, P, P, P, P]
+        lib.fmm_destroy_tree.argtypes = [P]
+        lib.fmm_destroy_tree.restype = None
+        lib.fmm_last_error.argtypes = []
+        lib.fmm_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("fmm_destroy_tree", "fmm_last_error"):
+                getattr(lib, name).restype = ctypes.c_int
+        _LIB = lib
+        return lib
+
+
+def _check(rc):
+    if rc != FMM_OK:
+        raise FmmError(rc, load().fmm_last_error().decode())
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int address / None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_contiguous():
+        raise ValueError("buffers must be contiguous")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Tree:
+    """Handle of an ``fmm_tree_t`` plus its sizes; closes on ``close()``."""
+
+    def __init__(self, handle, host_only):
+        self.handle = handle
+        self.host_only = host_only
+        self.sizes = fmm_get_sizes(self)
+        self.stats = fmm_get_stats(self)
+
+    @property
+    def value(self):
+        return self.handle.value
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            fmm_destroy_tree(self)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fmm_build_tree(desc, theta, G=1.0, box_lo=(0.0, 0.0, 0.0), box_size=1.0,
+                   precision=FMM_FP64, max_level=20, host_only=False):
+    lib = load()
+    d = np.ascontiguousarray(desc, dtype=np.int32)
+    if d.ndim != 2 or d.shape[1] != 14:
+        raise ValueError("descriptor array must be (n, 14) int32")
+    if isinstance(precision, str):
+        precision = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
+    cfg = FmmConfig(float(theta), float(G), (ctypes.c_double * 3)(*box_lo), float(box_size),
+                    int(precision), int(max_level), FMM_FLAG_HOST_ONLY if host_only else 0, 0)
+    h = ctypes.c_void_p()
+    _check(lib.fmm_build_tree(d.ctypes.data_as(ctypes.c_void_p), len(d), ctypes.byref(cfg),
+                              ctypes.byref(h)))
+    return Tree(h, host_only)
+
+
+def fmm_get_sizes(tree):
+    s = FmmSizes()
+    _check(load().fmm_get_sizes(tree.handle, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in FmmSizes._fields_}
+
+
+def fmm_get_stats(tree):
+    s = FmmStats()
+    _check(load().fmm_get_stats(tree.handle, ctypes.byref(s)))
+    out = {}
+    for k, _ in FmmStats._fields_:
+        v = getattr(s, k)
+        out[k] = list(v) if hasattr(v, "__len__") else v
+    return out
+
+
+def fmm_upward(tree, rho, M, com, stream=None):
+    _check(load().fmm_upward(tree.handle, _ptr(rho), _ptr(M), _ptr(com), _stream(stream)))
+
+
+def fmm_m2l(tree, M, com, L, L_comp, dL1, stream=None):
+    _check(load().fmm_m2l(tree.handle, _ptr(M), _ptr(com), _ptr(L), _ptr(L_comp), _ptr(dL1),
+                          _stream(stream)))
+
+
+def fmm_downward(tree, L, L_comp, dL1, com, L64, dL1_acc, stream=None):
+    _check(load().fmm_downward(tree.handle, _ptr(L), _ptr(L_comp), _ptr(dL1), _ptr(com),
+                               _ptr(L64), _ptr(dL1_acc), _stream(stream)))
+
+
+def fmm_forces(tree, L64, dL1_acc, rho, phi, g, totals, stream=None):
+    _check(load().fmm_forces(tree.handle, _ptr(L64), _ptr(dL1_acc), _ptr(rho), _ptr(phi),
+                             _ptr(g), _ptr(totals), _stream(stream)))
+
+
+def fmm_destroy_tree(tree):
+    load().fmm_destroy_tree(tree.handle)
+
+
+def fmm_last_error():
+    return load().fmm_last_error().decode()
+
+
+class Solver:
+    """Owns the device buffers of one tree and runs the four passes.
+
+    ``step(rho)`` enqueues upward, same-level, downward and forces on the
+    current stream; ``capture(rho)`` records that sequence once into a CUDA
+    graph which ``replay()`` relaunches.
+    """
+
+    def __init__(self, desc, theta, precision="mixed", G=1.0, box_lo=(0.0, 0.0, 0.0),
+                 box_size=1.0, device="cuda"):
+        import torch
+        self.tree = fmm_build_tree(desc, theta, G, box_lo, box_size, precision)
+        s = self.tree.sizes
+        n, nl, nt = s["n_nodes"], s["n_leaf"], s["n_trees"]
+        self.mixed = s["precision"] == FMM_MIXED
+        f64 = dict(dtype=torch.float64, device=device)
+        self.M = torch.zeros((n, NCOMP, NCELL), **f64)
+        self.com = torch.zeros((n, 3, NCELL), **f64)
+        if self.mixed:
+            self.L = torch.zeros((n, NCOMP, NCELL), dtype=torch.float32, device=device)
+            self.Lc = torch.zeros((n, NCOMP, NCELL), dtype=torch.float32, device=device)
+        else:
+            self.L = torch.zeros((n, NCOMP, NCELL), **f64)
+            self.Lc = None
+        self.dL1 = torch.zeros((n, 3, NCELL), **f64)
+        self.L64 = torch.zeros((n, NCOMP, NCELL), **f64)
+        self.dacc = torch.zeros((n, 3, NCELL), **f64)
+        self.phi = torch.zeros((nl, NCELL), **f64)
+        self.g = torch.zeros((nl, 3, NCELL), **f64)
+        self.totals = torch.zeros((nt, 8), **f64)
+        self.rho = torch.zeros((nl, NCELL), **f64)
+        self.graph = None
+
+    def upward(self, rho=None, stream=None):
+        fmm_upward(self.tree, self.rho if rho is None else rho, self.M, self.com, stream)
+
+    def m2l(self, stream=None):
+        fmm_m2l(self.tree, self.M, self.com, self.L, self.Lc, self.dL1, stream)
+
+    def downward(self, stream=None):
+        fmm_downward(self.tree, self.L, self.Lc, self.dL1, self.com, self.L64, self.dacc, stream)
+
+    def forces(self, rho=None, stream=None):
+        fmm_forces(self.tree, self.L64, self.dacc, self.rho if rho is None else rho, self.phi,
+                   self.g, self.totals, stream)
+
+    def step(self, rho=None, stream=None):
+        self.upward(rho, stream)
+        self.m2l(stream)
+        self.downward(stream)
+        self.forces(rho, stream)
+
+    def capture(self):
+        """Record step() on self.rho into a CUDA graph (call once, then replay)."""
+        import torch
+        self.step()                       # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def close(self):
+        self.graph = None
+        if self.tree is not None:
+            self.tree.close()
+            self.tree = None

@@ -1,0 +1,161 @@
+"""CPU tests of the C ABI: the library loads and exports every declared
+symbol, descriptors are validated on the host, and the host planner's
+stencils and interaction counts agree with the oracle's brute-force opening
+rule.  No GPU compute is called here (trees are planned host-only)."""
+
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1908_03121_gb300 as F
+from paper_1908_03121_gb300 import fmm as B
+from oracle import oracle as O
+from workloads import make_config, uniform_tree, adaptive_tree, leaf_nodes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fmm_gb300.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmm_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = F.load()
+    names = declared_symbols()
+    assert set(B.EXPORTED) == set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(B.FmmConfig) == 8 * 6 + 4 * 4
+    assert ctypes.sizeof(B.FmmSizes) == 8 * 4 + 4 * 2 + 8 * 11
+    assert ctypes.sizeof(B.FmmStats) == 8 * 4 + 8 * 3 + 8 * 4 + 8 * 4 + 4 * 4
+
+
+def plan(desc, theta):
+    return F.fmm_build_tree(desc, theta, host_only=True)
+
+
+def _adaptive(max_level=4, r=0.12):
+    def want(lo, hi):
+        c = np.array([0.31, 0.62, 0.45])
+        d = np.clip(c, lo, hi) - c
+        return float(d @ d) < r * r
+    return adaptive_tree(want, max_level)
+
+
+@pytest.mark.parametrize("case", ["cfg1", "cfg2", "adaptive4", "adaptive4_035"])
+def test_planner_counts_match_oracle(case):
+    if case.startswith("cfg"):
+        c = make_config(case)
+        desc, rho, theta = c["desc"], c["rho"], c["theta"]
+    else:
+        desc = _adaptive()
+        rho = np.ones((len(leaf_nodes(desc)), 512))
+        theta = 0.35 if case.endswith("035") else 0.5
+    t = plan(desc, theta)
+    ot = O.Tree(desc, theta)
+    M, com = O.upward(ot, rho)
+    _, _, counts = O.m2l(ot, M, com)
+    assert list(t.stats["interactions"]) == list(counts)
+
+
+def test_planner_stencil_sizes():
+    facts = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_facts.json")))
+    t = plan(uniform_tree(3), 0.35)
+    assert t.stats["stencil_union"] == facts["stencil_neighbours"]["value"]
+    assert t.stats["stencil_far"] + t.stats["stencil_near"] == 743
+    t = plan(uniform_tree(3), 0.5)
+    assert (t.stats["stencil_far"], t.stats["stencil_near"]) == (231, 32)
+    assert t.stats["reach"] == 5
+
+
+def test_sizes_report():
+    c = make_config("cfg2")
+    t = F.fmm_build_tree(c["desc"], 0.5, precision="mixed", host_only=True)
+    s = t.sizes
+    assert s["n_nodes"] == 73 and s["n_leaf"] == 64 and s["n_refined"] == 9
+    assert s["M_bytes"] == 73 * 20 * 512 * 8
+    assert s["L_bytes"] == 73 * 20 * 512 * 4 and s["Lcomp_bytes"] == s["L_bytes"]
+    assert s["g_bytes"] == 64 * 3 * 512 * 8 and s["totals_bytes"] == 64
+
+
+def expect_error(code, desc, theta=0.5, **kw):
+    with pytest.raises(F.FmmError) as ei:
+        F.fmm_build_tree(desc, theta, host_only=True, **kw)
+    assert ei.value.code == code, str(ei.value)
+
+
+def test_rejects_bad_config():
+    d = uniform_tree(2)
+    expect_error(B.FMM_ERR_INVALID_ARG, d, theta=0.7)
+    expect_error(B.FMM_ERR_INVALID_ARG, d, theta=0.25)
+    expect_error(B.FMM_ERR_INVALID_ARG, d, box_size=0.0)
+    expect_error(B.FMM_ERR_INVALID_ARG, d, precision=7)
+    expect_error(B.FMM_ERR_TREE, uniform_tree(3), max_level=2)
+
+
+def test_rejects_malformed_trees():
+    d = uniform_tree(3)
+    bad = d.copy(); bad[5, 1] += 1                       # wrong coordinates
+    expect_error(B.FMM_ERR_TREE, bad)
+    bad = d.copy(); bad[3, 4] = 2                        # wrong parent
+    expect_error(B.FMM_ERR_TREE, bad)
+    bad = d.copy(); bad[1, 5 + 3] = -1                   # partially refined
+    expect_error(B.FMM_ERR_TREE, bad)
+    bad = d.copy(); bad[0, 4] = 3                        # root with a parent
+    expect_error(B.FMM_ERR_TREE, bad)
+    bad = np.concatenate([d, d[-1:]])                    # duplicate node
+    expect_error(B.FMM_ERR_TREE, bad)
+    bad = d.copy(); bad[:, 13] = 1                       # tree 0 has no root
+    expect_error(B.FMM_ERR_TREE, bad)
+    bad = d.copy(); bad[7, 0] = 25                       # level above max_level
+    expect_error(B.FMM_ERR_TREE, bad)
+
+
+def test_rejects_unbalanced_refinement():
+    """A refined node whose in-domain same-level neighbour is missing."""
+    d = uniform_tree(2)
+    # refine only child 0 of the root, then child 0 of that child: the level-3
+    # refined node's neighbours at level 3 inside child 0 exist, but the
+    # nesting rule also needs its level-3 neighbours across the child-0 faces
+    rows = [list(r) for r in d]
+    def refine(i):
+        lvl, ix, iy, iz = rows[i][:4]
+        for k in range(8):
+            rows.append([lvl + 1, 2 * ix + (k & 1), 2 * iy + ((k >> 1) & 1),
+                         2 * iz + ((k >> 2) & 1), i] + [-1] * 8 + [0])
+            rows[i][5 + k] = len(rows) - 1
+    refine(1)
+    first = rows[1][5 + 7]      # the level-3 child touching the centre
+    refine(first)
+    bad = np.asarray(rows, dtype=np.int32)
+    expect_error(B.FMM_ERR_TREE, bad)
+
+
+def test_rejects_null_and_host_only_calls():
+    t = plan(uniform_tree(2), 0.5)
+    with pytest.raises(F.FmmError) as ei:
+        F.fmm_upward(t, 0, 0, 0, stream=0)
+    assert ei.value.code == B.FMM_ERR_INVALID_ARG
+    with pytest.raises(F.FmmError):
+        F.fmm_m2l(t, 1, 1, 1, 1, 1, stream=0)
+    assert "HOST_ONLY" in F.fmm_last_error()
+
+
+def test_batched_trees_plan_independently():
+    c = make_config("cfg1")
+    from workloads import concat_trees
+    d = concat_trees([c["desc"], c["desc"], c["desc"]])
+    t = plan(d, 0.5)
+    one = plan(c["desc"], 0.5)
+    assert list(t.stats["interactions"]) == [3 * v for v in one.stats["interactions"]]
+    assert t.sizes["n_trees"] == 3

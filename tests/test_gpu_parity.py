@@ -1,0 +1,322 @@
+"""GPU parity of the CUDA library (through its C ABI) against the FP64 oracle.
+
+Small trees are compared element by element, stage by stage and end to end;
+the full-size workloads (in the launch configuration the benchmark times) are
+compared on sampled cells that the oracle computes one by one.  Bars: the
+FP64 path to relative 1e-12, the mixed path to relative force error 1e-6
+(max |g - g_ref| / max |g_ref|) and net torque 1e-12 of sum |x cross f|.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1908_03121_gb300 as F
+from oracle import oracle as O
+from workloads import (make_config, uniform_tree, adaptive_tree, concat_trees,
+                       leaf_nodes, leaf_cell_centres)
+from workloads.density import gaussian_blobs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FORCE_TOL = 1e-6
+TORQUE_TOL = 1e-12
+ORDER_SLICES = [slice(0, 1), slice(1, 4), slice(4, 10), slice(10, 20)]
+
+
+# ------------------------------------------------------------------ cases
+def _adaptive_desc(max_level=4, centre=(0.31, 0.62, 0.45), r=0.12, tree_id=0):
+    c = np.asarray(centre)
+
+    def want(lo, hi):
+        d = np.clip(c, lo, hi) - c
+        return float(d @ d) < r * r
+    return adaptive_tree(want, max_level, tree_id=tree_id)
+
+
+def small_case(name):
+    """Small workloads the oracle solves completely in seconds."""
+    if name in ("cfg1", "cfg2"):
+        return make_config(name)
+    if name == "cfg2_t035":
+        return make_config("cfg2", theta=0.35)
+    rng = np.random.default_rng(7)
+    if name == "adaptive4":
+        desc = _adaptive_desc()
+    elif name == "batch3":
+        desc = concat_trees([uniform_tree(2), _adaptive_desc(4),
+                             _adaptive_desc(3, centre=(0.7, 0.2, 0.5), r=0.2)])
+    else:
+        raise ValueError(name)
+    pos = leaf_cell_centres(desc)
+    rho = gaussian_blobs(pos, rng.uniform(0.3, 0.7, size=(3, 3)), 0.08, 1.0)
+    return dict(name=name, desc=desc, rho=rho.reshape(-1, 512), theta=0.5, G=1.0,
+                box_lo=(0.0, 0.0, 0.0), box_size=1.0)
+
+
+SMALL = ["cfg1", "cfg2", "cfg2_t035", "adaptive4", "batch3"]
+_ORACLE = {}
+
+
+def oracle_solution(name):
+    if name not in _ORACLE:
+        c = small_case(name)
+        _ORACLE[name] = (c, O.solve(O.Tree.from_config(c), c["rho"]))
+    return _ORACLE[name]
+
+
+# ---------------------------------------------------------------- helpers
+def widths(desc, box_size=1.0):
+    return box_size / (8.0 * 2.0 ** (desc[:, 0].astype(np.float64) - 1))
+
+
+def level_to_phys(Llev, desc, G=1.0):
+    """Level units -> physical: L^(n) * G h^-(n+1)."""
+    h = widths(desc)[:, None, None]
+    out = np.empty_like(Llev, dtype=np.float64)
+    for n, sl in enumerate(ORDER_SLICES):
+        out[:, sl] = Llev[:, sl] * G * h ** (-(n + 1))
+    return out
+
+
+def phys_to_level(L, desc, G=1.0):
+    h = widths(desc)[:, None, None]
+    out = np.empty_like(L)
+    for n, sl in enumerate(ORDER_SLICES):
+        out[:, sl] = L[:, sl] / (G * h ** (-(n + 1)))
+    return out
+
+
+def rel_err(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def solve_gpu(c, precision):
+    s = F.Solver(c["desc"], c["theta"], precision=precision, G=c["G"], box_lo=c["box_lo"],
+                 box_size=c["box_size"])
+    s.rho.copy_(dev(c["rho"]))
+    s.step()
+    torch.cuda.synchronize()
+    return s
+
+
+def defined_L_mask(desc):
+    """L slots the library defines: all 20 for refined nodes, 0-3 for leaves."""
+    m = np.ones((len(desc), 20, 1), dtype=bool)
+    m[desc[:, 5] < 0, 4:, :] = False
+    return m
+
+
+def assert_L_close(L, Lref, desc, tol):
+    mask = np.broadcast_to(defined_L_mask(desc), L.shape)
+    for n, sl in enumerate(ORDER_SLICES):
+        for lev in np.unique(desc[:, 0]):
+            sel = desc[:, 0] == lev
+            a = np.where(mask[sel, sl], L[sel, sl], 0.0)
+            b = np.where(mask[sel, sl], Lref[sel, sl], 0.0)
+            if np.abs(b).max() == 0:
+                continue
+            e = rel_err(a, b)
+            assert e <= tol, f"order {n} level {lev}: rel err {e:.3e}"
+
+
+def tree_torque(tot):
+    return np.linalg.norm(tot[:, 3:6], axis=1) / tot[:, 7]
+
+
+def tree_force(tot):
+    return np.linalg.norm(tot[:, 0:3], axis=1) / tot[:, 6]
+
+
+# ------------------------------------------------------- stage by stage
+@pytest.mark.parametrize("name", SMALL)
+def test_upward_parity(name):
+    c, ref = oracle_solution(name)
+    s = solve_gpu(c, "fp64")
+    M, com = host(s.M), host(s.com)
+    refined = c["desc"][:, 5] >= 0
+    assert rel_err(M[:, 0], ref["M"][:, 0]) <= FP64_TOL
+    assert rel_err(M[refined][:, 4:10], ref["M"][refined][:, 4:10]) <= FP64_TOL
+    assert rel_err(M[refined][:, 10:20], ref["M"][refined][:, 10:20]) <= FP64_TOL
+    assert np.all(M[refined][:, 1:4] == 0.0)
+    assert np.abs(com[refined] - ref["com"][refined]).max() <= FP64_TOL * 1.0
+    s.close()
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_m2l_parity_fp64(name):
+    """The oracle's moments in, the GPU same-level pass out, FP64."""
+    c, ref = oracle_solution(name)
+    s = F.Solver(c["desc"], c["theta"], precision="fp64")
+    s.M.copy_(dev(ref["M"]))
+    s.com.copy_(dev(ref["com"]))
+    s.m2l()
+    torch.cuda.synchronize()
+    L = level_to_phys(host(s.L), c["desc"])
+    assert_L_close(L, ref["L"], c["desc"], FP64_TOL)
+    h = widths(c["desc"])[:, None, None]
+    assert rel_err(host(s.dL1) * h ** -2, ref["dL1"]) <= FP64_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_m2l_parity_mixed(name):
+    """Mixed precision: float contraction with compensated sums."""
+    c, ref = oracle_solution(name)
+    s = F.Solver(c["desc"], c["theta"], precision="mixed")
+    s.M.copy_(dev(ref["M"]))
+    s.com.copy_(dev(ref["com"]))
+    s.m2l()
+    torch.cuda.synchronize()
+    Llev = host(s.L).astype(np.float64) + host(s.Lc).astype(np.float64)
+    assert_L_close(level_to_phys(Llev, c["desc"]), ref["L"], c["desc"], 2e-6)
+    s.close()
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_downward_and_forces_parity(name):
+    """The oracle's same-level result in, GPU downward + forces out (FP64)."""
+    c, ref = oracle_solution(name)
+    s = F.Solver(c["desc"], c["theta"], precision="fp64")
+    s.com.copy_(dev(ref["com"]))
+    s.L.copy_(dev(phys_to_level(ref["L"], c["desc"])))
+    h = widths(c["desc"])[:, None, None]
+    s.dL1.copy_(dev(ref["dL1"] * h ** 2))
+    s.rho.copy_(dev(c["rho"]))
+    s.downward()
+    s.forces()
+    torch.cuda.synchronize()
+    assert_L_close(host(s.L64), ref["L64"], c["desc"], FP64_TOL)
+    assert rel_err(host(s.dacc), ref["dL1acc"]) <= FP64_TOL
+    assert rel_err(host(s.phi), ref["phi"]) <= FP64_TOL
+    assert rel_err(host(s.g), ref["g"]) <= FP64_TOL
+    tot, rt = host(s.totals), ref["totals"]
+    np.testing.assert_allclose(tot[:, 6:8], rt[:, 6:8], rtol=1e-13)
+    assert np.all(np.abs(tot[:, 0:6] - rt[:, 0:6]) <= 1e-13 * rt[:, 6:7].max())
+    s.close()
+
+
+# --------------------------------------------------------- end to end
+@pytest.mark.parametrize("name", SMALL)
+def test_end_to_end_fp64(name):
+    c, ref = oracle_solution(name)
+    s = solve_gpu(c, "fp64")
+    assert rel_err(host(s.g), ref["g"]) <= FP64_TOL
+    assert rel_err(host(s.phi), ref["phi"]) <= FP64_TOL
+    tot = host(s.totals)
+    assert np.all(tree_force(tot) <= 1e-13)
+    assert np.all(tree_torque(tot) <= 1e-13)
+    s.close()
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_end_to_end_mixed(name):
+    c, ref = oracle_solution(name)
+    s = solve_gpu(c, "mixed")
+    g, gref = host(s.g), ref["g"]
+    assert rel_err(g, gref) <= FORCE_TOL
+    assert rel_err(host(s.phi), ref["phi"]) <= FORCE_TOL
+    tot = host(s.totals)
+    assert np.all(tree_force(tot) <= 1e-10)
+    assert np.all(tree_torque(tot) <= TORQUE_TOL), tree_torque(tot)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_deterministic_and_graph_replay(precision):
+    c, _ = oracle_solution("adaptive4")
+    s = solve_gpu(c, precision)
+    g1, t1 = host(s.g).copy(), host(s.totals).copy()
+    s.step()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(s.g), g1) and np.array_equal(host(s.totals), t1)
+    s.capture()
+    s.g.zero_()
+    s.totals.zero_()
+    s.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(s.g), g1) and np.array_equal(host(s.totals), t1)
+    s.close()
+
+
+def test_in_tree_library_is_the_one_loaded():
+    F.load()
+    maps = open("/proc/self/maps").read()
+    assert F.library_path() in maps
+
+
+# ------------------------------------------------- full-size, sampled
+def _sample_cells(c, n, seed):
+    rng = np.random.default_rng(seed)
+    rho = c["rho"]
+    flat = rho.reshape(-1)
+    dense = np.argsort(flat)[-max(1, flat.size // 100):]
+    pick = np.concatenate([rng.choice(dense, n // 2, replace=False),
+                           rng.choice(flat.size, n - n // 2, replace=False)])
+    return pick // 512, pick % 512          # leaf rows, cells
+
+
+def _path_targets(desc, rows, cells):
+    leaves = leaf_nodes(desc)
+    targets = set()
+    for r, cell in zip(rows, cells):
+        node = int(leaves[r])
+        g = np.array([cell & 7, (cell >> 3) & 7, cell >> 6]) + 8 * desc[node, 1:4]
+        while node >= 0:
+            loc = g - 8 * desc[node, 1:4]
+            targets.add(node * 512 + int(loc[0] + 8 * loc[1] + 64 * loc[2]))
+            node = int(desc[node, 4])
+            g = g >> 1
+    return np.array(sorted(targets), dtype=np.int64)
+
+
+def sampled_reference(c, n=96, seed=3):
+    """Oracle field at sampled leaf cells: same-level results on the sampled
+    cells' ancestor paths only, then the full downward pass (the other cells'
+    results are zero and never reach the sampled ones)."""
+    tree = O.Tree.from_config(c)
+    M, com = O.upward(tree, c["rho"])
+    rows, cells = _sample_cells(c, n, seed)
+    targets = _path_targets(c["desc"], rows, cells)
+    L, dL1, _ = O.m2l(tree, M, com, targets=targets)
+    L64, acc = O.downward(tree, com, L, dL1)
+    phi, g, _ = O.forces(tree, L64, acc, c["rho"])
+    return dict(rows=rows, cells=cells, g=g[rows, :, cells], phi=phi[rows, cells],
+                targets=targets, L=L, M=M, com=com)
+
+
+@pytest.mark.parametrize("name", ["cfg3", "cfg4", "cfg5"])
+def test_full_size_sampled(name):
+    c = make_config(name)
+    ref = sampled_reference(c)
+    rows, cells = ref["rows"], ref["cells"]
+    tnodes, tcells = ref["targets"] // 512, ref["targets"] % 512
+    # FP64 path: sampled field and sampled same-level results
+    s = solve_gpu(c, "fp64")
+    assert rel_err(host(s.g)[rows, :, cells], ref["g"]) <= FP64_TOL
+    assert rel_err(host(s.phi)[rows, cells], ref["phi"]) <= FP64_TOL
+    Lgpu = level_to_phys(host(s.L), c["desc"])[tnodes, :, tcells]
+    Lref = ref["L"][tnodes, :, tcells]
+    for sl in ORDER_SLICES[:2]:
+        assert rel_err(Lgpu[:, sl], Lref[:, sl]) <= FP64_TOL
+    tot64 = host(s.totals)
+    assert np.all(tree_torque(tot64) <= 1e-13)
+    s.close()
+    # mixed path, the benchmark's configuration
+    s = solve_gpu(c, "mixed")
+    assert rel_err(host(s.g)[rows, :, cells], ref["g"]) <= FORCE_TOL
+    tot = host(s.totals)
+    assert np.all(tree_force(tot) <= 1e-10)
+    assert np.all(tree_torque(tot) <= TORQUE_TOL), tree_torque(tot)
+    s.close()

@@ -1,0 +1,444 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 cell-based FMM gravity solve (Octo-Tiger, arXiv 1908.03121).
+
+One step = the whole hot path on one synthetic workload: upward pass, same-level
+(M2L) pass, downward pass, forces and conservation sums, replayed from one
+captured CUDA graph.  The metric is same-level cell-interactions per second
+(evaluated directed target<-source cell pairs, all four kinds) over the whole
+step time.  Default workload: the level-7 contact binary (cfg5), mixed
+precision.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank solves its own replica (the solve has no
+exchange step); the time is the maximum over ranks and the value sums all
+ranks' interactions.  ``--impl reference`` times the FP64 CPU oracle instead,
+on a bounded sample of target cells per step, on the host's cores.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M2L cell-interactions/s on 1 GB300, FP32-mixed vs FP64 at rel. force err ≤1e-6"
+UNIT = "cell-interactions/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILES = os.path.join(ROOT, "profiles")
+# FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 rate of a GB300 (Blackwell Ultra): 1.25 TFLOP/s
+FP64_PEAK_TFLOPS = 1.25
+L2_FLUSH_BYTES = 256 << 20
+
+WORKLOAD_TEXT = {
+    "cfg1": "root + 8 leaf sub-grids (4096 cells), two Gaussians",
+    "cfg2": "uniform level-3 octree, 64 leaf sub-grids (32768 cells), polytrope binary q=0.3",
+    "cfg3": "adaptive octree to level 5 around a polytrope binary (q=0.3)",
+    "cfg4": "16 independent adaptive octrees (levels 4-7, q=0.1..1.0) batched in one solve",
+    "cfg5": "contact binary of two n=1.5 polytropes (q=0.3), adaptive octree to level 7",
+}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="cfg5")
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------- helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, pci=None):
+        self.proc = None
+        self.path = None
+        self.pci = pci
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.pci:
+            cmd += ["-i", self.pci]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fmm_m2l.cu", "fmm_tensor.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1908_03121_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(PROFILES, f"{kernel}_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    val = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not src or not val or src.group(1) != kernel_source_hash():
+        return None
+    return float(val.group(1))
+
+
+def workload_config(name, c, stats, sizes, precision):
+    cells = int(sizes["n_leaf"]) * 512
+    return {
+        "workload": f"{name}: {WORKLOAD_TEXT.get(name, name)}; {sizes['n_nodes']} sub-grids, "
+                    f"{sizes['n_leaf']} leaves ({cells} leaf cells), theta={c['theta']}, "
+                    f"order 3, {precision}",
+        "n_trees": int(sizes["n_trees"]),
+        "n_nodes": int(sizes["n_nodes"]),
+        "leaf_cells": cells,
+        "theta": c["theta"],
+        "interactions_per_step": int(sum(stats["interactions"])),
+        "interactions_by_kind": {"mp<-mp": stats["interactions"][0],
+                                 "mp<-mono": stats["interactions"][1],
+                                 "mono<-mono": stats["interactions"][2],
+                                 "mono<-mp": stats["interactions"][3]},
+        "l2": "flushed (256 MiB write) before every timed step; working set > L2",
+    }
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_rate(c, seconds, batch=4096, seed=0, n_threads=None):
+    """The FP64 oracle's same-level pass on random target cells of the workload,
+    batch after batch until ``seconds`` elapse.  Returns (rate, info)."""
+    from oracle import oracle as O
+    tree = O.Tree.from_config(c)
+    M, com = O.upward(tree, c["rho"])
+    rng = np.random.default_rng(seed)
+    n_threads = n_threads or os.cpu_count() or 1
+    total_cells = tree.n * 512
+    done = 0
+    inter = 0
+    t0 = time.perf_counter()
+    while True:
+        targets = np.sort(rng.choice(total_cells, size=batch, replace=False))
+        _, _, counts = O.m2l(tree, M, com, targets=targets, n_threads=n_threads,
+                            compact=True)
+        done += batch
+        inter += int(counts.sum())
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return inter / el, dict(cells=done, interactions=inter, seconds=el, cores=n_threads)
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from workloads import make_config
+    c = make_config(args.workload)
+    from oracle import oracle as O
+    tree = O.Tree.from_config(c)
+    M, com = O.upward(tree, c["rho"])
+    n_threads = os.cpu_count() or 1
+    rng = np.random.default_rng(1)
+    batch = 2048
+    total_cells = tree.n * 512
+
+    def one_step():
+        targets = np.sort(rng.choice(total_cells, size=batch, replace=False))
+        t0 = time.perf_counter()
+        _, _, counts = O.m2l(tree, M, com, targets=targets, n_threads=n_threads, compact=True)
+        return time.perf_counter() - t0, int(counts.sum())
+
+    for _ in range(args.warmup):
+        one_step()
+    times, inters = [], []
+    for _ in range(args.steps):
+        t, n = one_step()
+        times.append(t)
+        inters.append(n)
+    value = sum(inters) / sum(times)
+    ms = 1000.0 * sum(times) / len(times)
+    sample = (f"FP64 oracle same-level pass over {batch} random target cells per step "
+              f"(all levels) of {args.workload}, upward pass untimed")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload)}",
+                      "sample_cells_per_step": batch, "theta": c["theta"]},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours
+def time_graph(torch, solver, steps, warmup, flush, stream, clocks=None):
+    """Per-step device ms of graph replays; the L2 flush runs between steps,
+    outside the events."""
+    for _ in range(warmup):
+        flush()
+        solver.replay()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if clocks:
+        clocks.start()
+    for k in range(steps):
+        flush()
+        starts[k].record(stream)
+        solver.replay()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return float(np.mean(ms)), ms, clk
+
+
+def run_ours(args):
+    import torch
+    import paper_1908_03121_gb300 as F
+    from workloads import make_config
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    c = make_config(args.workload)
+    rho_host = torch.from_numpy(c["rho"]).pin_memory()
+    flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush_val = [0]
+
+    def flush():
+        flush_val[0] = (flush_val[0] + 1) & 0xFF
+        flush_buf.fill_(flush_val[0])
+
+    stream = torch.cuda.current_stream()
+    solver = F.Solver(c["desc"], c["theta"], precision=args.precision)
+    stats, sizes = solver.tree.stats, solver.tree.sizes
+    interactions = int(sum(stats["interactions"]))
+    solver.rho.copy_(rho_host.cuda())
+    solver.capture()
+    pci = None
+    try:
+        pci = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        pass
+    barrier()
+    torch.cuda.synchronize()
+    ms, per_step, clk = time_graph(torch, solver, args.steps, args.warmup, flush, stream,
+                                   ClockSampler(pci) if rank == 0 else None)
+    torch.cuda.synchronize()
+    barrier()
+    ms_max = max_over_ranks(ms)
+    value = interactions * world / (ms_max / 1000.0)
+
+    # end to end through the public API: pinned host density in, totals out
+    tot_host = torch.empty_like(solver.totals, device="cpu").pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver.rho.copy_(rho_host, non_blocking=True)
+        solver.replay()
+        tot_host.copy_(solver.totals, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    e2e_ms_max = max_over_ranks(float(np.mean(e2e_ms)))
+    e2e = {"value": interactions * world / (e2e_ms_max / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": int(rho_host.numel() * 8),
+           "d2h_bytes_per_step": int(tot_host.numel() * 8),
+           "ms_per_step": e2e_ms_max}
+
+    # accuracy and conservation of this run, against the FP64 GPU path
+    g_mixed = solver.g.clone()
+    tot = solver.totals.double().cpu().numpy()
+    net_torque = float(np.max(np.linalg.norm(tot[:, 3:6], axis=1) / tot[:, 7]))
+    net_force = float(np.max(np.linalg.norm(tot[:, 0:3], axis=1) / tot[:, 6]))
+    solver.graph = None
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+              "config": dict(workload_config(args.workload, c, stats, sizes, args.precision),
+                             parallelism=f"replicas x{world}" if world > 1 else "single GPU")}
+    result["e2e"] = e2e
+    result["gpu_launches"] = int(stats["launches_step"]) * args.steps
+    result["clocks"] = clk
+
+    if rank == 0:
+        # per-kernel device times, measured live with events on the launch stream
+        tsolver = F.Solver(c["desc"], c["theta"], precision=args.precision, timing=True)
+        tsolver.rho.copy_(solver.rho)
+        for _ in range(2):
+            flush()
+            tsolver.step()
+        tsolver.kernel_times()          # discard warm-up timings
+        nrep = max(3, min(args.steps, 20))
+        for _ in range(nrep):
+            flush()
+            tsolver.step()
+        kt = tsolver.kernel_times()
+        tsolver.close()
+        per_kernel = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0,
+                          "ms_per_step": v[0] / nrep, "launches_per_step": v[1] / nrep}
+                      for k, v in kt.items() if v[1]}
+        step_kernel_ms = sum(v["ms_per_step"] for v in per_kernel.values())
+        for v in per_kernel.values():
+            v["share"] = v["ms_per_step"] / step_kernel_ms if step_kernel_ms else 0.0
+        result["kernels"] = per_kernel
+        inter = stats["interactions"]
+        kin = stats["kernel_interactions"]
+        fl = stats["flops_per_interaction"]
+        # the multipole kernel evaluates every multipole-target pair except the
+        # root level's (all multipole<-multipole), which the root kernel takes
+        work = {"multipole": (kin[0] - inter[1]) * fl[0] + inter[1] * fl[1],
+                "monopole": kin[1] * fl[2],
+                "mono_multi": kin[2] * fl[3]}
+        dom = max(work, key=lambda k: per_kernel.get(k, {}).get("ms_per_step", 0.0))
+        dom_ms = per_kernel[dom]["ms_per_launch"]
+        achieved = work[dom] / (dom_ms / 1000.0) / 1e12
+        if args.precision == "mixed":
+            peak, which = FP32_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+        else:
+            peak, which = FP64_PEAK_TFLOPS, "FP64: GB300 rate 1.25 TFLOP/s"
+        result["roofline"] = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                              "unit": "TFLOP/s", "frac": achieved / peak,
+                              "traffic": profiled_traffic(dom, args.workload),
+                              "peak_source": which,
+                              "flops_per_launch": work[dom],
+                              "flops_per_interaction": fl}
+        result["m2l_interactions_per_s"] = interactions / (
+            sum(per_kernel.get(k, {}).get("ms_per_step", 0.0)
+                for k in ("pack", "root", "multipole", "monopole", "mono_multi")) / 1000.0)
+
+        # FP64 GPU path on the same workload: rate and the mixed path's error
+        if args.precision == "mixed" and args.fp64_steps > 0:
+            s64 = F.Solver(c["desc"], c["theta"], precision="fp64")
+            s64.rho.copy_(solver.rho)
+            s64.capture()
+            ms64, _, _ = time_graph(torch, s64, args.fp64_steps, 1, flush, stream)
+            g64 = s64.g
+            err = float((g_mixed - g64).abs().max() / g64.abs().max())
+            tot64 = s64.totals.cpu().numpy()
+            result["fp64_path"] = {
+                "value": interactions / (ms64 / 1000.0), "ms_per_step": ms64,
+                "speedup_mixed_over_fp64": ms64 / ms,
+                "net_torque": float(np.max(np.linalg.norm(tot64[:, 3:6], axis=1) / tot64[:, 7]))}
+            result["mixed_accuracy"] = {"force_err_vs_fp64_path": err, "net_torque": net_torque,
+                                        "net_force": net_force}
+            s64.close()
+
+        if world == 1 and not args.no_cpu_baseline:
+            rate, info = oracle_rate(c, args.cpu_seconds)
+            result["cpu_baseline"] = {
+                "value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                "sample": f"FP64 oracle same-level pass over {info['cells']} random target "
+                          f"cells of {args.workload} ({info['interactions']} interactions, "
+                          f"{info['seconds']:.1f} s), upward pass untimed"}
+        print(json.dumps(result), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -66,7 +66,17 @@ enum {
 enum { FMM_FP64 = 0, FMM_MIXED = 1 };
 
 enum {
-    FMM_FLAG_HOST_ONLY = 1           /* plan on the host only; no CUDA calls */
+    FMM_FLAG_HOST_ONLY = 1,          /* plan on the host only; no CUDA calls */
+    FMM_FLAG_TIMING = 2              /* bracket every kernel launch with CUDA
+                                        events on the call's stream (eager use
+                                        only: do not capture such a tree in a
+                                        graph); read back by fmm_get_stats */
+};
+
+/* kernel slots of fmm_stats.kernel_ms / kernel_launches */
+enum {
+    FMM_K_P2M = 0, FMM_K_M2M, FMM_K_PACK, FMM_K_ROOT, FMM_K_MULTIPOLE, FMM_K_MONOPOLE,
+    FMM_K_MONO_MULTI, FMM_K_L2L, FMM_K_FORCES, FMM_K_REDUCE, FMM_K_COUNT
 };
 
 typedef struct {
@@ -120,10 +130,16 @@ typedef struct {
     double flops_per_interaction[4]; /* operation count of one interaction */
     int64_t work_items[4];           /* nodes handled by each same-level kernel:
                                         multipole, monopole, monopole<-multipole, root */
+    int64_t kernel_interactions[4];  /* interactions evaluated by each of those kernels */
     int32_t reach;                   /* largest per-axis stencil offset */
     int32_t launches_m2l;            /* kernel launches per fmm_m2l call */
     int32_t launches_step;           /* kernel launches per upward+m2l+downward+forces */
-    int32_t reserved;
+    int32_t timing;                  /* 1 if the tree was built with FMM_FLAG_TIMING */
+    /* FMM_FLAG_TIMING only: device time (ms) and launch count per kernel slot
+     * (FMM_K_*), summed over the launches since the previous fmm_get_stats
+     * call, which waits for those launches and then resets the sums. */
+    double kernel_ms[16];
+    int64_t kernel_launches[16];
 } fmm_stats;
 
 /*
@@ -147,7 +163,8 @@ int fmm_get_sizes(fmm_tree_t tree, fmm_sizes *out);
 
 /* Interaction counts of the opening rule, stencil sizes, the operation-count
  * model (Sec. 4.3 quotes 455 and 12 operations for its two main kernels;
- * this library reports its own counts) and launch counts (host, immediate). */
+ * this library reports its own counts) and launch counts (host, immediate;
+ * with FMM_FLAG_TIMING it first waits for the timed launches). */
 int fmm_get_stats(fmm_tree_t tree, fmm_stats *out);
 
 /*

@@ -402,8 +402,10 @@ int oracle_upward(const int32_t *desc, int64_t n, const double *cfg,
 
 /* --------------------------------------------------------------- M2L */
 
+/* all same-level interactions of target cell c of node i: packed L20 and
+ * dL1 (orders above the target's need are zero) */
 static void o_m2l_target(const otree *t, const double *M, const double *com,
-                         int64_t i, int c, double *L, double *dL1, int64_t cnt[4])
+                         int64_t i, int c, double L20[NCOMP], double dL13[3], int64_t cnt[4])
 {
     int level = o_level(t, i);
     int a_leaf = o_is_leaf(t, i);
@@ -435,27 +437,27 @@ static void o_m2l_target(const otree *t, const double *M, const double *com,
             cnt[kind - 1]++;
         }
     }
-    double p20[NCOMP];
-    memset(p20, 0, sizeof p20);
-    for (int n = 0; n <= nmax; ++n) pack(Lf[n], n, p20);
-    for (int k = 0; k < NCOMP; ++k) L[(i * NCOMP + k) * NCELL + c] = p20[k];
-    for (int a = 0; a < 3; ++a) dL1[(i * 3 + a) * NCELL + c] = d1[a];
+    memset(L20, 0, sizeof(double) * NCOMP);
+    for (int n = 0; n <= nmax; ++n) pack(Lf[n], n, L20);
+    for (int a = 0; a < 3; ++a) dL13[a] = d1[a];
 }
 
 /*
  * Same-level interactions for every cell (targets == NULL) or for the listed
  * cells (targets[k] = node * 512 + cell; the other cells are left untouched).
  * L: [n][20][512] (orders 2 and 3 are zero for leaf cells, which never need
- * them); dL1: [n][3][512]; counts[4]: evaluated pairs per kind.
+ * them); dL1: [n][3][512]; counts[4]: evaluated pairs per kind.  With
+ * compact != 0 (targets given), L is [n_targets][20] and dL1 [n_targets][3].
  */
 int oracle_m2l(const int32_t *desc, int64_t n, const double *cfg,
                const double *M, const double *com, double *L, double *dL1,
                int64_t *counts, const int64_t *targets, int64_t n_targets,
-               int n_threads)
+               int n_threads, int compact)
 {
     otree T, *t = &T;
     o_init(t, desc, n, cfg);
     int64_t total = targets ? n_targets : n * NCELL;
+    if (!targets) compact = 0;
     int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -464,7 +466,17 @@ int oracle_m2l(const int32_t *desc, int64_t n, const double *cfg,
     for (int64_t k = 0; k < total; ++k) {
         int64_t tc = targets ? targets[k] : k;
         int64_t cnt[4] = { 0, 0, 0, 0 };
-        o_m2l_target(t, M, com, tc / NCELL, (int)(tc % NCELL), L, dL1, cnt);
+        int64_t i = tc / NCELL;
+        int c = (int)(tc % NCELL);
+        double L20[NCOMP], d3[3];
+        o_m2l_target(t, M, com, i, c, L20, d3, cnt);
+        if (compact) {
+            for (int q = 0; q < NCOMP; ++q) L[k * NCOMP + q] = L20[q];
+            for (int a = 0; a < 3; ++a) dL1[k * 3 + a] = d3[a];
+        } else {
+            for (int q = 0; q < NCOMP; ++q) L[(i * NCOMP + q) * NCELL + c] = L20[q];
+            for (int a = 0; a < 3; ++a) dL1[(i * 3 + a) * NCELL + c] = d3[a];
+        }
         c0 += cnt[0]; c1 += cnt[1]; c2 += cnt[2]; c3 += cnt[3];
     }
     (void)n_threads;

@@ -48,7 +48,7 @@ def _lib():
             P = ctypes.c_void_p
             I64 = ctypes.c_int64
             lib.oracle_upward.argtypes = [P, I64, P, P, P, P]
-            lib.oracle_m2l.argtypes = [P, I64, P, P, P, P, P, P, P, I64, ctypes.c_int]
+            lib.oracle_m2l.argtypes = [P, I64, P, P, P, P, P, P, P, I64, ctypes.c_int, ctypes.c_int]
             lib.oracle_sources.argtypes = [P, I64, P, I64, ctypes.c_int, P, P, I64]
             lib.oracle_sources.restype = I64
             lib.oracle_coverage.argtypes = [P, I64, P, P, P]
@@ -101,25 +101,31 @@ def upward(tree, rho):
     return M, com
 
 
-def m2l(tree, M, com, targets=None, n_threads=0):
+def m2l(tree, M, com, targets=None, n_threads=0, compact=False):
     """Returns (L [n,20,512], dL1 [n,3,512], counts[4]).
 
     With ``targets`` (int64 node*512+cell), only those cells are computed and
-    the rest of L / dL1 is zero.  counts = (mp<-mp, mp<-mono, mono<-mono,
-    mono<-mp) evaluated pairs.
+    the rest of L / dL1 is zero; with ``compact`` as well, L is
+    [n_targets, 20] and dL1 [n_targets, 3].  counts = (mp<-mp, mp<-mono,
+    mono<-mono, mono<-mp) evaluated pairs.
     """
     M = _f64(M)
     com = _f64(com)
-    L = np.zeros((tree.n, NCOMP, NCELL))
-    dL1 = np.zeros((tree.n, 3, NCELL))
     counts = np.zeros(4, dtype=np.int64)
     if targets is None:
         tp, nt = None, 0
+        compact = False
     else:
         targets = np.ascontiguousarray(targets, dtype=np.int64)
         tp, nt = _p(targets), len(targets)
+    if compact:
+        L = np.zeros((nt, NCOMP))
+        dL1 = np.zeros((nt, 3))
+    else:
+        L = np.zeros((tree.n, NCOMP, NCELL))
+        dL1 = np.zeros((tree.n, 3, NCELL))
     _lib().oracle_m2l(_p(tree.desc), tree.n, _p(tree.cfg), _p(M), _p(com), _p(L),
-                      _p(dL1), _p(counts), tp, nt, int(n_threads))
+                      _p(dL1), _p(counts), tp, nt, int(n_threads), int(bool(compact)))
     return L, dL1, counts
 
 

@@ -230,14 +230,18 @@ cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *
     const ListRange &r = t->plan.leaves;
     const auto &c = t->cfg;
     if (r.count > 0) {
+        timing_begin(t, FMM_K_FORCES, s);
         forces_kernel<<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.lists + r.off, L64, dacc,
                                                         rho, phi, g, t->dev.partials, c.box_lo[0],
                                                         c.box_lo[1], c.box_lo[2], c.box_size);
+        timing_end(t, s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    timing_begin(t, FMM_K_REDUCE, s);
     reduce_kernel<<<unsigned(t->n_trees), 512, 0, s>>>(t->dev.tree_leaf_off, t->dev.tree_leaf_rows,
                                                        t->dev.partials, totals);
+    timing_end(t, s);
     return cudaGetLastError();
 }
 

@@ -76,6 +76,41 @@ int sm_count_of_current_device()
     return n > 0 ? n : 1;
 }
 
+static void timing_fold(const fmm_tree_s *t)
+{
+    TimerState &T = t->timer;
+    if (T.used == 0) return;
+    cudaEventSynchronize(T.ev[size_t(2 * T.used - 1)]);
+    for (int i = 0; i < T.used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, T.ev[size_t(2 * i)], T.ev[size_t(2 * i + 1)]) == cudaSuccess) {
+            T.ms[T.slot[size_t(i)]] += ms;
+            T.launches[T.slot[size_t(i)]]++;
+        }
+    }
+    T.used = 0;
+}
+
+void timing_begin(const fmm_tree_s *t, int slot, cudaStream_t s)
+{
+    if (!(t->cfg.flags & FMM_FLAG_TIMING)) return;
+    TimerState &T = t->timer;
+    if (2 * T.used + 2 > int(T.ev.size())) timing_fold(t);
+    cudaEventRecord(T.ev[size_t(2 * T.used)], s);
+    T.slot[size_t(T.used)] = slot;
+    T.open_slot = slot;
+}
+
+void timing_end(const fmm_tree_s *t, cudaStream_t s)
+{
+    if (!(t->cfg.flags & FMM_FLAG_TIMING)) return;
+    TimerState &T = t->timer;
+    if (T.open_slot < 0) return;
+    cudaEventRecord(T.ev[size_t(2 * T.used + 1)], s);
+    T.used++;
+    T.open_slot = -1;
+}
+
 }  // namespace fmm
 
 using namespace fmm;
@@ -256,14 +291,17 @@ static void slot_tables(const fmm_tree_s *t, std::vector<int64_t> &tab)
     }
 }
 
-// flop model: operation count of one interaction of each kind as the kernels
-// evaluate it (fused multiply-add = 2), excluding compensation.
-static const double kFlops[4] = {
-    /* mp<-mp   */ 376.0,
-    /* mp<-mono */ 376.0,
-    /* mono<-mono */ 8.0,
-    /* mono<-mp */ 240.0,
-};
+// Flop model: operations of one interaction of each kind as the kernels
+// evaluate it, counted from their source (fused multiply-add = 2, the
+// reciprocal square root = 1), compensation excluded:
+//   derivative tensors D0..D4 from R: 126; offset R: 3 (leaf source) or 6;
+//   multipole<-multipole: contraction of orders 0-3 (108) + correction
+//     sums S1 (60) and S2 (30)                                  -> 330
+//   multipole<-monopole: M0 D^(n) for 20 components (40) + S2   -> 199
+//   monopole<-monopole: tabulated weights, 4 FMAs               ->   8
+//   monopole<-multipole: orders 0-1 (76) + S1 (60)              -> 268
+// (Sec. 4.3 quotes 455 and 12 for the paper's own kernels.)
+static const double kFlops[4] = {330.0, 199.0, 8.0, 268.0};
 
 static void plan_work(fmm_tree_s *t)
 {
@@ -273,7 +311,7 @@ static void plan_work(fmm_tree_s *t)
     const int64_t n = t->n;
     std::vector<int64_t> cost(size_t(n), 0);
     std::vector<char> has_refined_nbr(size_t(n), 0);
-    for (int k = 0; k < 4; ++k) P.interactions[k] = 0;
+    for (int k = 0; k < 4; ++k) P.interactions[k] = P.kernel_interactions[k] = 0;
     for (int64_t i = 0; i < n; ++i) {
         const NodeInfo &x = t->info[size_t(i)];
         bool leaf = x.leaf_row >= 0;
@@ -289,6 +327,7 @@ static void plan_work(fmm_tree_s *t)
                 }
             if (leaf) P.interactions[2] += far + nearc;
             else P.interactions[0] += far;
+            P.kernel_interactions[3] += leaf ? far + nearc : far;
             cost[size_t(i)] = leaf ? (far + nearc) : far * 40;
             continue;
         }
@@ -311,6 +350,11 @@ static void plan_work(fmm_tree_s *t)
             }
         }
         for (int k = 0; k < 4; ++k) P.interactions[k] += c[k];
+        if (!leaf) P.kernel_interactions[0] += c[0] + c[1];
+        else {
+            P.kernel_interactions[1] += c[2];
+            P.kernel_interactions[2] += c[3];
+        }
         cost[size_t(i)] = leaf ? c[2] + 30 * c[3] : 45 * (c[0] + c[1]);
     }
     // node lists
@@ -376,6 +420,8 @@ static int upload(T **dst, const std::vector<T> &src)
 
 static void free_device(fmm_tree_s *t)
 {
+    for (cudaEvent_t e : t->timer.ev) cudaEventDestroy(e);
+    t->timer.ev.clear();
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64,
                     d.tree_leaf_off, d.tree_leaf_rows, d.mass, d.mp, d.counters, d.partials};
@@ -405,6 +451,13 @@ static int upload_tree(fmm_tree_s *t)
         (e = cudaMalloc(reinterpret_cast<void **>(&d.partials), part_b)) != cudaSuccess)
         return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
     d.workspace_bytes = mass_b + mp_b + part_b + 64 * sizeof(int32_t);
+    if (t->cfg.flags & FMM_FLAG_TIMING) {
+        const int records = 256;
+        t->timer.ev.resize(size_t(2 * records));
+        t->timer.slot.assign(size_t(records), 0);
+        for (auto &ev : t->timer.ev)
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
     return FMM_OK;
 }
 
@@ -534,6 +587,7 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     o->work_items[1] = P.work_mono.count;
     o->work_items[2] = P.work_mx.count;
     o->work_items[3] = P.roots.count;
+    for (int k = 0; k < 4; ++k) o->kernel_interactions[k] = P.kernel_interactions[k];
     o->reach = P.reach;
     int m2l = 1 /*pack*/ + (P.roots.count > 0) + (P.work_mp.count > 0) + (P.work_mono.count > 0) +
               (P.work_mx.count > 0);
@@ -543,6 +597,16 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     for (int lev = 1; lev <= t->max_level; ++lev) down += P.nodes_at[size_t(lev)].count > 0;
     o->launches_m2l = m2l;
     o->launches_step = up + m2l + down + 2;
+    if ((t->cfg.flags & FMM_FLAG_TIMING) && !t->host_only) {
+        o->timing = 1;
+        timing_fold(t);
+        for (int k = 0; k < FMM_K_COUNT; ++k) {
+            o->kernel_ms[k] = t->timer.ms[k];
+            o->kernel_launches[k] = t->timer.launches[k];
+            t->timer.ms[k] = 0.0;
+            t->timer.launches[k] = 0;
+        }
+    }
     return FMM_OK;
 }
 
@@ -559,11 +623,15 @@ int fmm_upward(fmm_tree_t t, const double *rho, double *M, double *com, fmm_stre
     if (rc) return rc;
     if (!rho || !M || !com) return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    timing_begin(t, FMM_K_P2M, s);
     cudaError_t e = launch_p2m(t, rho, M, s);
+    timing_end(t, s);
     if (e != cudaSuccess) return cuda_fail(e, "p2m launch");
     for (int lev = t->max_level - 1; lev >= 1; --lev) {
         if (t->plan.refined_at[size_t(lev)].count == 0) continue;
+        timing_begin(t, FMM_K_M2M, s);
         e = launch_m2m_level(t, lev, M, com, s);
+        timing_end(t, s);
         if (e != cudaSuccess) return cuda_fail(e, "m2m launch");
     }
     return FMM_OK;
@@ -578,7 +646,9 @@ int fmm_m2l(fmm_tree_t t, const double *M, const double *com, void *L, float *L_
     if (t->cfg.precision == FMM_MIXED && !L_comp)
         return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    timing_begin(t, FMM_K_PACK, s);
     cudaError_t e = launch_pack(t, M, com, s);
+    timing_end(t, s);
     if (e != cudaSuccess) return cuda_fail(e, "pack launch");
     int nl = 0;
     e = launch_m2l(t, L, L_comp, dL1, s, &nl);
@@ -597,7 +667,9 @@ int fmm_downward(fmm_tree_t t, const void *L, const float *L_comp, const double 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (int lev = 1; lev <= t->max_level; ++lev) {
         if (t->plan.nodes_at[size_t(lev)].count == 0) continue;
+        timing_begin(t, FMM_K_L2L, s);
         cudaError_t e = launch_l2l_level(t, lev, L, L_comp, dL1, com, L64, dL1_acc, s);
+        timing_end(t, s);
         if (e != cudaSuccess) return cuda_fail(e, "l2l launch");
     }
     return FMM_OK;

@@ -84,8 +84,21 @@ struct Plan {
     std::vector<ListRange> nodes_at;     // [level] all nodes (L2L)
     ListRange work_mp, work_mono, work_mx, roots;
     int64_t interactions[4] = {0, 0, 0, 0};
+    int64_t kernel_interactions[4] = {0, 0, 0, 0};  // multipole, monopole, mono<-multi, root
 };
 
+}  // namespace fmm
+
+namespace fmm {
+// event pairs around timed launches (FMM_FLAG_TIMING)
+struct TimerState {
+    std::vector<cudaEvent_t> ev;     // 2 per record
+    std::vector<int> slot;           // kernel slot per record
+    int used = 0;
+    int open_slot = -1;
+    double ms[16] = {0};
+    int64_t launches[16] = {0};
+};
 }  // namespace fmm
 
 struct fmm_tree_s {
@@ -102,6 +115,7 @@ struct fmm_tree_s {
     bool host_only = false;
     int device = -1;
     fmm::DeviceTables dev;
+    mutable fmm::TimerState timer;
 };
 
 namespace fmm {
@@ -122,5 +136,9 @@ cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *
                           cudaStream_t s);
 
 int sm_count_of_current_device();
+
+// FMM_FLAG_TIMING hooks around one kernel launch (no-ops otherwise)
+void timing_begin(const fmm_tree_s *t, int slot, cudaStream_t s);
+void timing_end(const fmm_tree_s *t, cudaStream_t s);
 
 }  // namespace fmm

@@ -632,7 +632,9 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         KParams R = P;
         R.list = d.lists + Pl.roots.off;
         R.n_items = int32_t(Pl.roots.count);
+        timing_begin(t, FMM_K_ROOT, s);
         root_kernel<T><<<unsigned(Pl.roots.count), kThreads, 0, s>>>(R);
+        timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -642,7 +644,9 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         K.n_items = int32_t(Pl.work_mp.count);
         K.counter = d.counters + Q_MP;
         int g = persistent_grid(mp_kernel<T>, wbytes, Pl.work_mp.count, sms);
+        timing_begin(t, FMM_K_MULTIPOLE, s);
         mp_kernel<T><<<g, kThreads, wbytes, s>>>(K);
+        timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -652,7 +656,9 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         K.n_items = int32_t(Pl.work_mono.count);
         K.counter = d.counters + Q_MONO;
         int g = persistent_grid(mono_kernel<T>, wbytes, Pl.work_mono.count, sms);
+        timing_begin(t, FMM_K_MONOPOLE, s);
         mono_kernel<T><<<g, kThreads, wbytes, s>>>(K);
+        timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -662,7 +668,9 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         K.n_items = int32_t(Pl.work_mx.count);
         K.counter = d.counters + Q_MX;
         int g = persistent_grid(mx_kernel<T>, 0, Pl.work_mx.count, sms);
+        timing_begin(t, FMM_K_MONO_MULTI, s);
         mx_kernel<T><<<g, kThreads, 0, s>>>(K);
+        timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -23,6 +23,9 @@ FMM_ERR_NOMEM = -5
 FMM_FP64 = 0
 FMM_MIXED = 1
 FMM_FLAG_HOST_ONLY = 1
+FMM_FLAG_TIMING = 2
+KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_multi", "l2l",
+                "forces", "reduce")
 
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
             "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_destroy_tree",
@@ -58,9 +61,11 @@ class FmmStats(ctypes.Structure):
     _fields_ = [("interactions", ctypes.c_int64 * 4), ("stencil_far", ctypes.c_int64),
                 ("stencil_near", ctypes.c_int64), ("stencil_union", ctypes.c_int64),
                 ("flops_per_interaction", ctypes.c_double * 4),
-                ("work_items", ctypes.c_int64 * 4), ("reach", ctypes.c_int32),
+                ("work_items", ctypes.c_int64 * 4), ("kernel_interactions", ctypes.c_int64 * 4),
+                ("reach", ctypes.c_int32),
                 ("launches_m2l", ctypes.c_int32), ("launches_step", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("kernel_ms", ctypes.c_double * 16),
+                ("kernel_launches", ctypes.c_int64 * 16)]
 
 
 _LOCK = threading.Lock()
@@ -150,15 +155,16 @@ class Tree:
 
 
 def fmm_build_tree(desc, theta, G=1.0, box_lo=(0.0, 0.0, 0.0), box_size=1.0,
-                   precision=FMM_FP64, max_level=20, host_only=False):
+                   precision=FMM_FP64, max_level=20, host_only=False, timing=False):
     lib = load()
     d = np.ascontiguousarray(desc, dtype=np.int32)
     if d.ndim != 2 or d.shape[1] != 14:
         raise ValueError("descriptor array must be (n, 14) int32")
     if isinstance(precision, str):
         precision = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
+    flags = (FMM_FLAG_HOST_ONLY if host_only else 0) | (FMM_FLAG_TIMING if timing else 0)
     cfg = FmmConfig(float(theta), float(G), (ctypes.c_double * 3)(*box_lo), float(box_size),
-                    int(precision), int(max_level), FMM_FLAG_HOST_ONLY if host_only else 0, 0)
+                    int(precision), int(max_level), flags, 0)
     h = ctypes.c_void_p()
     _check(lib.fmm_build_tree(d.ctypes.data_as(ctypes.c_void_p), len(d), ctypes.byref(cfg),
                               ctypes.byref(h)))
@@ -217,9 +223,9 @@ class Solver:
     """
 
     def __init__(self, desc, theta, precision="mixed", G=1.0, box_lo=(0.0, 0.0, 0.0),
-                 box_size=1.0, device="cuda"):
+                 box_size=1.0, device="cuda", timing=False):
         import torch
-        self.tree = fmm_build_tree(desc, theta, G, box_lo, box_size, precision)
+        self.tree = fmm_build_tree(desc, theta, G, box_lo, box_size, precision, timing=timing)
         s = self.tree.sizes
         n, nl, nt = s["n_nodes"], s["n_leaf"], s["n_trees"]
         self.mixed = s["precision"] == FMM_MIXED
@@ -259,6 +265,12 @@ class Solver:
         self.m2l(stream)
         self.downward(stream)
         self.forces(rho, stream)
+
+    def kernel_times(self):
+        """Per-kernel device ms since the last call (trees built with timing=True)."""
+        st = fmm_get_stats(self.tree)
+        return {k: (st["kernel_ms"][i], st["kernel_launches"][i])
+                for i, k in enumerate(KERNEL_SLOTS)}
 
     def capture(self):
         """Record step() on self.rho into a CUDA graph (call once, then replay)."""

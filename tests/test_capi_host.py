@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(B.FmmConfig) == 8 * 6 + 4 * 4
     assert ctypes.sizeof(B.FmmSizes) == 8 * 4 + 4 * 2 + 8 * 11
-    assert ctypes.sizeof(B.FmmStats) == 8 * 4 + 8 * 3 + 8 * 4 + 8 * 4 + 4 * 4
+    assert ctypes.sizeof(B.FmmStats) == 8 * 4 + 8 * 3 + 8 * 4 + 8 * 4 + 8 * 4 + 4 * 4 + 8 * 16 + 8 * 16
 
 
 def plan(desc, theta):
@@ -66,6 +66,7 @@ def test_planner_counts_match_oracle(case):
     M, com = O.upward(ot, rho)
     _, _, counts = O.m2l(ot, M, com)
     assert list(t.stats["interactions"]) == list(counts)
+    assert sum(t.stats["kernel_interactions"]) == sum(counts)
 
 
 def test_planner_stencil_sizes():

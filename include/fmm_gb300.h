@@ -229,7 +229,9 @@ int fmm_downward(fmm_tree_t tree, const void *L, const float *L_comp,
  *   g:      device double [n_leaf][3][512], written.
  *   totals: device double [n_trees][8], written: sum f (3), sum x cross f
  *           (3), sum |f|, sum |x cross f|, x measured from the box centre.
- *           Summation order is fixed, so results are deterministic.
+ *           The sums are FP64 in a fixed order (deterministic); the per-cell
+ *           magnitudes in the last two, which only normalise the first two,
+ *           are formed in float.
  */
 int fmm_forces(fmm_tree_t tree, const double *L64, const double *dL1_acc,
                const double *rho, double *phi, double *g, double *totals,

@@ -424,7 +424,8 @@ static void free_device(fmm_tree_s *t)
     t->timer.ev.clear();
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64,
-                    d.tree_leaf_off, d.tree_leaf_rows, d.mass, d.mp, d.counters, d.partials};
+                    d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.mass, d.mp, d.counters,
+                    d.partials};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceTables{};
@@ -438,7 +439,7 @@ static int upload_tree(fmm_tree_s *t)
         (rc = upload(&d.nbr, t->nbr)) || (rc = upload(&d.lists, t->lists)) ||
         (rc = upload(&d.stencil, t->stencil)) || (rc = upload(&d.coef32, t->coef32)) ||
         (rc = upload(&d.coef64, t->coef64)) || (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||
-        (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)))
+        (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)) || (rc = upload(&d.levels, t->levels)))
         return rc;
     size_t es = t->cfg.precision == FMM_MIXED ? sizeof(float) : sizeof(double);
     size_t mass_b = size_t(t->n) * NCELL * es;
@@ -533,6 +534,19 @@ int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config
     }
     build_stencils(t);
     plan_work(t);
+    // per-level geometry: h = box / (8 * 2^(l-1)) is exact up to the box edge
+    t->levels.assign(size_t(t->max_level + 1) * LEVEL_FIELDS, 0.0);
+    for (int lev = 1; lev <= t->max_level; ++lev) {
+        double *L = &t->levels[size_t(lev) * LEVEL_FIELDS];
+        const double h = cfg->box_size / (8.0 * std::ldexp(1.0, lev - 1));
+        L[LV_H] = h;
+        L[LV_IH] = 1.0 / h;
+        L[LV_H3] = h * h * h;
+        L[LV_S0] = cfg->G / h;
+        L[LV_S1] = L[LV_S0] / h;
+        L[LV_S2] = L[LV_S1] / h;
+        L[LV_S3] = L[LV_S2] / h;
+    }
     if (!t->host_only) {
         if (cudaGetDevice(&t->device) != cudaSuccess) {
             delete t;

@@ -31,6 +31,12 @@ constexpr int NCELL = 512;
 constexpr int NCOMP = 20;
 constexpr int NMP = 19;          // packed multipole fields per refined cell
 
+// per-level geometry table (device, [level][LEVEL_FIELDS] doubles), filled on
+// the host so that no kernel divides: h, 1/h, h^3, and the level-unit ->
+// physical scales G h^-(n+1) of orders n = 0..3
+constexpr int LEVEL_FIELDS = 8;
+enum { LV_H = 0, LV_IH, LV_H3, LV_S0, LV_S1, LV_S2, LV_S3 };
+
 // per-node table row (device and host)
 struct NodeInfo {
     int32_t level, ix, iy, iz;
@@ -56,6 +62,7 @@ struct DeviceTables {
     double *coef64 = nullptr;        // [8][ent_stride][4]
     int32_t *tree_leaf_off = nullptr;   // [n_trees + 1]
     int32_t *tree_leaf_rows = nullptr;  // [n_leaf]
+    double *levels = nullptr;        // [max_level + 1][LEVEL_FIELDS]
     // workspace
     void *mass = nullptr;            // [n][512] float or double
     void *mp = nullptr;              // [n_refined][19][512] float or double
@@ -111,6 +118,7 @@ struct fmm_tree_s {
     std::vector<float> coef32;
     std::vector<double> coef64;
     std::vector<int32_t> tree_leaf_off, tree_leaf_rows;
+    std::vector<double> levels;
     fmm::Plan plan;
     bool host_only = false;
     int device = -1;

@@ -66,11 +66,11 @@ struct KParams {
 // A2 = mult M2 / (2 h^2), A3 = mult M3 / (6 h^3) at mp[row][field][pi].
 template <typename T>
 __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ info,
+                                                   const double *__restrict__ levels,
                                                    const double *__restrict__ M,
                                                    const double *__restrict__ com,
                                                    T *__restrict__ mass, T *__restrict__ mp,
-                                                   double lo_x, double lo_y, double lo_z,
-                                                   double box_size)
+                                                   double lo_x, double lo_y, double lo_z)
 {
     const int node = blockIdx.x;
     const NodeInfo ni = info[node];
@@ -80,20 +80,19 @@ __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ 
     const double *Mn = M + size_t(node) * NCOMP * NCELL + c;
     mass[size_t(node) * NCELL + pi] = T(Mn[0]);
     if (ni.mp_row < 0) return;
-    const double h = box_size / (8.0 * double(1u << (ni.level - 1)));
-    const double ih = 1.0 / h;
+    const double h = levels[ni.level * LEVEL_FIELDS + LV_H];
+    const double ih = levels[ni.level * LEVEL_FIELDS + LV_IH];
     T *out = mp + size_t(ni.mp_row) * NMP * NCELL + pi;
     const double ctr[3] = {lo_x + (8.0 * ni.ix + x + 0.5) * h, lo_y + (8.0 * ni.iy + y + 0.5) * h,
                            lo_z + (8.0 * ni.iz + z + 0.5) * h};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         out[a * NCELL] = T((com[(size_t(node) * 3 + a) * NCELL + c] - ctr[a]) * ih);
-    const double ih2 = ih * ih, ih3 = ih2 * ih;
+    const double w2 = 0.5 * ih * ih, w3 = (1.0 / 6.0) * ih * ih * ih;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) out[(3 + q) * NCELL] = T(mult2(q) * Mn[(4 + q) * NCELL] * 0.5 * ih2);
+    for (int q = 0; q < 6; ++q) out[(3 + q) * NCELL] = T(mult2(q) * w2 * Mn[(4 + q) * NCELL]);
 #pragma unroll
-    for (int q = 0; q < 10; ++q)
-        out[(9 + q) * NCELL] = T(mult3(q) * Mn[(10 + q) * NCELL] * (1.0 / 6.0) * ih3);
+    for (int q = 0; q < 10; ++q) out[(9 + q) * NCELL] = T(mult3(q) * w3 * Mn[(10 + q) * NCELL]);
 }
 
 // ------------------------------------------------------------ common bits
@@ -262,7 +261,9 @@ __device__ __forceinline__ void source_cell(int ax, int ay, int az, int ox, int 
 
 // ------------------------------------------------------------ mp_kernel
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) mp_kernel(KParams P)
+// float: two CTAs per SM (128 registers; the (hi, lo) pairs, touched once per
+// chunk, are what the register budget squeezes)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) mp_kernel(KParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *W = reinterpret_cast<T *>(smem_raw);
@@ -510,61 +511,97 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
 
 // ---------------------------------------------------------- root_kernel
 // Level 1 holds one node per tree and every pair is a candidate: a refined
-// root evaluates its well-separated pairs, a leaf root all pairs.
+// root evaluates its well-separated pairs, a leaf root all pairs.  The
+// 512 x 511 pairs of one root are spread over 16 CTAs of 32 targets, each
+// target's 512 sources over 4 warps; the 4 partial sums are folded in a
+// fixed order (deterministic).
+constexpr int kRootSlices = 4;
+constexpr int kRootThreads = 32 * kRootSlices;
+constexpr int kRootGroups = NCELL / 32;
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) root_kernel(KParams P)
+__global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
 {
+    constexpr int NV = 20 + 3 + 15;                 // L, S1, S2
+    __shared__ T sh_hi[kRootSlices][NV][32];
+    __shared__ T sh_lo[kRootSlices][sizeof(T) == 4 ? 20 : 1][32];   // float only
     const int node = P.list[blockIdx.x];
     const NodeInfo ti = P.info[node];
     const bool leaf = ti.leaf_row >= 0;
     const T *mass = static_cast<const T *>(P.mass);
     const T *mpd = static_cast<const T *>(P.mp);
-    for (int half = 0; half < 2; ++half) {
-        const int cell = threadIdx.x + half * kThreads;
-        const int ax = cell & 7, ay = (cell >> 3) & 7, az = cell >> 6;
-        const int tpi = parity_index(ax, ay, az);
-        T dA[3] = {T(0), T(0), T(0)};
-        if (!leaf)
-            for (int a = 0; a < 3; ++a) dA[a] = mpd[(size_t(ti.mp_row) * NMP + a) * NCELL + tpi];
-        Acc<T, 20> L;
-        L.zero();
-        T S1[3] = {T(0), T(0), T(0)}, S2[15];
-        for (int q = 0; q < 15; ++q) S2[q] = T(0);
-        int done = 0;
-        for (int b = 0; b < NCELL; ++b) {
-            const int ox = (b & 7) - ax, oy = ((b >> 3) & 7) - ay, oz = (b >> 6) - az;
-            const double o2 = double(ox * ox + oy * oy + oz * oz);
-            const bool far = P.theta2 * o2 > 1.0;
-            if (b == cell || !(far || leaf)) continue;
-            const int pi = parity_index(b & 7, (b >> 3) & 7, b >> 6);
-            T m0, dB[3] = {T(0), T(0), T(0)}, A2[6], A3[10];
-            for (int q = 0; q < 6; ++q) A2[q] = T(0);
-            for (int q = 0; q < 10; ++q) A3[q] = T(0);
-            if (!leaf) load_source<T>(P, node, ti.mp_row, pi, m0, dB, A2, A3);
-            else m0 = mass[size_t(node) * NCELL + pi];
-            accumulate_mp<T, true>(dA[0] - dB[0] - T(ox), dA[1] - dB[1] - T(oy),
-                                   dA[2] - dB[2] - T(oz), m0, A2, A3, L, S1, S2);
-            if (++done == kChunk) {
-                L.flush();
-                done = 0;
-            }
+    const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const int cell = blockIdx.y * 32 + lane;
+    const int ax = cell & 7, ay = (cell >> 3) & 7, az = cell >> 6;
+    const int tpi = parity_index(ax, ay, az);
+    T dA[3] = {T(0), T(0), T(0)};
+    if (!leaf)
+        for (int a = 0; a < 3; ++a) dA[a] = mpd[(size_t(ti.mp_row) * NMP + a) * NCELL + tpi];
+    Acc<T, 20> L;
+    L.zero();
+    T S1[3] = {T(0), T(0), T(0)}, S2[15];
+    for (int q = 0; q < 15; ++q) S2[q] = T(0);
+    int done = 0;
+    const int b0 = slice * (NCELL / kRootSlices);
+    for (int b = b0; b < b0 + NCELL / kRootSlices; ++b) {
+        const int ox = (b & 7) - ax, oy = ((b >> 3) & 7) - ay, oz = (b >> 6) - az;
+        const double o2 = double(ox * ox + oy * oy + oz * oz);
+        const bool far = P.theta2 * o2 > 1.0;
+        if (b == cell || !(far || leaf)) continue;
+        const int pi = parity_index(b & 7, (b >> 3) & 7, b >> 6);
+        T m0, dB[3] = {T(0), T(0), T(0)}, A2[6], A3[10];
+        for (int q = 0; q < 6; ++q) A2[q] = T(0);
+        for (int q = 0; q < 10; ++q) A3[q] = T(0);
+        if (!leaf) load_source<T>(P, node, ti.mp_row, pi, m0, dB, A2, A3);
+        else m0 = mass[size_t(node) * NCELL + pi];
+        accumulate_mp<T, true>(dA[0] - dB[0] - T(ox), dA[1] - dB[1] - T(oy), dA[2] - dB[2] - T(oz),
+                               m0, A2, A3, L, S1, S2);
+        if (++done == kChunk) {
+            L.flush();
+            done = 0;
         }
-        L.flush();
-        const int nk = leaf ? 4 : 20;
-        for (int k = 0; k < nk; ++k) store_L<T>(P, node, k, cell, L.hi[k], L.lo[k]);
-        double corr[3] = {double(S1[0]), double(S1[1]), double(S1[2])};
-        if (!leaf) {
-            const double m0A = double(mass[size_t(node) * NCELL + tpi]);
-            for (int i = 0; i < 3; ++i) {
-                double s = 0.0;
-                for (int q = 0; q < 10; ++q)
-                    s += double(mpd[(size_t(ti.mp_row) * NMP + 9 + q) * NCELL + tpi]) *
-                         double(S2[r4_of(i, q)]);
-                corr[i] -= s / m0A;
-            }
-        }
-        for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = corr[i];
     }
+    L.flush();
+    for (int k = 0; k < 20; ++k) {
+        sh_hi[slice][k][lane] = L.hi[k];
+        if constexpr (sizeof(T) == 4) sh_lo[slice][k][lane] = L.lo[k];
+    }
+    for (int i = 0; i < 3; ++i) sh_hi[slice][20 + i][lane] = S1[i];
+    for (int q = 0; q < 15; ++q) sh_hi[slice][23 + q][lane] = S2[q];
+    __syncthreads();
+    if (slice != 0) return;
+    const int nk = leaf ? 4 : 20;
+    for (int k = 0; k < nk; ++k) {
+        T hi = T(0), lo = T(0);
+        for (int sl = 0; sl < kRootSlices; ++sl) {
+            if constexpr (sizeof(T) == 4) {
+                float sum, err;
+                two_sum(hi, sh_hi[sl][k][lane], sum, err);
+                hi = sum;
+                lo += err + sh_lo[sl][k][lane];
+            } else {
+                hi += sh_hi[sl][k][lane];
+            }
+        }
+        store_L<T>(P, node, k, cell, hi, lo);
+    }
+    double s1[3] = {0.0, 0.0, 0.0}, s2[15];
+    for (int q = 0; q < 15; ++q) s2[q] = 0.0;
+    for (int sl = 0; sl < kRootSlices; ++sl) {
+        for (int i = 0; i < 3; ++i) s1[i] += double(sh_hi[sl][20 + i][lane]);
+        for (int q = 0; q < 15; ++q) s2[q] += double(sh_hi[sl][23 + q][lane]);
+    }
+    double corr[3] = {s1[0], s1[1], s1[2]};
+    if (!leaf) {
+        const double m0A = double(mass[size_t(node) * NCELL + tpi]);
+        for (int i = 0; i < 3; ++i) {
+            double acc = 0.0;
+            for (int q = 0; q < 10; ++q)
+                acc += double(mpd[(size_t(ti.mp_row) * NMP + 9 + q) * NCELL + tpi]) * s2[r4_of(i, q)];
+            corr[i] -= acc / m0A;
+        }
+    }
+    for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = corr[i];
 }
 
 // ---------------------------------------------------------- launching
@@ -633,7 +670,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         R.list = d.lists + Pl.roots.off;
         R.n_items = int32_t(Pl.roots.count);
         timing_begin(t, FMM_K_ROOT, s);
-        root_kernel<T><<<unsigned(Pl.roots.count), kThreads, 0, s>>>(R);
+        root_kernel<T><<<dim3(unsigned(Pl.roots.count), kRootGroups), kRootThreads, 0, s>>>(R);
         timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -685,12 +722,12 @@ cudaError_t launch_pack(const fmm_tree_s *t, const double *M, const double *com,
     const auto &c = t->cfg;
     if (c.precision == FMM_MIXED)
         pack_kernel<float><<<unsigned(t->n), 512, 0, s>>>(
-            t->dev.info, M, com, static_cast<float *>(t->dev.mass), static_cast<float *>(t->dev.mp),
-            c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
+            t->dev.info, t->dev.levels, M, com, static_cast<float *>(t->dev.mass),
+            static_cast<float *>(t->dev.mp), c.box_lo[0], c.box_lo[1], c.box_lo[2]);
     else
         pack_kernel<double><<<unsigned(t->n), 512, 0, s>>>(
-            t->dev.info, M, com, static_cast<double *>(t->dev.mass), static_cast<double *>(t->dev.mp),
-            c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
+            t->dev.info, t->dev.levels, M, com, static_cast<double *>(t->dev.mass),
+            static_cast<double *>(t->dev.mp), c.box_lo[0], c.box_lo[1], c.box_lo[2]);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,18 @@ __host__ __device__ constexpr int r2_of(int i, int j)
 }
 // rank-3 component (i, j, k)
 __host__ __device__ constexpr int r3_ijk(int i, int j, int k) { return r3_of(i, r2_of(j, k)); }
+// the index pair / triple of a rank-2 / rank-3 component
+__host__ __device__ constexpr int i2_at(int q, int which)
+{
+    constexpr int t[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    return t[q][which];
+}
+__host__ __device__ constexpr int i3_at(int q, int which)
+{
+    constexpr int t[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                              {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+    return t[q][which];
+}
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }

@@ -1,8 +1,14 @@
 // Upward pass (Sec. 4.3, first step): cell masses from the leaf densities,
 // then, level by level from the deepest, each refined cell's mass, centre of
-// mass and central moments from its eight child cells.  FP64 throughout.
-// HBM-bound: every child value is read once and every parent value written
-// once.
+// mass and central moments from its eight child cells, in FP64.
+//
+// GB300's FP64 pipe runs at a small fraction of its FP32 rate, so the kernels
+// keep FP64 operation counts low: cell widths come from a per-level table
+// (no divisions), and when the eight children are leaf cells -- the bulk of
+// the work, at the finest refined level -- their offsets from the parent
+// cell centre are exactly (+-h/2, +-h/2, +-h/2), so the raw moments about
+// that centre are signed sums of the eight masses (a 3-D Hadamard transform),
+// shifted to the centre of mass afterwards.
 #include "fmm_internal.h"
 #include "fmm_tensor.cuh"
 
@@ -10,24 +16,38 @@ namespace fmm {
 
 namespace {
 
-__device__ __forceinline__ double cell_width(double box_size, int level)
-{
-    return box_size / (8.0 * double(1u << (level - 1)));
-}
-
 // P2M: leaf cells hold m = rho h^3 at their centre (point-mass reading of a
 // locally homogeneous density).  One thread per cell, cells x-fastest.
 __global__ void __launch_bounds__(512) p2m_kernel(const NodeInfo *__restrict__ info,
                                                   const int32_t *__restrict__ leaves,
+                                                  const double *__restrict__ levels,
                                                   const double *__restrict__ rho,
-                                                  double *__restrict__ M, double box_size)
+                                                  double *__restrict__ M)
 {
     const int node = leaves[blockIdx.x];
     const NodeInfo ni = info[node];
-    const double h = cell_width(box_size, ni.level);
-    const double h3 = h * h * h;
+    const double h3 = levels[ni.level * LEVEL_FIELDS + LV_H3];
     const int c = threadIdx.x;
     M[(size_t(node) * NCOMP) * NCELL + c] = rho[size_t(ni.leaf_row) * NCELL + c] * h3;
+}
+
+// Central moments about X = ref + d from raw moments S2, S3 about ref:
+//   M2_ij = S2_ij - M0 d_i d_j,
+//   M3_ijk = S3_ijk - (S2_ij d_k + S2_ik d_j + S2_jk d_i) + 2 M0 d_i d_j d_k.
+__device__ __forceinline__ void central_from_raw(double m0, const double d[3], const double S2[6],
+                                                 const double S3[10], double M2[6], double M3[10])
+{
+    constexpr int I2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    constexpr int I3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                               {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) M2[q] = S2[q] - m0 * d[I2[q][0]] * d[I2[q][1]];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        const int a = I3[q][0], b = I3[q][1], c = I3[q][2];
+        M3[q] = S3[q] - (S2[r2_of(a, b)] * d[c] + S2[r2_of(a, c)] * d[b] + S2[r2_of(b, c)] * d[a]) +
+                2.0 * m0 * d[a] * d[b] * d[c];
+    }
 }
 
 // M2M: parent cell (x,y,z) of a refined node takes the 2x2x2 child cells of
@@ -35,13 +55,12 @@ __global__ void __launch_bounds__(512) p2m_kernel(const NodeInfo *__restrict__ i
 //   M0 = sum m_c,  X = sum m_c X_c / M0,  s_c = X_c - X,
 //   M2_ij  = sum (M2c_ij + m_c s_i s_j),
 //   M3_ijk = sum (M3c_ijk + M2c_ij s_k + M2c_ik s_j + M2c_jk s_i + m_c s_i s_j s_k).
-// Leaf child cells are point masses at their centre (no M2, M3 reads).
 __global__ void __launch_bounds__(512) m2m_kernel(const NodeInfo *__restrict__ info,
                                                   const int32_t *__restrict__ children,
                                                   const int32_t *__restrict__ nodes,
+                                                  const double *__restrict__ levels,
                                                   double *__restrict__ M, double *__restrict__ com,
-                                                  double lo_x, double lo_y, double lo_z,
-                                                  double box_size)
+                                                  double lo_x, double lo_y, double lo_z)
 {
     const int node = nodes[blockIdx.x];
     const NodeInfo ni = info[node];
@@ -49,61 +68,83 @@ __global__ void __launch_bounds__(512) m2m_kernel(const NodeInfo *__restrict__ i
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
     const int k = (x >> 2) + 2 * (y >> 2) + 4 * (z >> 2);
     const int ch = children[node * 8 + k];
-    const NodeInfo ci = info[ch];
-    const bool child_leaf = ci.leaf_row >= 0;
-    const double hc = cell_width(box_size, ni.level + 1);
-    const double hp = 2.0 * hc;
-    // reference point: the parent cell centre (keeps the sums well scaled)
+    const bool child_leaf = info[ch].leaf_row >= 0;
+    const double hp = levels[ni.level * LEVEL_FIELDS + LV_H];
+    const double q = 0.25 * hp;                 // half a child cell width
     const double ref[3] = {lo_x + (8.0 * ni.ix + x + 0.5) * hp, lo_y + (8.0 * ni.iy + y + 0.5) * hp,
                            lo_z + (8.0 * ni.iz + z + 0.5) * hp};
-    double m[8], X[8][3];
-    double m0 = 0.0, mx[3] = {0.0, 0.0, 0.0};
+    const size_t cbase = size_t(ch) * NCOMP * NCELL;
+    const int c0 = 2 * (x & 3) + 16 * (y & 3) + 128 * (z & 3);   // child cell of j = 0
+    double m0, d[3], M2[6], M3[10];
+    if (child_leaf) {
+        // child j sits at ref + q (e_x, e_y, e_z), e = +-1 from the bits of j
+        double m[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int cx = 2 * (x & 3) + (j & 1), cy = 2 * (y & 3) + ((j >> 1) & 1),
-                  cz = 2 * (z & 3) + (j >> 2);
-        const int cc = cx + 8 * cy + 64 * cz;
-        m[j] = M[(size_t(ch) * NCOMP) * NCELL + cc];
-        if (child_leaf) {
-            X[j][0] = lo_x + (8.0 * ci.ix + cx + 0.5) * hc;
-            X[j][1] = lo_y + (8.0 * ci.iy + cy + 0.5) * hc;
-            X[j][2] = lo_z + (8.0 * ci.iz + cz + 0.5) * hc;
-        } else {
+        for (int j = 0; j < 8; ++j)
+            m[j] = M[cbase + c0 + (j & 1) + 8 * ((j >> 1) & 1) + 64 * (j >> 2)];
+        // Hadamard transform over the three sign bits
+        double a[8];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) X[j][a] = com[(size_t(ch) * 3 + a) * NCELL + cc];
+        for (int j = 0; j < 8; j += 2) { a[j] = m[j] + m[j + 1]; a[j + 1] = m[j + 1] - m[j]; }
+        double b[8];
+#pragma unroll
+        for (int j = 0; j < 8; j += 4)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) { b[j + i] = a[j + i] + a[j + i + 2]; b[j + i + 2] = a[j + i + 2] - a[j + i]; }
+        double e[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { e[i] = b[i] + b[i + 4]; e[i + 4] = b[i + 4] - b[i]; }
+        // e[bits] = sum_j m_j prod_{axis in bits} e_axis(j): 0 -> M0, 1 -> Ex,
+        // 2 -> Ey, 3 -> Exy, 4 -> Ez, 5 -> Exz, 6 -> Eyz, 7 -> Exyz
+        m0 = e[0];
+        const double im0 = 1.0 / m0;
+        d[0] = q * e[1] * im0;
+        d[1] = q * e[2] * im0;
+        d[2] = q * e[4] * im0;
+        const double q2 = q * q, q3 = q2 * q;
+        const double S2[6] = {q2 * m0, q2 * e[3], q2 * e[5], q2 * m0, q2 * e[6], q2 * m0};
+        const double S3[10] = {q3 * e[1], q3 * e[2], q3 * e[4], q3 * e[1], q3 * e[7],
+                               q3 * e[1], q3 * e[2], q3 * e[4], q3 * e[2], q3 * e[4]};
+        central_from_raw(m0, d, S2, S3, M2, M3);
+    } else {
+        double mj[8], X[8][3];
+        m0 = 0.0;
+        double mr[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int cc = c0 + (j & 1) + 8 * ((j >> 1) & 1) + 64 * (j >> 2);
+            mj[j] = M[cbase + cc];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) X[j][t] = com[(size_t(ch) * 3 + t) * NCELL + cc] - ref[t];
+            m0 += mj[j];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) mr[t] += mj[j] * X[j][t];
         }
-        m0 += m[j];
+        const double im0 = 1.0 / m0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) mx[a] += m[j] * (X[j][a] - ref[a]);
-    }
-    double Xp[3];
+        for (int t = 0; t < 3; ++t) d[t] = mr[t] * im0;
+        constexpr int I2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+        constexpr int I3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                                   {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Xp[a] = ref[a] + mx[a] / m0;
-    double M2[6] = {0, 0, 0, 0, 0, 0};
-    double M3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    constexpr int I2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-    constexpr int I3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
-                               {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+        for (int t = 0; t < 6; ++t) M2[t] = 0.0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int cx = 2 * (x & 3) + (j & 1), cy = 2 * (y & 3) + ((j >> 1) & 1),
-                  cz = 2 * (z & 3) + (j >> 2);
-        const int cc = cx + 8 * cy + 64 * cz;
-        const double s[3] = {X[j][0] - Xp[0], X[j][1] - Xp[1], X[j][2] - Xp[2]};
-        double c2[6] = {0, 0, 0, 0, 0, 0};
-        if (!child_leaf) {
+        for (int t = 0; t < 10; ++t) M3[t] = 0.0;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) c2[q] = M[(size_t(ch) * NCOMP + 4 + q) * NCELL + cc];
+        for (int j = 0; j < 8; ++j) {
+            const int cc = c0 + (j & 1) + 8 * ((j >> 1) & 1) + 64 * (j >> 2);
+            const double s[3] = {X[j][0] - d[0], X[j][1] - d[1], X[j][2] - d[2]};
+            double c2[6];
 #pragma unroll
-            for (int q = 0; q < 10; ++q) M3[q] += M[(size_t(ch) * NCOMP + 10 + q) * NCELL + cc];
-        }
+            for (int t = 0; t < 6; ++t) c2[t] = M[cbase + (4 + t) * NCELL + cc];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) M2[q] += c2[q] + m[j] * s[I2[q][0]] * s[I2[q][1]];
+            for (int t = 0; t < 6; ++t) M2[t] += c2[t] + mj[j] * s[I2[t][0]] * s[I2[t][1]];
 #pragma unroll
-        for (int q = 0; q < 10; ++q) {
-            const int a = I3[q][0], b = I3[q][1], d = I3[q][2];
-            M3[q] += c2[r2_of(a, b)] * s[d] + c2[r2_of(a, d)] * s[b] + c2[r2_of(b, d)] * s[a] +
-                     m[j] * s[a] * s[b] * s[d];
+            for (int t = 0; t < 10; ++t) {
+                const int a = I3[t][0], b = I3[t][1], e = I3[t][2];
+                M3[t] += M[cbase + (10 + t) * NCELL + cc] + c2[r2_of(a, b)] * s[e] +
+                         c2[r2_of(a, e)] * s[b] + c2[r2_of(b, e)] * s[a] + mj[j] * s[a] * s[b] * s[e];
+            }
         }
     }
     double *out = M + size_t(node) * NCOMP * NCELL + c;
@@ -112,11 +153,11 @@ __global__ void __launch_bounds__(512) m2m_kernel(const NodeInfo *__restrict__ i
     out[2 * NCELL] = 0.0;
     out[3 * NCELL] = 0.0;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) out[(4 + q) * NCELL] = M2[q];
+    for (int t = 0; t < 6; ++t) out[(4 + t) * NCELL] = M2[t];
 #pragma unroll
-    for (int q = 0; q < 10; ++q) out[(10 + q) * NCELL] = M3[q];
+    for (int t = 0; t < 10; ++t) out[(10 + t) * NCELL] = M3[t];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) com[(size_t(node) * 3 + a) * NCELL + c] = Xp[a];
+    for (int t = 0; t < 3; ++t) com[(size_t(node) * 3 + t) * NCELL + c] = ref[t] + d[t];
 }
 
 }  // namespace
@@ -125,8 +166,8 @@ cudaError_t launch_p2m(const fmm_tree_s *t, const double *rho, double *M, cudaSt
 {
     const ListRange &r = t->plan.leaves;
     if (r.count == 0) return cudaSuccess;
-    p2m_kernel<<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.lists + r.off, rho, M,
-                                                 t->cfg.box_size);
+    p2m_kernel<<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.lists + r.off, t->dev.levels,
+                                                 rho, M);
     return cudaGetLastError();
 }
 
@@ -136,8 +177,8 @@ cudaError_t launch_m2m_level(const fmm_tree_s *t, int level, double *M, double *
     const ListRange &r = t->plan.refined_at[size_t(level)];
     if (r.count == 0) return cudaSuccess;
     m2m_kernel<<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.children, t->dev.lists + r.off,
-                                                 M, com, t->cfg.box_lo[0], t->cfg.box_lo[1],
-                                                 t->cfg.box_lo[2], t->cfg.box_size);
+                                                 t->dev.levels, M, com, t->cfg.box_lo[0],
+                                                 t->cfg.box_lo[1], t->cfg.box_lo[2]);
     return cudaGetLastError();
 }
 

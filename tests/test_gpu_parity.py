@@ -205,7 +205,9 @@ def test_downward_and_forces_parity(name):
     assert rel_err(host(s.phi), ref["phi"]) <= FP64_TOL
     assert rel_err(host(s.g), ref["g"]) <= FP64_TOL
     tot, rt = host(s.totals), ref["totals"]
-    np.testing.assert_allclose(tot[:, 6:8], rt[:, 6:8], rtol=1e-13)
+    # sum |f| and sum |x cross f| only normalise the net sums: the library
+    # forms the per-cell magnitudes in float (the sums themselves are FP64)
+    np.testing.assert_allclose(tot[:, 6:8], rt[:, 6:8], rtol=1e-6)
     assert np.all(np.abs(tot[:, 0:6] - rt[:, 0:6]) <= 1e-13 * rt[:, 6:7].max())
     s.close()
 

@@ -304,6 +304,9 @@ def run_ours(args):
     stats, sizes = solver.tree.stats, solver.tree.sizes
     interactions = int(sum(stats["interactions"]))
     solver.rho.copy_(rho_host.cuda())
+    from paper_1908_03121_gb300 import autotune
+    solver.step()
+    best, tune_results = autotune.tune(solver)
     solver.capture()
     pci = None
     try:
@@ -350,7 +353,8 @@ def run_ours(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
               "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
               "config": dict(workload_config(args.workload, c, stats, sizes, args.precision),
-                             parallelism=f"replicas x{world}" if world > 1 else "single GPU")}
+                             parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                             tuning=best)}
     result["e2e"] = e2e
     result["gpu_launches"] = int(stats["launches_step"]) * args.steps
     result["clocks"] = clk
@@ -358,6 +362,7 @@ def run_ours(args):
     if rank == 0:
         # per-kernel device times, measured live with events on the launch stream
         tsolver = F.Solver(c["desc"], c["theta"], precision=args.precision, timing=True)
+        F.fmm_set_tuning(tsolver.tree, **best)
         tsolver.rho.copy_(solver.rho)
         for _ in range(2):
             flush()
@@ -405,6 +410,8 @@ def run_ours(args):
         if args.precision == "mixed" and args.fp64_steps > 0:
             s64 = F.Solver(c["desc"], c["theta"], precision="fp64")
             s64.rho.copy_(solver.rho)
+            s64.step()
+            autotune.tune(s64)
             s64.capture()
             ms64, _, _ = time_graph(torch, s64, args.fp64_steps, 1, flush, stream)
             g64 = s64.g

@@ -237,6 +237,21 @@ int fmm_forces(fmm_tree_t tree, const double *L64, const double *dL1_acc,
                const double *rho, double *phi, double *g, double *totals,
                fmm_stream_t stream);
 
+/* Launch-shape knobs of the same-level kernels, for the autotuner
+ * (paper_1908_03121_gb300/autotune.py); zeros select the defaults.  No
+ * counterpart in the paper: its kernels had one fixed shape (Sec. 5.1). */
+typedef struct {
+    int32_t mono_subgrids;           /* sub-grids per pass of the monopole kernel:
+                                        1, 2 or 4 (float) / 1, 2 (double) */
+    int32_t ctas_per_sm;             /* cap on persistent CTAs per SM (0 = occupancy) */
+    int32_t reserved[6];
+} fmm_tuning;
+
+/* Set / read the tree's tuning (host, immediate; affects later launches).
+ * Errors: FMM_ERR_INVALID_ARG for NULL or out-of-range values. */
+int fmm_set_tuning(fmm_tree_t tree, const fmm_tuning *tuning);
+int fmm_get_tuning(fmm_tree_t tree, fmm_tuning *tuning);
+
 /* Release the tree's host and device memory (synchronises the device first). */
 void fmm_destroy_tree(fmm_tree_t tree);
 

@@ -1,0 +1,59 @@
+"""Autotuner for the same-level kernels' launch shapes.
+
+Times ``fmm_m2l`` on the caller's tree for every candidate of
+``fmm_tuning`` (sub-grids per pass of the monopole kernel, persistent CTAs per
+SM) with CUDA events on the current stream, keeps the fastest and leaves it
+set on the tree.  Each candidate is run ``reps`` times after one warm-up; the
+median decides.  Results are cached per tree size and precision for the
+process.
+"""
+
+import itertools
+
+import numpy as np
+
+from . import fmm as B
+
+MONO_SUBGRIDS = (1, 2, 4)
+CTAS_PER_SM = (0, 1, 2)
+_CACHE = {}
+
+
+def _key(solver):
+    s = solver.tree.sizes
+    return (s["n_nodes"], s["n_leaf"], s["n_refined"], s["precision"])
+
+
+def tune(solver, reps=5, verbose=False):
+    """Pick and set the fastest tuning for ``solver`` (an ``fmm.Solver``)."""
+    import torch
+    key = _key(solver)
+    if key in _CACHE:
+        B.fmm_set_tuning(solver.tree, **_CACHE[key][0])
+        return _CACHE[key]
+    mixed = solver.mixed
+    candidates = [dict(mono_subgrids=nb, ctas_per_sm=cap)
+                  for nb, cap in itertools.product(MONO_SUBGRIDS, CTAS_PER_SM)
+                  if mixed or nb != 4]
+    stream = torch.cuda.current_stream()
+    results = []
+    for cand in candidates:
+        B.fmm_set_tuning(solver.tree, **cand)
+        solver.m2l()
+        times = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solver.m2l()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        results.append((float(np.median(times)), cand))
+        if verbose:
+            print(f"  {cand}: {np.median(times):.3f} ms")
+    results.sort(key=lambda r: r[0])
+    best = results[0][1]
+    B.fmm_set_tuning(solver.tree, **best)
+    _CACHE[key] = (best, results)
+    return _CACHE[key]

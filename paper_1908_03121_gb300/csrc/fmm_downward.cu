@@ -59,12 +59,14 @@ __device__ __forceinline__ void shift_increments(const T P[20], const T d[3], T 
     }
 }
 
-template <bool MIXED, int NMAX>
-__device__ __forceinline__ void l2l_cell(const NodeInfo &ni, int node, int c,
-                                         const double *__restrict__ lv, const void *__restrict__ Lv,
-                                         const float *__restrict__ Lc, const double *dL1,
-                                         const double *__restrict__ com, double *__restrict__ L64,
-                                         double *dacc, double lo_x, double lo_y, double lo_z)
+// FP64 path: the whole re-centring in double
+template <int NMAX>
+__device__ __forceinline__ void l2l_cell_fp64(const NodeInfo &ni, int node, int c,
+                                              const double *__restrict__ lv,
+                                              const double *__restrict__ Lv, const double *dL1,
+                                              const double *__restrict__ com,
+                                              double *__restrict__ L64, double *dacc, double lo_x,
+                                              double lo_y, double lo_z)
 {
     constexpr int NK = NMAX == 1 ? 4 : 20;
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
@@ -72,13 +74,8 @@ __device__ __forceinline__ void l2l_cell(const NodeInfo &ni, int node, int c,
     const double sc[4] = {L[LV_S0], L[LV_S1], L[LV_S2], L[LV_S3]};
     double out[20];
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        const size_t idx = (size_t(node) * NCOMP + k) * NCELL + c;
-        double v;
-        if (MIXED) v = double(static_cast<const float *>(Lv)[idx]) + double(Lc[idx]);
-        else v = static_cast<const double *>(Lv)[idx];
-        out[k] = v * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
-    }
+    for (int k = 0; k < NK; ++k)
+        out[k] = Lv[(size_t(node) * NCOMP + k) * NCELL + c] * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
     double corr[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc[1];
@@ -101,21 +98,10 @@ __device__ __forceinline__ void l2l_cell(const NodeInfo &ni, int node, int c,
         double P[20];
 #pragma unroll
         for (int k = 0; k < 20; ++k) P[k] = L64[(size_t(ni.parent) * NCOMP + k) * NCELL + pc];
-        if (MIXED) {
-            float Pf[20], df[3], inc[20];
+        double inc[20];
+        shift_increments<double, NMAX>(P, d, inc);
 #pragma unroll
-            for (int k = 0; k < 20; ++k) Pf[k] = float(P[k]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) df[a] = float(d[a]);
-            shift_increments<float, NMAX>(Pf, df, inc);
-#pragma unroll
-            for (int k = 0; k < NK; ++k) out[k] += P[k] + double(inc[k]);
-        } else {
-            double inc[20];
-            shift_increments<double, NMAX>(P, d, inc);
-#pragma unroll
-            for (int k = 0; k < NK; ++k) out[k] += P[k] + inc[k];
-        }
+        for (int k = 0; k < NK; ++k) out[k] += P[k] + inc[k];
 #pragma unroll
         for (int a = 0; a < 3; ++a) corr[a] += dacc[(size_t(ni.parent) * 3 + a) * NCELL + pc];
     }
@@ -123,6 +109,92 @@ __device__ __forceinline__ void l2l_cell(const NodeInfo &ni, int node, int c,
     for (int k = 0; k < NK; ++k) L64[(size_t(node) * NCOMP + k) * NCELL + c] = out[k];
 #pragma unroll
     for (int a = 0; a < 3; ++a) dacc[(size_t(node) * 3 + a) * NCELL + c] = corr[a];
+}
+
+// Mixed path.  The parent level left a float copy of each refined cell's
+// final expansion and of its centre-of-mass offset from the cell centre in
+// `down`, so the shift d = (child centre - parent centre) + child offset -
+// parent offset (the first term is exactly +-h/2 per axis) and the
+// increments are formed in float; they are folded into the cell's own
+// (hi, lo) level-unit pair by TwoSum, and the one FP64 operation per
+// component is the final accumulation L64 = (hi + lo) G h^-(n+1) + L64_parent.
+template <int NMAX>
+__device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int c,
+                                               const NodeInfo *__restrict__ info,
+                                               const double *__restrict__ lv,
+                                               const float *__restrict__ Lhi,
+                                               const float *__restrict__ Llo, const double *dL1,
+                                               const double *__restrict__ com,
+                                               double *__restrict__ L64, double *dacc,
+                                               float *__restrict__ down, double lo_x,
+                                               double lo_y, double lo_z)
+{
+    constexpr int NK = NMAX == 1 ? 4 : 20;
+    const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+    const double *L = lv + ni.level * LEVEL_FIELDS;
+    const double sc[4] = {L[LV_S0], L[LV_S1], L[LV_S2], L[LV_S3]};
+    float hi[20], lo[20];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const size_t idx = (size_t(node) * NCOMP + k) * NCELL + c;
+        hi[k] = Lhi[idx];
+        lo[k] = Llo[idx];
+    }
+    float offc[3] = {0.f, 0.f, 0.f};          // own centre-of-mass offset
+    if (NMAX == 3) {
+        const double h = L[LV_H];
+        offc[0] = float(com[(size_t(node) * 3 + 0) * NCELL + c] - (lo_x + (8.0 * ni.ix + x + 0.5) * h));
+        offc[1] = float(com[(size_t(node) * 3 + 1) * NCELL + c] - (lo_y + (8.0 * ni.iy + y + 0.5) * h));
+        offc[2] = float(com[(size_t(node) * 3 + 2) * NCELL + c] - (lo_z + (8.0 * ni.iz + z + 0.5) * h));
+    }
+    double out[20];
+    double corr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc[1];
+    if (ni.parent >= 0) {
+        const int pc = (4 * (ni.ix & 1) + (x >> 1)) + 8 * (4 * (ni.iy & 1) + (y >> 1)) +
+                       64 * (4 * (ni.iz & 1) + (z >> 1));
+        const int prow = info[ni.parent].mp_row;
+        const float *pd = down + size_t(prow) * 23 * NCELL + pc;
+        float Pf[20];
+#pragma unroll
+        for (int k = 0; k < 20; ++k) Pf[k] = pd[k * NCELL];
+        const float hc = float(L[LV_H]);
+        const float d[3] = {(float(x & 1) - 0.5f) * hc + offc[0] - pd[20 * NCELL],
+                            (float(y & 1) - 0.5f) * hc + offc[1] - pd[21 * NCELL],
+                            (float(z & 1) - 0.5f) * hc + offc[2] - pd[22 * NCELL]};
+        float inc[20];
+        shift_increments<float, NMAX>(Pf, d, inc);
+        const float rs[4] = {float(L[LV_R0]), float(L[LV_R1]), float(L[LV_R2]), float(L[LV_R3])};
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            float s, e;
+            two_sum(hi[k], inc[k] * rs[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3], s, e);
+            hi[k] = s;
+            lo[k] += e;
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            out[k] = fma(double(hi[k]) + double(lo[k]), sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3],
+                         L64[(size_t(ni.parent) * NCOMP + k) * NCELL + pc]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) corr[a] += dacc[(size_t(ni.parent) * 3 + a) * NCELL + pc];
+    } else {
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            out[k] = (double(hi[k]) + double(lo[k])) * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) L64[(size_t(node) * NCOMP + k) * NCELL + c] = out[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dacc[(size_t(node) * 3 + a) * NCELL + c] = corr[a];
+    if (NMAX == 3) {
+        float *od = down + size_t(ni.mp_row) * 23 * NCELL + c;
+#pragma unroll
+        for (int k = 0; k < 20; ++k) od[k * NCELL] = float(out[k]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) od[(20 + a) * NCELL] = offc[a];
+    }
 }
 
 template <bool MIXED>
@@ -134,16 +206,27 @@ __global__ void __launch_bounds__(512) l2l_kernel(const NodeInfo *__restrict__ i
                                                   const double *dL1,  // may alias dacc
                                                   const double *__restrict__ com,
                                                   double *__restrict__ L64, double *dacc,
-                                                  double lo_x, double lo_y, double lo_z)
+                                                  float *__restrict__ down, double lo_x,
+                                                  double lo_y, double lo_z)
 {
     const int node = nodes[blockIdx.x];
     const NodeInfo ni = info[node];
-    if (ni.leaf_row >= 0)
-        l2l_cell<MIXED, 1>(ni, node, threadIdx.x, levels, Lv, Lc, dL1, com, L64, dacc, lo_x, lo_y,
-                           lo_z);
-    else
-        l2l_cell<MIXED, 3>(ni, node, threadIdx.x, levels, Lv, Lc, dL1, com, L64, dacc, lo_x, lo_y,
-                           lo_z);
+    const int c = threadIdx.x;
+    if (MIXED) {
+        const float *Lhi = static_cast<const float *>(Lv);
+        if (ni.leaf_row >= 0)
+            l2l_cell_mixed<1>(ni, node, c, info, levels, Lhi, Lc, dL1, com, L64, dacc, down, lo_x,
+                              lo_y, lo_z);
+        else
+            l2l_cell_mixed<3>(ni, node, c, info, levels, Lhi, Lc, dL1, com, L64, dacc, down, lo_x,
+                              lo_y, lo_z);
+    } else {
+        const double *L = static_cast<const double *>(Lv);
+        if (ni.leaf_row >= 0)
+            l2l_cell_fp64<1>(ni, node, c, levels, L, dL1, com, L64, dacc, lo_x, lo_y, lo_z);
+        else
+            l2l_cell_fp64<3>(ni, node, c, levels, L, dL1, com, L64, dacc, lo_x, lo_y, lo_z);
+    }
 }
 
 // block sum of 8 doubles, fixed order; result in thread 0
@@ -253,11 +336,12 @@ cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L, cons
     if (c.precision == FMM_MIXED)
         l2l_kernel<true><<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.lists + r.off,
                                                            t->dev.levels, L, Lc, dL1, com, L64, dacc,
-                                                           c.box_lo[0], c.box_lo[1], c.box_lo[2]);
+                                                           t->dev.down, c.box_lo[0], c.box_lo[1],
+                                                           c.box_lo[2]);
     else
         l2l_kernel<false><<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.lists + r.off,
                                                             t->dev.levels, L, Lc, dL1, com, L64,
-                                                            dacc, c.box_lo[0], c.box_lo[1],
+                                                            dacc, nullptr, c.box_lo[0], c.box_lo[1],
                                                             c.box_lo[2]);
     return cudaGetLastError();
 }

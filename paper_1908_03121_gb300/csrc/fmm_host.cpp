@@ -260,6 +260,24 @@ static void build_stencils(fmm_tree_s *t)
         }
     P.stencil_union = 0;
     for (char c : in_union) P.stencil_union += c;
+    // slots reachable by each entry from each half (z-cells 0-3 / 4-7) of a node
+    t->slot_mask.assign(size_t(16) * P.ent_stride, 0);
+    for (int p = 0; p < 8; ++p) {
+        const int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
+        for (int h = 0; h < 2; ++h)
+            for (size_t k = 0; k < lists[p].size(); ++k) {
+                const StencilEntry &e = lists[p][k];
+                int32_t m = 0;
+                for (int cz = 2 * h; cz < 2 * h + 2; ++cz)
+                    for (int cy = 0; cy < 4; ++cy)
+                        for (int cx = 0; cx < 4; ++cx) {
+                            const int bx = 2 * cx + pp[0] + e.ox + 8, by = 2 * cy + pp[1] + e.oy + 8,
+                                      bz = 2 * cz + pp[2] + e.oz + 8;
+                            m |= 1 << ((bx >> 3) + 3 * (by >> 3) + 9 * (bz >> 3));
+                        }
+                t->slot_mask[(size_t(p) * 2 + h) * P.ent_stride + k] = m;
+            }
+    }
 }
 
 // --------------------------------------------------- interaction counting
@@ -425,7 +443,7 @@ static void free_device(fmm_tree_s *t)
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.mass, d.mp, d.counters,
-                    d.partials};
+                    d.partials, d.down, d.slot_mask};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceTables{};
@@ -439,7 +457,8 @@ static int upload_tree(fmm_tree_s *t)
         (rc = upload(&d.nbr, t->nbr)) || (rc = upload(&d.lists, t->lists)) ||
         (rc = upload(&d.stencil, t->stencil)) || (rc = upload(&d.coef32, t->coef32)) ||
         (rc = upload(&d.coef64, t->coef64)) || (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||
-        (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)) || (rc = upload(&d.levels, t->levels)))
+        (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)) || (rc = upload(&d.levels, t->levels)) ||
+        (rc = upload(&d.slot_mask, t->slot_mask)))
         return rc;
     size_t es = t->cfg.precision == FMM_MIXED ? sizeof(float) : sizeof(double);
     size_t mass_b = size_t(t->n) * NCELL * es;
@@ -452,6 +471,12 @@ static int upload_tree(fmm_tree_s *t)
         (e = cudaMalloc(reinterpret_cast<void **>(&d.partials), part_b)) != cudaSuccess)
         return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
     d.workspace_bytes = mass_b + mp_b + part_b + 64 * sizeof(int32_t);
+    if (t->cfg.precision == FMM_MIXED) {
+        size_t down_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 23 * NCELL * sizeof(float);
+        if ((e = cudaMalloc(reinterpret_cast<void **>(&d.down), down_b)) != cudaSuccess)
+            return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+        d.workspace_bytes += down_b;
+    }
     if (t->cfg.flags & FMM_FLAG_TIMING) {
         const int records = 256;
         t->timer.ev.resize(size_t(2 * records));
@@ -546,6 +571,7 @@ int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config
         L[LV_S1] = L[LV_S0] / h;
         L[LV_S2] = L[LV_S1] / h;
         L[LV_S3] = L[LV_S2] / h;
+        for (int k = 0; k < 4; ++k) L[LV_R0 + k] = 1.0 / L[LV_S0 + k];
     }
     if (!t->host_only) {
         if (cudaGetDevice(&t->device) != cudaSuccess) {
@@ -710,6 +736,24 @@ void fmm_destroy_tree(fmm_tree_t t)
         free_device(t);
     }
     delete t;
+}
+
+int fmm_set_tuning(fmm_tree_t t, const fmm_tuning *tu)
+{
+    if (!t || !tu) return fail(FMM_ERR_INVALID_ARG, "NULL argument");
+    if (tu->mono_subgrids < 0 || tu->mono_subgrids > 4 || tu->mono_subgrids == 3)
+        return fail(FMM_ERR_INVALID_ARG, "mono_subgrids must be 0, 1, 2 or 4");
+    if (tu->ctas_per_sm < 0 || tu->ctas_per_sm > 32)
+        return fail(FMM_ERR_INVALID_ARG, "ctas_per_sm must lie in 0..32");
+    t->tuning = *tu;
+    return FMM_OK;
+}
+
+int fmm_get_tuning(fmm_tree_t t, fmm_tuning *tu)
+{
+    if (!t || !tu) return fail(FMM_ERR_INVALID_ARG, "NULL argument");
+    *tu = t->tuning;
+    return FMM_OK;
 }
 
 const char *fmm_last_error(void) { return g_last_error.c_str(); }

@@ -32,10 +32,10 @@ constexpr int NCOMP = 20;
 constexpr int NMP = 19;          // packed multipole fields per refined cell
 
 // per-level geometry table (device, [level][LEVEL_FIELDS] doubles), filled on
-// the host so that no kernel divides: h, 1/h, h^3, and the level-unit ->
-// physical scales G h^-(n+1) of orders n = 0..3
-constexpr int LEVEL_FIELDS = 8;
-enum { LV_H = 0, LV_IH, LV_H3, LV_S0, LV_S1, LV_S2, LV_S3 };
+// the host so that no kernel divides: h, 1/h, h^3, the level-unit ->
+// physical scales G h^-(n+1) of orders n = 0..3 and their inverses
+constexpr int LEVEL_FIELDS = 12;
+enum { LV_H = 0, LV_IH, LV_H3, LV_S0, LV_S1, LV_S2, LV_S3, LV_R0, LV_R1, LV_R2, LV_R3 };
 
 // per-node table row (device and host)
 struct NodeInfo {
@@ -63,11 +63,16 @@ struct DeviceTables {
     int32_t *tree_leaf_off = nullptr;   // [n_trees + 1]
     int32_t *tree_leaf_rows = nullptr;  // [n_leaf]
     double *levels = nullptr;        // [max_level + 1][LEVEL_FIELDS]
+    int32_t *slot_mask = nullptr;    // [8][2][ent_stride]: neighbour slots (bit per
+                                     // slot) an entry reaches from a node half
     // workspace
     void *mass = nullptr;            // [n][512] float or double
     void *mp = nullptr;              // [n_refined][19][512] float or double
     int32_t *counters = nullptr;     // work-queue heads
     double *partials = nullptr;      // [n_leaf][8]
+    float *down = nullptr;           // mixed only: [n_refined][23][512] float copy
+                                     // of each refined cell's final expansion (20)
+                                     // and centre-of-mass offset from its centre (3)
     size_t workspace_bytes = 0;
 };
 
@@ -119,7 +124,9 @@ struct fmm_tree_s {
     std::vector<double> coef64;
     std::vector<int32_t> tree_leaf_off, tree_leaf_rows;
     std::vector<double> levels;
+    std::vector<int32_t> slot_mask;
     fmm::Plan plan;
+    fmm_tuning tuning{};
     bool host_only = false;
     int device = -1;
     fmm::DeviceTables dev;

@@ -52,6 +52,7 @@ struct KParams {
     const void *coef;
     int n_far, n_near;       // identical for every parity
     int ent_stride;          // entries reserved per parity
+    const int32_t *slot_mask;  // [8][2][ent_stride] neighbour slots an entry can reach
     int reach, py, pz, sub_stride;
     const void *mass;
     const void *mp;
@@ -111,19 +112,26 @@ template <typename T>
 __device__ __forceinline__ void stage_window(T *W, const int *s_nbr, const int *s_leaf,
                                              const T *__restrict__ mass, const KParams &P)
 {
-    const int E = 8 + 2 * P.reach;
-    const int n = E * E * E;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-        const int ux = idx % E, uy = (idx / E) % E, uz = idx / (E * E);
-        const int bx = ux - P.reach + 8, by = uy - P.reach + 8, bz = uz - P.reach + 8;
-        const int slot = (bx >> 3) + 3 * (by >> 3) + 9 * (bz >> 3);
-        T v = T(0);
-        if (s_leaf[slot]) {
-            const int node = s_nbr[slot];
-            v = __ldg(mass + size_t(node) * NCELL + parity_index(bx & 7, by & 7, bz & 7));
+    const int R = P.reach;
+    const int E = 8 + 2 * R;
+    // one (ux, uy) column per thread pass, z innermost; the parity index and
+    // the window address both split into an (x, y) part and a z part
+    for (int t = threadIdx.x; t < E * E; t += blockDim.x) {
+        const int ux = t % E, uy = t / E;
+        const int bx = ux - R + 8, by = uy - R + 8;           // >= 1
+        const int sxy = (bx >> 3) + 3 * (by >> 3);
+        const int lx = bx & 7, ly = by & 7;
+        const int pxy = ((lx & 1) + 2 * (ly & 1)) * 64 + (lx >> 1) + 4 * (ly >> 1);
+        const int wxy = ((ux & 1) + 2 * (uy & 1)) * P.sub_stride + (ux >> 1) + P.py * (uy >> 1);
+        for (int uz = 0; uz < E; ++uz) {
+            const int bz = uz - R + 8;
+            const int slot = sxy + 9 * (bz >> 3);
+            const int lz = bz & 7;
+            T v = T(0);
+            if (s_leaf[slot])
+                v = __ldg(mass + size_t(s_nbr[slot]) * NCELL + pxy + 256 * (lz & 1) + 16 * (lz >> 1));
+            W[wxy + 4 * (uz & 1) * P.sub_stride + P.pz * (uz >> 1)] = v;
         }
-        const int q = (ux & 1) + 2 * (uy & 1) + 4 * (uz & 1);
-        W[q * P.sub_stride + (ux >> 1) + P.py * (uy >> 1) + P.pz * (uz >> 1)] = v;
     }
 }
 
@@ -355,13 +363,42 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) mp_kernel(KP
 // ---------------------------------------------------------- mono_kernel
 // Leaf target, leaf sources: R = -o exactly, so L0 += c0(o) m and
 // L1 += c1(o) m with per-offset weights c0 = -1/|o|, c1 = -o/|o|^3.
-// Two target cells per thread (z and z+4 of one parity) share each weight.
-template <typename T>
+// Each pass takes NB sub-grids (consecutive in the cost-sorted queue), each
+// with its own staged window; every thread holds two target cells (z and
+// z+4 of one parity) per sub-grid, so each loaded weight feeds 2 NB cells.
+template <typename T, int NB>
+__device__ __forceinline__ void mono_entry(const T *W, int wstride, int base0, int base1,
+                                           const StencilEntry *ent, const T *coef, int e,
+                                           Acc<T, 4> (&A)[NB], Acc<T, 4> (&B)[NB])
+{
+    const int w = __ldg(&ent[e].woff);
+    T c[4];
+    if constexpr (sizeof(T) == 4) {
+        const float4 cc = __ldg(reinterpret_cast<const float4 *>(coef) + e);
+        c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+    } else {
+        const double2 c01 = __ldg(reinterpret_cast<const double2 *>(coef) + 2 * e);
+        const double2 c23 = __ldg(reinterpret_cast<const double2 *>(coef) + 2 * e + 1);
+        c[0] = c01.x; c[1] = c01.y; c[2] = c23.x; c[3] = c23.y;
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const T m0 = W[b * wstride + base0 + w];
+        const T m1 = W[b * wstride + base1 + w];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            A[b].part[k] += c[k] * m0;
+            B[b].part[k] += c[k] * m1;
+        }
+    }
+}
+
+template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *W = reinterpret_cast<T *>(smem_raw);
-    __shared__ int s_nbr[27], s_leaf[27], s_row[27], s_item;
+    __shared__ int s_nbr[NB][27], s_leaf[NB][27], s_row[NB][27], s_item;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = warp;
     const int px = p & 1, py = (p >> 1) & 1, pz = p >> 2;
@@ -370,55 +407,61 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
     const T *coef = static_cast<const T *>(P.coef) + size_t(p) * P.ent_stride * 4;
     const T *mass = static_cast<const T *>(P.mass);
     const int n_ent = P.n_far + P.n_near;
+    const int wstride = 8 * P.sub_stride;
     const int base0 = cx + P.py * cy + P.pz * cz;
     const int base1 = base0 + 2 * P.pz;
     for (;;) {
-        const int item = pull_item(P.counter, &s_item);
-        if (item >= P.n_items) break;
-        const int node = P.list[item];
-        load_slots(node, P, s_nbr, s_leaf, s_row);
+        if (threadIdx.x == 0) s_item = atomicAdd(P.counter, NB);
         __syncthreads();
-        stage_window<T>(W, s_nbr, s_leaf, mass, P);
-        __syncthreads();
-        Acc<T, 4> A, B;
-        A.zero();
-        B.zero();
-        for (int e0 = 0; e0 < n_ent; e0 += kChunk) {
-            const int e1 = min(e0 + kChunk, n_ent);
-            for (int e = e0; e < e1; ++e) {
-                const int w = __ldg(&ent[e].woff);
-                T c[4];
-                if constexpr (sizeof(T) == 4) {
-                    const float4 cc = __ldg(reinterpret_cast<const float4 *>(coef) + e);
-                    c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
-                } else {
-                    const double2 c01 = __ldg(reinterpret_cast<const double2 *>(coef) + 2 * e);
-                    const double2 c23 = __ldg(reinterpret_cast<const double2 *>(coef) + 2 * e + 1);
-                    c[0] = c01.x; c[1] = c01.y; c[2] = c23.x; c[3] = c23.y;
-                }
-                const T m0 = W[base0 + w];
-                const T m1 = W[base1 + w];
+        const int item0 = s_item;
+        if (item0 >= P.n_items) break;
+        int nodes[NB];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    A.part[k] += c[k] * m0;
-                    B.part[k] += c[k] * m1;
-                }
-            }
-            A.flush();
-            B.flush();
+        for (int b = 0; b < NB; ++b) nodes[b] = item0 + b < P.n_items ? P.list[item0 + b] : -1;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (nodes[b] >= 0) load_slots(nodes[b], P, s_nbr[b], s_leaf[b], s_row[b]);
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (nodes[b] >= 0) stage_window<T>(W + b * wstride, s_nbr[b], s_leaf[b], mass, P);
+        __syncthreads();
+        Acc<T, 4> A[NB], B[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            A[b].zero();
+            B[b].zero();
         }
+        int e = 0;
+        for (; e + kChunk <= n_ent; e += kChunk) {
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j)
+                mono_entry<T, NB>(W, wstride, base0, base1, ent, coef, e + j, A, B);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                A[b].flush();
+                B[b].flush();
+            }
+        }
+        for (; e < n_ent; ++e) mono_entry<T, NB>(W, wstride, base0, base1, ent, coef, e, A, B);
         const int ax = 2 * cx + px, ay = 2 * cy + py;
         const int cell0 = ax + 8 * ay + 64 * (2 * cz + pz);
         const int cell1 = cell0 + 64 * 4;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            store_L<T>(P, node, k, cell0, A.hi[k], A.lo[k]);
-            store_L<T>(P, node, k, cell1, B.hi[k], B.lo[k]);
-        }
+        for (int b = 0; b < NB; ++b) {
+            if (nodes[b] < 0) continue;
+            A[b].flush();
+            B[b].flush();
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            P.dL1[(size_t(node) * 3 + i) * NCELL + cell0] = 0.0;
-            P.dL1[(size_t(node) * 3 + i) * NCELL + cell1] = 0.0;
+            for (int k = 0; k < 4; ++k) {
+                store_L<T>(P, nodes[b], k, cell0, A[b].hi[k], A[b].lo[k]);
+                store_L<T>(P, nodes[b], k, cell1, B[b].hi[k], B[b].lo[k]);
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                P.dL1[(size_t(nodes[b]) * 3 + i) * NCELL + cell0] = 0.0;
+                P.dL1[(size_t(nodes[b]) * 3 + i) * NCELL + cell1] = 0.0;
+            }
         }
         __syncthreads();
     }
@@ -427,11 +470,14 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
 // ------------------------------------------------------------ mx_kernel
 // Leaf target, refined sources (monopole<-multipole): orders 0-1 and the
 // correction S1 (the target has no third moment).  Adds to what mono_kernel
-// stored for the same node, so it runs after it on the same stream.
+// stored for the same node, so it runs after it on the same stream.  Work
+// items are node halves (z < 4, z >= 4); a host table gives, per parity,
+// half and stencil entry, the neighbour slots its sources can fall in, so a
+// warp skips (uniformly) every entry that cannot reach a refined neighbour.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
 {
-    __shared__ int s_nbr[27], s_leaf[27], s_row[27], s_item;
+    __shared__ int s_nbr[27], s_leaf[27], s_row[27], s_item, s_mask;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = warp;
     const int px = p & 1, py = (p >> 1) & 1, pz = p >> 2;
@@ -441,70 +487,78 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
     for (;;) {
         const int item = pull_item(P.counter, &s_item);
         if (item >= P.n_items) break;
-        const int node = P.list[item];
+        const int node = P.list[item >> 1];
+        const int half = item & 1;
         load_slots(node, P, s_nbr, s_leaf, s_row);
         __syncthreads();
-        for (int half = 0; half < 2; ++half) {
-            const int cz = cz0 + 2 * half;
-            const int ax = 2 * cx + px, ay = 2 * cy + py, az = 2 * cz + pz;
-            Acc<T, 4> L;
-            L.zero();
-            T S1[3] = {T(0), T(0), T(0)};
-            for (int e0 = 0; e0 < n_ent; e0 += kChunk) {
-                const int e1 = min(e0 + kChunk, n_ent);
-                for (int e = e0; e < e1; ++e) {
-                    const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + e));
-                    int slot, pi;
-                    source_cell(ax, ay, az, E.x, E.y, E.z, slot, pi);
-                    const int row = s_row[slot];
-                    if (!__any_sync(0xffffffffu, row >= 0)) continue;
-                    T m0 = T(0), dB[3] = {T(0), T(0), T(0)}, A2[6], A3[10];
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) A2[q] = T(0);
-#pragma unroll
-                    for (int q = 0; q < 10; ++q) A3[q] = T(0);
-                    if (row >= 0) load_source<T>(P, s_nbr[slot], row, pi, m0, dB, A2, A3);
-                    DTensors<T, true> D;
-                    D.eval(-T(E.x) - dB[0], -T(E.y) - dB[1], -T(E.z) - dB[2]);
-                    T l0 = m0 * D.D0;
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) l0 += A2[q] * D.D2[q];
-#pragma unroll
-                    for (int q = 0; q < 10; ++q) l0 -= A3[q] * D.D3[q];
-                    L.part[0] -= l0;
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        T l1 = m0 * D.D1[i];
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) l1 += A2[q] * D.D3[r3_of(i, q)];
-                        L.part[1 + i] -= l1;
-                        T s = T(0);
-#pragma unroll
-                        for (int q = 0; q < 10; ++q) s += A3[q] * D.D4[r4_of(i, q)];
-                        S1[i] += s;
-                    }
-                }
-                L.flush();
-            }
-            const int cell = ax + 8 * ay + 64 * az;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const size_t idx = (size_t(node) * NCOMP + k) * NCELL + cell;
-                if constexpr (sizeof(T) == 4) {
-                    float *Lh = static_cast<float *>(P.L);
-                    float s, e;
-                    two_sum(Lh[idx], L.hi[k], s, e);
-                    const float lo = P.Lc[idx] + L.lo[k] + e;
-                    const float s2 = s + lo;
-                    Lh[idx] = s2;
-                    P.Lc[idx] = lo - (s2 - s);
-                } else {
-                    static_cast<double *>(P.L)[idx] += L.hi[k];
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = double(S1[i]);
+        if (threadIdx.x < 32) {
+            const unsigned bits = __ballot_sync(0xffffffffu, threadIdx.x < 27 && s_row[threadIdx.x] >= 0);
+            if (threadIdx.x == 0) s_mask = int(bits);
         }
+        __syncthreads();
+        const int rmask = s_mask;
+        const int32_t *smask = P.slot_mask + (size_t(p) * 2 + half) * P.ent_stride;
+        const int cz = cz0 + 2 * half;
+        const int ax = 2 * cx + px, ay = 2 * cy + py, az = 2 * cz + pz;
+        Acc<T, 4> L;
+        L.zero();
+        T S1[3] = {T(0), T(0), T(0)};
+        int done = 0;
+        for (int e = 0; e < n_ent; ++e) {
+            if (!(__ldg(&smask[e]) & rmask)) continue;
+            const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + e));
+            int slot, pi;
+            source_cell(ax, ay, az, E.x, E.y, E.z, slot, pi);
+            const int row = s_row[slot];
+            T m0 = T(0), dB[3] = {T(0), T(0), T(0)}, A2[6], A3[10];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) A2[q] = T(0);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) A3[q] = T(0);
+            if (row >= 0) load_source<T>(P, s_nbr[slot], row, pi, m0, dB, A2, A3);
+            DTensors<T, true> D;
+            D.eval(-T(E.x) - dB[0], -T(E.y) - dB[1], -T(E.z) - dB[2]);
+            T l0 = m0 * D.D0;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) l0 += A2[q] * D.D2[q];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) l0 -= A3[q] * D.D3[q];
+            L.part[0] -= l0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                T l1 = m0 * D.D1[i];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) l1 += A2[q] * D.D3[r3_of(i, q)];
+                L.part[1 + i] -= l1;
+                T sacc = T(0);
+#pragma unroll
+                for (int q = 0; q < 10; ++q) sacc += A3[q] * D.D4[r4_of(i, q)];
+                S1[i] += sacc;
+            }
+            if (++done == kChunk) {
+                L.flush();
+                done = 0;
+            }
+        }
+        L.flush();
+        const int cell = ax + 8 * ay + 64 * az;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const size_t idx = (size_t(node) * NCOMP + k) * NCELL + cell;
+            if constexpr (sizeof(T) == 4) {
+                float *Lh = static_cast<float *>(P.L);
+                float s, e;
+                two_sum(Lh[idx], L.hi[k], s, e);
+                const float lo = P.Lc[idx] + L.lo[k] + e;
+                const float s2 = s + lo;
+                Lh[idx] = s2;
+                P.Lc[idx] = lo - (s2 - s);
+            } else {
+                static_cast<double *>(P.L)[idx] += L.hi[k];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = double(S1[i]);
         __syncthreads();
     }
 }
@@ -615,23 +669,41 @@ struct Kernels {
         if ((e = cudaFuncSetAttribute(mp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(window_bytes))) != cudaSuccess)
             return e;
-        if ((e = cudaFuncSetAttribute(mono_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(mono_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(window_bytes))) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(mono_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(2 * window_bytes))) != cudaSuccess)
+            return e;
+        if (sizeof(T) == 4 &&
+            (e = cudaFuncSetAttribute(mono_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(4 * window_bytes))) != cudaSuccess)
             return e;
         done_bytes = window_bytes;
         return cudaSuccess;
     }
 };
 
+// persistent grid: SMs x resident CTAs (optionally capped by the tuning)
 template <typename Kern>
-int persistent_grid(Kern k, size_t smem, int64_t items, int sms)
+int persistent_grid(Kern k, size_t smem, int64_t items, int sms, int cap_per_sm)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
+    if (cap_per_sm > 0 && cap_per_sm < per_sm) per_sm = cap_per_sm;
     int64_t g = int64_t(per_sm) * sms;
     return int(items < g ? items : g);
+}
+
+template <typename T, int NB>
+cudaError_t launch_mono(const KParams &K, size_t wbytes, int sms, int cap, cudaStream_t s)
+{
+    const int64_t passes = (K.n_items + NB - 1) / NB;
+    const int g = persistent_grid(mono_kernel<T, NB>, NB * wbytes, passes, sms, cap);
+    mono_kernel<T, NB><<<g, kThreads, NB * wbytes, s>>>(K);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -658,6 +730,8 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     P.Lc = Lc;
     P.dL1 = dL1;
     P.theta2 = t->cfg.theta * t->cfg.theta;
+    P.slot_mask = d.slot_mask;
+    const int cap = t->tuning.ctas_per_sm;
     const size_t wbytes = size_t(8) * Pl.sub_stride * sizeof(T);
     cudaError_t e = Kernels<T>::configure(wbytes);
     if (e != cudaSuccess) return e;
@@ -680,7 +754,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         K.list = d.lists + Pl.work_mp.off;
         K.n_items = int32_t(Pl.work_mp.count);
         K.counter = d.counters + Q_MP;
-        int g = persistent_grid(mp_kernel<T>, wbytes, Pl.work_mp.count, sms);
+        int g = persistent_grid(mp_kernel<T>, wbytes, Pl.work_mp.count, sms, cap);
         timing_begin(t, FMM_K_MULTIPOLE, s);
         mp_kernel<T><<<g, kThreads, wbytes, s>>>(K);
         timing_end(t, s);
@@ -692,19 +766,23 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         K.list = d.lists + Pl.work_mono.off;
         K.n_items = int32_t(Pl.work_mono.count);
         K.counter = d.counters + Q_MONO;
-        int g = persistent_grid(mono_kernel<T>, wbytes, Pl.work_mono.count, sms);
+        int nb = t->tuning.mono_subgrids;
+        if (nb != 1 && nb != 2 && nb != 4) nb = sizeof(T) == 4 ? 2 : 1;
+        if (sizeof(T) != 4 && nb == 4) nb = 2;
         timing_begin(t, FMM_K_MONOPOLE, s);
-        mono_kernel<T><<<g, kThreads, wbytes, s>>>(K);
+        e = nb == 1 ? launch_mono<T, 1>(K, wbytes, sms, cap, s)
+            : nb == 2 ? launch_mono<T, 2>(K, wbytes, sms, cap, s)
+                      : launch_mono<T, sizeof(T) == 4 ? 4 : 2>(K, wbytes, sms, cap, s);
         timing_end(t, s);
         ++nl;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (e != cudaSuccess) return e;
     }
     if (Pl.work_mx.count) {
         KParams K = P;
         K.list = d.lists + Pl.work_mx.off;
-        K.n_items = int32_t(Pl.work_mx.count);
+        K.n_items = int32_t(2 * Pl.work_mx.count);       // node halves
         K.counter = d.counters + Q_MX;
-        int g = persistent_grid(mx_kernel<T>, 0, Pl.work_mx.count, sms);
+        int g = persistent_grid(mx_kernel<T>, 0, K.n_items, sms, cap);
         timing_begin(t, FMM_K_MONO_MULTI, s);
         mx_kernel<T><<<g, kThreads, 0, s>>>(K);
         timing_end(t, s);

@@ -28,8 +28,8 @@ KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_mul
                 "forces", "reduce")
 
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
-            "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_destroy_tree",
-            "fmm_last_error")
+            "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_set_tuning", "fmm_get_tuning",
+            "fmm_destroy_tree", "fmm_last_error")
 
 NCELL = 512
 NCOMP = 20
@@ -68,6 +68,11 @@ class FmmStats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64 * 16)]
 
 
+class FmmTuning(ctypes.Structure):
+    _fields_ = [("mono_subgrids", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
 _LOCK = threading.Lock()
 _LIB = None
 
@@ -95,6 +100,8 @@ def load(build=True):
         lib.fmm_forces.argtypes = [P, P, P, P, P, P, P, P]
         lib.fmm_destroy_tree.argtypes = [P]
         lib.fmm_destroy_tree.restype = None
+        lib.fmm_set_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
+        lib.fmm_get_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_last_error.argtypes = []
         lib.fmm_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -208,6 +215,17 @@ def fmm_forces(tree, L64, dL1_acc, rho, phi, g, totals, stream=None):
 
 def fmm_destroy_tree(tree):
     load().fmm_destroy_tree(tree.handle)
+
+
+def fmm_set_tuning(tree, mono_subgrids=0, ctas_per_sm=0):
+    t = FmmTuning(int(mono_subgrids), int(ctas_per_sm))
+    _check(load().fmm_set_tuning(tree.handle, ctypes.byref(t)))
+
+
+def fmm_get_tuning(tree):
+    t = FmmTuning()
+    _check(load().fmm_get_tuning(tree.handle, ctypes.byref(t)))
+    return {"mono_subgrids": t.mono_subgrids, "ctas_per_sm": t.ctas_per_sm}
 
 
 def fmm_last_error():

@@ -252,6 +252,33 @@ typedef struct {
 int fmm_set_tuning(fmm_tree_t tree, const fmm_tuning *tuning);
 int fmm_get_tuning(fmm_tree_t tree, fmm_tuning *tuning);
 
+/*
+ * fmm_forces_noalloc -- the leaf-force pass for callers that cannot allocate
+ * device memory.  The paper has no counterpart; it exists for callers such as
+ * a framework that owns all device memory through its own pool and forbids
+ * side allocations, or a foreign-language host that can pass pointers but not
+ * manage CUDA allocations.  Same results as fmm_forces (potential, field and
+ * the FP64 conservation sums, same per-cell arithmetic), but it needs no tree
+ * handle and allocates nothing: the per-leaf-node partial sums go to a fixed
+ * array of 65536 x 8 doubles (4 MiB) that the library holds on every GPU that
+ * loads it, until the process exits.
+ *   leaf_table: device int32 [n_leaf][6], one row per leaf node in leaf-row
+ *               order: node index, level, ix, iy, iz, tree_id (the tree's
+ *               descriptor values).
+ *   n_leaf:     1..65536 (FMM_ERR_INVALID_ARG beyond the array's size).
+ *   n_trees:    number of trees, 1..65535; totals gets one row per tree.
+ *   box_size:   edge of the domain (box_lo does not enter the sums).
+ *   L64, dL1_acc, rho, phi, g, totals: as for fmm_forces.
+ * Every call shares the fixed array and overwrites the rows it uses before
+ * reading them; calls whose work overlaps on the GPU race on it, so serialise
+ * them.  The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ */
+int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int32_t n_trees,
+                       double box_size, const double *L64, const double *dL1_acc,
+                       const double *rho, double *phi, double *g, double *totals,
+                       fmm_stream_t stream);
+
 /* Release the tree's host and device memory (synchronises the device first). */
 void fmm_destroy_tree(fmm_tree_t tree);
 

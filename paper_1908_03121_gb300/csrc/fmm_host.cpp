@@ -68,6 +68,8 @@ void mono_coef(int ox, int oy, int oz, double c[4])
 
 namespace fmm {
 
+void record_error(const std::string &msg) { g_last_error = msg; }
+
 int sm_count_of_current_device()
 {
     int dev = 0, n = 0;

@@ -152,6 +152,9 @@ cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *
 
 int sm_count_of_current_device();
 
+// set the calling thread's fmm_last_error() message
+void record_error(const std::string &msg);
+
 // FMM_FLAG_TIMING hooks around one kernel launch (no-ops otherwise)
 void timing_begin(const fmm_tree_s *t, int slot, cudaStream_t s);
 void timing_end(const fmm_tree_s *t, cudaStream_t s);

@@ -29,7 +29,7 @@ KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_mul
 
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
             "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_set_tuning", "fmm_get_tuning",
-            "fmm_destroy_tree", "fmm_last_error")
+            "fmm_forces_noalloc", "fmm_destroy_tree", "fmm_last_error")
 
 NCELL = 512
 NCOMP = 20
@@ -100,6 +100,8 @@ def load(build=True):
         lib.fmm_forces.argtypes = [P, P, P, P, P, P, P, P]
         lib.fmm_destroy_tree.argtypes = [P]
         lib.fmm_destroy_tree.restype = None
+        lib.fmm_forces_noalloc.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                           P, P, P, P, P, P, P]
         lib.fmm_set_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_get_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_last_error.argtypes = []
@@ -215,6 +217,16 @@ def fmm_forces(tree, L64, dL1_acc, rho, phi, g, totals, stream=None):
 
 def fmm_destroy_tree(tree):
     load().fmm_destroy_tree(tree.handle)
+
+
+def fmm_forces_noalloc(leaf_table, n_leaf, n_trees, box_size, L64, dL1_acc, rho, phi, g,
+                       totals, stream=None):
+    """The leaf-force pass without a tree handle or any allocation (for callers
+    that cannot allocate device memory); ``leaf_table`` is a device int32
+    [n_leaf, 6] tensor (node, level, ix, iy, iz, tree_id per leaf node)."""
+    _check(load().fmm_forces_noalloc(_ptr(leaf_table), int(n_leaf), int(n_trees),
+                                     float(box_size), _ptr(L64), _ptr(dL1_acc), _ptr(rho),
+                                     _ptr(phi), _ptr(g), _ptr(totals), _stream(stream)))
 
 
 def fmm_set_tuning(tree, mono_subgrids=0, ctas_per_sm=0):

@@ -313,15 +313,15 @@ static void slot_tables(const fmm_tree_s *t, std::vector<int64_t> &tab)
 
 // Flop model: operations of one interaction of each kind as the kernels
 // evaluate it, counted from their source (fused multiply-add = 2, the
-// reciprocal square root = 1), compensation excluded:
-//   derivative tensors D0..D4 from R: 126; offset R: 3 (leaf source) or 6;
-//   multipole<-multipole: contraction of orders 0-3 (108) + correction
-//     sums S1 (60) and S2 (30)                                  -> 330
-//   multipole<-monopole: M0 D^(n) for 20 components (40) + S2   -> 199
-//   monopole<-monopole: tabulated weights, 4 FMAs               ->   8
-//   monopole<-multipole: orders 0-1 (76) + S1 (60)              -> 268
+// reciprocal square root = 1), compensation excluded.  The contraction works
+// in traceless bases (D2 5, D3 7 + 2 dependent, 12 slice values of D4):
+//   derivative tensors from R: 92; offset R: 3 (leaf source) or 6;
+//   multipole<-multipole: orders 0-3 (86) + correction weights and sum (56) -> 240
+//   multipole<-monopole:  M0 D^(n) (32) + weights (7) and sum (42)         -> 176
+//   monopole<-monopole:   tabulated weights, 4 FMAs                        ->   8
+//   monopole<-multipole:  orders 0-1 (62) + correction sum (42)            -> 199
 // (Sec. 4.3 quotes 455 and 12 for the paper's own kernels.)
-static const double kFlops[4] = {330.0, 199.0, 8.0, 268.0};
+static const double kFlops[4] = {240.0, 176.0, 8.0, 199.0};
 
 static void plan_work(fmm_tree_s *t)
 {

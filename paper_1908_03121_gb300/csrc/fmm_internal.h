@@ -7,11 +7,12 @@
 //     so the 64 cells of one parity class (which share one stencil) are
 //     contiguous;
 //   - packed same-level source data (workspace), in level units:
-//       mass[node][512]          cell mass (all nodes)
-//       mp[mp_row][19][512]      refined nodes only: centre-of-mass offset
-//                                from the cell centre in cell widths (3),
-//                                A2 = mult * M2 / (2 h^2) (6),
-//                                A3 = mult * M3 / (6 h^3) (10)
+//       mass[node][512]            cell mass (all nodes)
+//       mp[mp_row][4][512][4]      refined nodes only, four groups of four:
+//                                  (M0, centre-of-mass offset from the cell
+//                                  centre in cell widths), then the traceless
+//                                  projections B2 (5) and B3 (7) of
+//                                  A2 = mult * M2 / (2 h^2), A3 = mult * M3 / (6 h^3)
 //     where mult is the number of index permutations of a symmetric
 //     component (so full-tensor contractions become plain dot products).
 #pragma once
@@ -29,7 +30,7 @@ namespace fmm {
 constexpr int NSIDE = 8;
 constexpr int NCELL = 512;
 constexpr int NCOMP = 20;
-constexpr int NMP = 19;          // packed multipole fields per refined cell
+constexpr int NMP = 16;          // packed same-level values per refined cell
 
 // per-level geometry table (device, [level][LEVEL_FIELDS] doubles), filled on
 // the host so that no kernel divides: h, 1/h, h^3, the level-unit ->

@@ -23,12 +23,15 @@
 // work queues; a warp holds 32 targets of one child parity so the stencil
 // loop is warp-uniform; leaf-source masses of the 26-neighbour halo are staged
 // once per sub-grid into a parity-split, bank-padded shared-memory window;
-// refined-source moments stream through L1 from a parity-split packed
-// layout, so a warp's 32 loads of one field are contiguous.
+// refined-source moments stream through L1 as four vector loads from a
+// parity-split packed layout, so a warp's loads are contiguous.  Orders 2-4
+// of the derivative tensors are traceless, so the contraction works in
+// traceless bases (fmm_tensor.cuh): 16 accumulated components instead of 20,
+// 16 packed source values instead of 20, and about a quarter fewer products.
 // Mixed precision: offsets are formed from double-precision centres of mass
 // (packed as offsets from the cell centre, in cell widths), the contraction
 // runs in float with per-chunk sums folded into (hi, lo) pairs by TwoSum, and
-// the correction is finished in double.
+// the correction's compensated sum is stored and carried down in double.
 #include <cstdio>
 
 #include "fmm_internal.h"
@@ -63,8 +66,11 @@ struct KParams {
 };
 
 // ------------------------------------------------------------------ pack
-// mass[node][pi] = M0; refined nodes also get delta = (X - centre)/h,
-// A2 = mult M2 / (2 h^2), A3 = mult M3 / (6 h^3) at mp[row][field][pi].
+// mass[node][pi] = M0 for every node.  Refined nodes also get, in level
+// units, four groups of four values at mp[row][g][pi][0..3]:
+//   g0 = (M0, delta), delta = (X - centre) / h,
+//   g1 = B2[0..3], g2 = (B2[4], B3[0..2]), g3 = B3[3..6],
+// the traceless projections of A2 = mult M2 / (2 h^2), A3 = mult M3 / (6 h^3).
 template <typename T>
 __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ info,
                                                    const double *__restrict__ levels,
@@ -83,17 +89,27 @@ __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ 
     if (ni.mp_row < 0) return;
     const double h = levels[ni.level * LEVEL_FIELDS + LV_H];
     const double ih = levels[ni.level * LEVEL_FIELDS + LV_IH];
-    T *out = mp + size_t(ni.mp_row) * NMP * NCELL + pi;
     const double ctr[3] = {lo_x + (8.0 * ni.ix + x + 0.5) * h, lo_y + (8.0 * ni.iy + y + 0.5) * h,
                            lo_z + (8.0 * ni.iz + z + 0.5) * h};
+    double d[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        out[a * NCELL] = T((com[(size_t(node) * 3 + a) * NCELL + c] - ctr[a]) * ih);
+    for (int a = 0; a < 3; ++a) d[a] = (com[(size_t(node) * 3 + a) * NCELL + c] - ctr[a]) * ih;
     const double w2 = 0.5 * ih * ih, w3 = (1.0 / 6.0) * ih * ih * ih;
+    double A2[6], A3[10];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) out[(3 + q) * NCELL] = T(mult2(q) * w2 * Mn[(4 + q) * NCELL]);
+    for (int q = 0; q < 6; ++q) A2[q] = mult2(q) * w2 * Mn[(4 + q) * NCELL];
 #pragma unroll
-    for (int q = 0; q < 10; ++q) out[(9 + q) * NCELL] = T(mult3(q) * w3 * Mn[(10 + q) * NCELL]);
+    for (int q = 0; q < 10; ++q) A3[q] = mult3(q) * w3 * Mn[(10 + q) * NCELL];
+    // symmetric order: A2 xx xy xz yy yz zz; A3 xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+    const double v[16] = {Mn[0],         d[0],          d[1],          d[2],
+                          A2[0] - A2[5], A2[3] - A2[5], A2[1],         A2[2],
+                          A2[4],         A3[0] - A3[5], A3[1] - A3[8], A3[2] - A3[9],
+                          A3[3] - A3[5], A3[4],         A3[6] - A3[8], A3[7] - A3[9]};
+    T *out = mp + (size_t(ni.mp_row) * 4 * NCELL + pi) * 4;
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[size_t(g) * NCELL * 4 + j] = T(v[4 * g + j]);
 }
 
 // ------------------------------------------------------------ common bits
@@ -198,22 +214,99 @@ __device__ __forceinline__ void store_L(const KParams &P, int node, int k, int c
     }
 }
 
-// One multipole or monopole source, accumulated into the full order-3
-// expansion plus the two correction sums S1 (sum D4 : A3_B) and
-// S2 (sum M0_B D4), all with the sign of L folded in.
-template <typename T, bool SRC_MP>
-__device__ __forceinline__ void accumulate_mp(T Rx, T Ry, T Rz, T m0, const T *A2, const T *A3,
-                                              Acc<T, 20> &L, T *S1, T *S2)
+// store -(a + b) for a traceless-dependent component
+template <typename T, int N>
+__device__ __forceinline__ void store_neg_sum(const KParams &P, int node, int k, int cell,
+                                              const Acc<T, N> &L, int a, int b)
 {
-    DTensors<T, true> D;
-    D.eval(Rx, Ry, Rz);
-    // L0 = -(M0 D0 + A2.D2 - A3.D3)
+    if constexpr (sizeof(T) == 4) {
+        float s, e;
+        two_sum(L.hi[a], L.hi[b], s, e);
+        store_L<T>(P, node, k, cell, -s, -(L.lo[a] + L.lo[b] + e));
+    } else {
+        store_L<T>(P, node, k, cell, -(L.hi[a] + L.hi[b]), T(0));
+    }
+}
+
+// the 16 traceless accumulators of a multipole target -> 20 stored components
+// accumulators: 0 L0 | 1-3 L1 | 4-8 L2 (xx yy xy xz yz) | 9-15 L3 (xxx xxy
+// xxz xyy xyz yyy yyz)
+template <typename T>
+__device__ __forceinline__ void store_target(const KParams &P, int node, int cell,
+                                             const Acc<T, 16> &L)
+{
+    constexpr int direct[16] = {0, 1, 2, 3, 4, 7, 5, 6, 8, 10, 11, 12, 13, 14, 16, 17};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) store_L<T>(P, node, direct[k], cell, L.hi[k], L.lo[k]);
+    store_neg_sum<T, 16>(P, node, 9, cell, L, 4, 5);      // zz  = -(xx + yy)
+    store_neg_sum<T, 16>(P, node, 15, cell, L, 9, 12);    // xzz = -(xxx + xyy)
+    store_neg_sum<T, 16>(P, node, 18, cell, L, 10, 14);   // yzz = -(xxy + yyy)
+    store_neg_sum<T, 16>(P, node, 19, cell, L, 11, 15);   // zzz = -(xxz + yyz)
+}
+
+// packed data of one source cell (level units)
+template <typename T>
+struct Src {
+    T m0, d[3], B2[5], B3[7];
+};
+
+template <typename T>
+__device__ __forceinline__ void load4(const T *p, T v[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_source(const KParams &P, int row, int pi, Src<T> &s)
+{
+    const T *base = static_cast<const T *>(P.mp) + (size_t(row) * 4 * NCELL + pi) * 4;
+    T v[16];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) load4<T>(base + size_t(g) * NCELL * 4, v + 4 * g);
+    s.m0 = v[0];
+    s.d[0] = v[1]; s.d[1] = v[2]; s.d[2] = v[3];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) s.B2[k] = v[4 + k];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) s.B3[q] = v[9 + q];
+}
+
+template <typename T>
+__device__ __forceinline__ void zero_moments(Src<T> &s)
+{
+    s.d[0] = s.d[1] = s.d[2] = T(0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) s.B2[k] = T(0);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) s.B3[q] = T(0);
+}
+
+// One source (multipole if SRC_MP, else a point mass m0 = s.m0) into a
+// multipole target's 16 traceless accumulators and the correction sum
+//   S_i += sum_q (B3_B - M0_B a3_A)_q D4[i, q],  a3_A = B3_A / M0_A,
+// with the sign of L folded in:
+//   L0 -= M0 D0 + B2.D2 - B3.D3,  L1_i -= M0 D1_i + B2.D3[i,.],
+//   L2 -= M0 D2,  L3 -= M0 D3.
+template <typename T, bool SRC_MP>
+__device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const T a3A[7],
+                                       Acc<T, 16> &L, Acc<T, 3> &S)
+{
+    DTraceless<T> D;
+    D.template eval<true>(Rx, Ry, Rz);
+    const T m0 = s.m0;
     T l0 = m0 * D.D0;
     if (SRC_MP) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) l0 += A2[q] * D.D2[q];
+        for (int k = 0; k < 5; ++k) l0 += s.B2[k] * D.D2[k];
 #pragma unroll
-        for (int q = 0; q < 10; ++q) l0 -= A3[q] * D.D3[q];
+        for (int q = 0; q < 7; ++q) l0 -= s.B3[q] * D.D3[q];
     }
     L.part[0] -= l0;
 #pragma unroll
@@ -221,41 +314,51 @@ __device__ __forceinline__ void accumulate_mp(T Rx, T Ry, T Rz, T m0, const T *A
         T l1 = m0 * D.D1[i];
         if (SRC_MP) {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) l1 += A2[q] * D.D3[r3_of(i, q)];
+            for (int k = 0; k < 5; ++k) l1 += s.B2[k] * D.d3slice(i, k);
         }
         L.part[1 + i] -= l1;
     }
 #pragma unroll
-    for (int q = 0; q < 6; ++q) L.part[4 + q] -= m0 * D.D2[q];
+    for (int k = 0; k < 5; ++k) L.part[4 + k] -= m0 * D.D2[k];
 #pragma unroll
-    for (int q = 0; q < 10; ++q) L.part[10 + q] -= m0 * D.D3[q];
-    if (SRC_MP) {
+    for (int q = 0; q < 7; ++q) L.part[9 + q] -= m0 * D.D3[q];
+    T w[7];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            T s = T(0);
+    for (int q = 0; q < 7; ++q) w[q] = SRC_MP ? s.B3[q] - m0 * a3A[q] : -m0 * a3A[q];
 #pragma unroll
-            for (int q = 0; q < 10; ++q) s += A3[q] * D.D4[r4_of(i, q)];
-            S1[i] += s;
-        }
+    for (int i = 0; i < 3; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) acc += w[q] * D.U[i][q];
+        S.part[i] += acc;
     }
-#pragma unroll
-    for (int q = 0; q < 15; ++q) S2[q] += m0 * D.D4[q];
 }
 
-// load the packed data of one refined source cell
+// One multipole source into a leaf target (orders 0-1 and the correction;
+// the target has no third moment)
 template <typename T>
-__device__ __forceinline__ void load_source(const KParams &P, int node, int row, int pi, T &m0,
-                                            T *dB, T *A2, T *A3)
+__device__ __forceinline__ void acc_mx(T Rx, T Ry, T Rz, const Src<T> &s, Acc<T, 4> &L,
+                                       Acc<T, 3> &S)
 {
-    const T *mass = static_cast<const T *>(P.mass);
-    const T *mp = static_cast<const T *>(P.mp) + size_t(row) * NMP * NCELL + pi;
-    m0 = __ldg(mass + size_t(node) * NCELL + pi);
+    DTraceless<T> D;
+    D.template eval<true>(Rx, Ry, Rz);
+    T l0 = s.m0 * D.D0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dB[a] = __ldg(mp + a * NCELL);
+    for (int k = 0; k < 5; ++k) l0 += s.B2[k] * D.D2[k];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) A2[q] = __ldg(mp + (3 + q) * NCELL);
+    for (int q = 0; q < 7; ++q) l0 -= s.B3[q] * D.D3[q];
+    L.part[0] -= l0;
 #pragma unroll
-    for (int q = 0; q < 10; ++q) A3[q] = __ldg(mp + (9 + q) * NCELL);
+    for (int i = 0; i < 3; ++i) {
+        T l1 = s.m0 * D.D1[i];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) l1 += s.B2[k] * D.d3slice(i, k);
+        L.part[1 + i] -= l1;
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) acc += s.B3[q] * D.U[i][q];
+        S.part[i] += acc;
+    }
 }
 
 // per-lane source position: slot of the neighbour node and parity index
@@ -265,6 +368,25 @@ __device__ __forceinline__ void source_cell(int ax, int ay, int az, int ox, int 
     const int bx = ax + ox + 8, by = ay + oy + 8, bz = az + oz + 8;   // >= 1
     slot = (bx >> 3) + 3 * (by >> 3) + 9 * (bz >> 3);
     pi = parity_index(bx & 7, by & 7, bz & 7);
+}
+
+// own packed data of a multipole target: centre-of-mass offset and a3 = B3/M0
+template <typename T>
+__device__ __forceinline__ void load_target(const KParams &P, int row, int pi, T dA[3], T a3A[7])
+{
+    Src<T> own;
+    load_source<T>(P, row, pi, own);
+    const T im0 = T(1) / own.m0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dA[a] = own.d[a];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) a3A[q] = own.B3[q] * im0;
+}
+
+template <typename T>
+__device__ __forceinline__ double acc_value(const Acc<T, 3> &S, int i)
+{
+    return double(S.hi[i]) + double(S.lo[i]);
 }
 
 // ------------------------------------------------------------ mp_kernel
@@ -282,7 +404,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) mp_kernel(KP
     const int cx = lane & 3, cy = (lane >> 2) & 3, cz0 = lane >> 4;
     const StencilEntry *ent = P.stencil + p * P.ent_stride;
     const T *mass = static_cast<const T *>(P.mass);
-    const T *mpd = static_cast<const T *>(P.mp);
     for (;;) {
         const int item = pull_item(P.counter, &s_item);
         if (item >= P.n_items) break;
@@ -296,15 +417,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) mp_kernel(KP
             const int cz = cz0 + 2 * half;
             const int ax = 2 * cx + px, ay = 2 * cy + py, az = 2 * cz + pz;
             const int base = cx + P.py * cy + P.pz * cz;
-            const int tpi = parity_index(ax, ay, az);
-            const T *own = mpd + size_t(ti.mp_row) * NMP * NCELL + tpi;
-            const T dAx = own[0], dAy = own[NCELL], dAz = own[2 * NCELL];
-            Acc<T, 20> L;
+            T dA[3], a3A[7];
+            load_target<T>(P, ti.mp_row, parity_index(ax, ay, az), dA, a3A);
+            Acc<T, 16> L;
+            Acc<T, 3> S;
             L.zero();
-            T S1[3] = {T(0), T(0), T(0)};
-            T S2[15];
-#pragma unroll
-            for (int q = 0; q < 15; ++q) S2[q] = T(0);
+            S.zero();
             // well-separated sources: refined (full moments) or leaf (mass)
             for (int e0 = 0; e0 < P.n_far; e0 += kChunk) {
                 const int e1 = min(e0 + kChunk, P.n_far);
@@ -313,48 +431,37 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) mp_kernel(KP
                     int slot, pi;
                     source_cell(ax, ay, az, E.x, E.y, E.z, slot, pi);
                     const int row = s_row[slot];
-                    T m0, dB[3] = {T(0), T(0), T(0)}, A2[6], A3[10];
+                    Src<T> src;
                     if (row >= 0) {
-                        load_source<T>(P, s_nbr[slot], row, pi, m0, dB, A2, A3);
+                        load_source<T>(P, row, pi, src);
                     } else {
-                        m0 = W[base + E.w];
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) A2[q] = T(0);
-#pragma unroll
-                        for (int q = 0; q < 10; ++q) A3[q] = T(0);
+                        src.m0 = W[base + E.w];
+                        zero_moments<T>(src);
                     }
-                    accumulate_mp<T, true>(dAx - dB[0] - T(E.x), dAy - dB[1] - T(E.y),
-                                           dAz - dB[2] - T(E.z), m0, A2, A3, L, S1, S2);
+                    acc_mp<T, true>(dA[0] - src.d[0] - T(E.x), dA[1] - src.d[1] - T(E.y),
+                                    dA[2] - src.d[2] - T(E.z), src, a3A, L, S);
                 }
                 L.flush();
+                S.flush();
             }
             // near sources: leaf cells only (the window holds 0 elsewhere)
             for (int e0 = P.n_far; e0 < P.n_far + P.n_near; e0 += kChunk) {
                 const int e1 = min(e0 + kChunk, P.n_far + P.n_near);
                 for (int e = e0; e < e1; ++e) {
                     const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + e));
-                    const T m0 = W[base + E.w];
-                    accumulate_mp<T, false>(dAx - T(E.x), dAy - T(E.y), dAz - T(E.z), m0, nullptr,
-                                            nullptr, L, S1, S2);
+                    Src<T> src;
+                    src.m0 = W[base + E.w];
+                    acc_mp<T, false>(dA[0] - T(E.x), dA[1] - T(E.y), dA[2] - T(E.z), src, a3A,
+                                     L, S);
                 }
                 L.flush();
+                S.flush();
             }
             const int cell = ax + 8 * ay + 64 * az;
+            store_target<T>(P, node, cell, L);
 #pragma unroll
-            for (int k = 0; k < 20; ++k) store_L<T>(P, node, k, cell, L.hi[k], L.lo[k]);
-            // correction, finished in double:
-            //   dL1_i = S1_i - (1/M0_A) sum_q A3_A,q S2_(i,q)
-            const double m0A = double(mass[size_t(node) * NCELL + tpi]);
-            double A3A[10];
-#pragma unroll
-            for (int q = 0; q < 10; ++q) A3A[q] = double(own[(9 + q) * NCELL]);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                double s = 0.0;
-#pragma unroll
-                for (int q = 0; q < 10; ++q) s += A3A[q] * double(S2[r4_of(i, q)]);
-                P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = double(S1[i]) - s / m0A;
-            }
+            for (int i = 0; i < 3; ++i)
+                P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(S, i);
         }
         __syncthreads();
     }
@@ -469,7 +576,7 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
 
 // ------------------------------------------------------------ mx_kernel
 // Leaf target, refined sources (monopole<-multipole): orders 0-1 and the
-// correction S1 (the target has no third moment).  Adds to what mono_kernel
+// correction (the target has no third moment).  Adds to what mono_kernel
 // stored for the same node, so it runs after it on the same stream.  Work
 // items are node halves (z < 4, z >= 4); a host table gives, per parity,
 // half and stencil entry, the neighbour slots its sources can fall in, so a
@@ -501,8 +608,9 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
         const int cz = cz0 + 2 * half;
         const int ax = 2 * cx + px, ay = 2 * cy + py, az = 2 * cz + pz;
         Acc<T, 4> L;
+        Acc<T, 3> S;
         L.zero();
-        T S1[3] = {T(0), T(0), T(0)};
+        S.zero();
         int done = 0;
         for (int e = 0; e < n_ent; ++e) {
             if (!(__ldg(&smask[e]) & rmask)) continue;
@@ -510,37 +618,22 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
             int slot, pi;
             source_cell(ax, ay, az, E.x, E.y, E.z, slot, pi);
             const int row = s_row[slot];
-            T m0 = T(0), dB[3] = {T(0), T(0), T(0)}, A2[6], A3[10];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) A2[q] = T(0);
-#pragma unroll
-            for (int q = 0; q < 10; ++q) A3[q] = T(0);
-            if (row >= 0) load_source<T>(P, s_nbr[slot], row, pi, m0, dB, A2, A3);
-            DTensors<T, true> D;
-            D.eval(-T(E.x) - dB[0], -T(E.y) - dB[1], -T(E.z) - dB[2]);
-            T l0 = m0 * D.D0;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) l0 += A2[q] * D.D2[q];
-#pragma unroll
-            for (int q = 0; q < 10; ++q) l0 -= A3[q] * D.D3[q];
-            L.part[0] -= l0;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                T l1 = m0 * D.D1[i];
-#pragma unroll
-                for (int q = 0; q < 6; ++q) l1 += A2[q] * D.D3[r3_of(i, q)];
-                L.part[1 + i] -= l1;
-                T sacc = T(0);
-#pragma unroll
-                for (int q = 0; q < 10; ++q) sacc += A3[q] * D.D4[r4_of(i, q)];
-                S1[i] += sacc;
+            Src<T> src;
+            if (row >= 0) {
+                load_source<T>(P, row, pi, src);
+            } else {
+                src.m0 = T(0);
+                zero_moments<T>(src);
             }
+            acc_mx<T>(-T(E.x) - src.d[0], -T(E.y) - src.d[1], -T(E.z) - src.d[2], src, L, S);
             if (++done == kChunk) {
                 L.flush();
+                S.flush();
                 done = 0;
             }
         }
         L.flush();
+        S.flush();
         const int cell = ax + 8 * ay + 64 * az;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -558,7 +651,7 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
             }
         }
 #pragma unroll
-        for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = double(S1[i]);
+        for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(S, i);
         __syncthreads();
     }
 }
@@ -576,25 +669,22 @@ constexpr int kRootGroups = NCELL / 32;
 template <typename T>
 __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
 {
-    constexpr int NV = 20 + 3 + 15;                 // L, S1, S2
+    constexpr int NV = 16 + 3;                      // L (traceless), S
     __shared__ T sh_hi[kRootSlices][NV][32];
-    __shared__ T sh_lo[kRootSlices][sizeof(T) == 4 ? 20 : 1][32];   // float only
+    __shared__ T sh_lo[kRootSlices][sizeof(T) == 4 ? NV : 1][32];   // float only
     const int node = P.list[blockIdx.x];
     const NodeInfo ti = P.info[node];
     const bool leaf = ti.leaf_row >= 0;
     const T *mass = static_cast<const T *>(P.mass);
-    const T *mpd = static_cast<const T *>(P.mp);
     const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
     const int cell = blockIdx.y * 32 + lane;
     const int ax = cell & 7, ay = (cell >> 3) & 7, az = cell >> 6;
-    const int tpi = parity_index(ax, ay, az);
-    T dA[3] = {T(0), T(0), T(0)};
-    if (!leaf)
-        for (int a = 0; a < 3; ++a) dA[a] = mpd[(size_t(ti.mp_row) * NMP + a) * NCELL + tpi];
-    Acc<T, 20> L;
+    T dA[3] = {T(0), T(0), T(0)}, a3A[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    if (!leaf) load_target<T>(P, ti.mp_row, parity_index(ax, ay, az), dA, a3A);
+    Acc<T, 16> L;
+    Acc<T, 3> S;
     L.zero();
-    T S1[3] = {T(0), T(0), T(0)}, S2[15];
-    for (int q = 0; q < 15; ++q) S2[q] = T(0);
+    S.zero();
     int done = 0;
     const int b0 = slice * (NCELL / kRootSlices);
     for (int b = b0; b < b0 + NCELL / kRootSlices; ++b) {
@@ -603,29 +693,38 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
         const bool far = P.theta2 * o2 > 1.0;
         if (b == cell || !(far || leaf)) continue;
         const int pi = parity_index(b & 7, (b >> 3) & 7, b >> 6);
-        T m0, dB[3] = {T(0), T(0), T(0)}, A2[6], A3[10];
-        for (int q = 0; q < 6; ++q) A2[q] = T(0);
-        for (int q = 0; q < 10; ++q) A3[q] = T(0);
-        if (!leaf) load_source<T>(P, node, ti.mp_row, pi, m0, dB, A2, A3);
-        else m0 = mass[size_t(node) * NCELL + pi];
-        accumulate_mp<T, true>(dA[0] - dB[0] - T(ox), dA[1] - dB[1] - T(oy), dA[2] - dB[2] - T(oz),
-                               m0, A2, A3, L, S1, S2);
+        Src<T> src;
+        if (!leaf) {
+            load_source<T>(P, ti.mp_row, pi, src);
+        } else {
+            src.m0 = mass[size_t(node) * NCELL + pi];
+            zero_moments<T>(src);
+        }
+        acc_mp<T, true>(dA[0] - src.d[0] - T(ox), dA[1] - src.d[1] - T(oy),
+                        dA[2] - src.d[2] - T(oz), src, a3A, L, S);
         if (++done == kChunk) {
             L.flush();
+            S.flush();
             done = 0;
         }
     }
     L.flush();
-    for (int k = 0; k < 20; ++k) {
+    S.flush();
+    for (int k = 0; k < 16; ++k) {
         sh_hi[slice][k][lane] = L.hi[k];
         if constexpr (sizeof(T) == 4) sh_lo[slice][k][lane] = L.lo[k];
     }
-    for (int i = 0; i < 3; ++i) sh_hi[slice][20 + i][lane] = S1[i];
-    for (int q = 0; q < 15; ++q) sh_hi[slice][23 + q][lane] = S2[q];
+    for (int i = 0; i < 3; ++i) {
+        sh_hi[slice][16 + i][lane] = S.hi[i];
+        if constexpr (sizeof(T) == 4) sh_lo[slice][16 + i][lane] = S.lo[i];
+    }
     __syncthreads();
     if (slice != 0) return;
-    const int nk = leaf ? 4 : 20;
-    for (int k = 0; k < nk; ++k) {
+    Acc<T, 16> F;
+    Acc<T, 3> FS;
+    F.zero();
+    FS.zero();
+    for (int k = 0; k < NV; ++k) {
         T hi = T(0), lo = T(0);
         for (int sl = 0; sl < kRootSlices; ++sl) {
             if constexpr (sizeof(T) == 4) {
@@ -637,25 +736,15 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
                 hi += sh_hi[sl][k][lane];
             }
         }
-        store_L<T>(P, node, k, cell, hi, lo);
+        if (k < 16) { F.hi[k] = hi; F.lo[k] = lo; }
+        else { FS.hi[k - 16] = hi; FS.lo[k - 16] = lo; }
     }
-    double s1[3] = {0.0, 0.0, 0.0}, s2[15];
-    for (int q = 0; q < 15; ++q) s2[q] = 0.0;
-    for (int sl = 0; sl < kRootSlices; ++sl) {
-        for (int i = 0; i < 3; ++i) s1[i] += double(sh_hi[sl][20 + i][lane]);
-        for (int q = 0; q < 15; ++q) s2[q] += double(sh_hi[sl][23 + q][lane]);
+    if (leaf) {
+        for (int k = 0; k < 4; ++k) store_L<T>(P, node, k, cell, F.hi[k], F.lo[k]);
+    } else {
+        store_target<T>(P, node, cell, F);
     }
-    double corr[3] = {s1[0], s1[1], s1[2]};
-    if (!leaf) {
-        const double m0A = double(mass[size_t(node) * NCELL + tpi]);
-        for (int i = 0; i < 3; ++i) {
-            double acc = 0.0;
-            for (int q = 0; q < 10; ++q)
-                acc += double(mpd[(size_t(ti.mp_row) * NMP + 9 + q) * NCELL + tpi]) * s2[r4_of(i, q)];
-            corr[i] -= acc / m0A;
-        }
-    }
-    for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = corr[i];
+    for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(FS, i);
 }
 
 // ---------------------------------------------------------- launching

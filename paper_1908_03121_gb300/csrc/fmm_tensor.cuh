@@ -116,6 +116,89 @@ struct DTensors {
     }
 };
 
+// The same tensors in traceless bases.  Every D^(n), n >= 2, is traceless in
+// each index pair, so only some components are independent:
+//   rank 2 (5): xx yy xy xz yz                     (zz = -xx - yy)
+//   rank 3 (7): xxx xxy xxz xyy xyz yyy yyz        (xzz = -xxx - xyy,
+//                                                   yzz = -xxy - yyy,
+//                                                   zzz = -xxz - yyz)
+// and contracting a traceless tensor T with a symmetric moment only sees the
+// moment's traceless part, which is stored in the matching basis:
+//   B2 = [A2xx - A2zz, A2yy - A2zz, A2xy, A2xz, A2yz],
+//   B3 = [A3xxx - A3xzz, A3xxy - A3yzz, A3xxz - A3zzz, A3xyy - A3xzz, A3xyz,
+//         A3yyy - A3yzz, A3yyz - A3zzz],
+// so that sum_q A2_q T_q = B2 . T(5) and sum_q A3_q T_q = B3 . T(7).
+// D4 enters only through the slices U_i = D4[i, basis-7 triples]; the twelve
+// components those need are the nine independent ones below plus
+// xxzz = -xxxx - xxyy, xyzz = -xxxy - xyyy, yyzz = -xxyy - yyyy.
+template <typename T>
+struct DTraceless {
+    T D0, D1[3];
+    T D2[5];                 // xx yy xy xz yz
+    T D3[9];                 // xxx xxy xxz xyy xyz yyy yyz | xzz yzz
+    T U[3][7];               // D4 slices for the B3 basis
+
+    template <bool WITH_D4>
+    __device__ __forceinline__ void eval(T x, T y, T z)
+    {
+        const T r2 = x * x + y * y + z * z;
+        const T ri = rsqrt_t<T>(r2);
+        const T ri2 = ri * ri;
+        const T d1 = -ri * ri2;
+        const T d2 = T(-3) * d1 * ri2;
+        const T d3 = T(-5) * d2 * ri2;
+        D0 = ri;
+        D1[0] = d1 * x; D1[1] = d1 * y; D1[2] = d1 * z;
+        const T xx = x * x, yy = y * y, xy = x * y, xz = x * z, yz = y * z;
+        D2[0] = d2 * xx + d1;
+        D2[1] = d2 * yy + d1;
+        D2[2] = d2 * xy;
+        D2[3] = d2 * xz;
+        D2[4] = d2 * yz;
+        const T d3x = d3 * x, d3y = d3 * y;
+        const T t2 = T(3) * d2;
+        D3[0] = d3x * xx + t2 * x;      // xxx
+        D3[1] = d3x * xy + d2 * y;      // xxy
+        D3[2] = d3x * xz + d2 * z;      // xxz
+        D3[3] = d3x * yy + d2 * x;      // xyy
+        D3[4] = d3x * yz;               // xyz
+        D3[5] = d3y * yy + t2 * y;      // yyy
+        D3[6] = d3y * yz + d2 * z;      // yyz
+        D3[7] = -(D3[0] + D3[3]);       // xzz
+        D3[8] = -(D3[1] + D3[5]);       // yzz
+        if (WITH_D4) {
+            const T d4 = T(-7) * d3 * ri2;
+            const T t3 = T(3) * d3, t6 = T(6) * d3;
+            const T d4xx = d4 * xx, d4yy = d4 * yy, d4xy = d4 * xy;
+            const T xxxx = d4xx * xx + t6 * xx + t2;
+            const T xxxy = d4xx * xy + t3 * xy;
+            const T xxxz = d4xx * xz + t3 * xz;
+            const T xxyy = d4xx * yy + d3 * (xx + yy) + d2;
+            const T xxyz = d4xx * yz + d3 * yz;
+            const T xyyy = d4xy * yy + t3 * xy;
+            const T xyyz = d4xy * yz + d3 * xz;
+            const T yyyy = d4yy * yy + t6 * yy + t2;
+            const T yyyz = d4yy * yz + t3 * yz;
+            const T xxzz = -(xxxx + xxyy), xyzz = -(xxxy + xyyy), yyzz = -(xxyy + yyyy);
+            // slices in the B3 basis (xxx xxy xxz xyy xyz yyy yyz)
+            U[0][0] = xxxx; U[0][1] = xxxy; U[0][2] = xxxz; U[0][3] = xxyy;
+            U[0][4] = xxyz; U[0][5] = xyyy; U[0][6] = xyyz;
+            U[1][0] = xxxy; U[1][1] = xxyy; U[1][2] = xxyz; U[1][3] = xyyy;
+            U[1][4] = xyyz; U[1][5] = yyyy; U[1][6] = yyyz;
+            U[2][0] = xxxz; U[2][1] = xxyz; U[2][2] = xxzz; U[2][3] = xyyz;
+            U[2][4] = xyzz; U[2][5] = yyyz; U[2][6] = yyzz;
+        }
+    }
+
+    // D3[i, B2 pair] for L1_i = sum_k B2_k D3slice(i, k)
+    __device__ __forceinline__ T d3slice(int i, int k) const
+    {
+        // i = x: xxx xyy xxy xxz xyz ; y: xxy yyy xyy xyz yyz ; z: xxz yyz xyz xzz yzz
+        constexpr int idx[3][5] = {{0, 3, 1, 2, 4}, {1, 5, 3, 4, 6}, {2, 6, 4, 7, 8}};
+        return D3[idx[i][k]];
+    }
+};
+
 // cell (x,y,z) of a node -> parity-split position
 __host__ __device__ __forceinline__ int parity_index(int x, int y, int z)
 {

@@ -251,8 +251,8 @@ __device__ __forceinline__ void block_sum8(double v[8], double (*sh)[8])
     }
 }
 
-// 128 threads per leaf node, 4 cells each (z, z+2, z+4, z+6 of one column)
-constexpr int kForceThreads = 128;
+// 64 threads per leaf node, one (x, y) column of 8 cells each
+constexpr int kForceThreads = 64;
 
 __global__ void __launch_bounds__(kForceThreads) forces_kernel(
     const NodeInfo *__restrict__ info, const int32_t *__restrict__ leaves,
@@ -267,12 +267,16 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
     const double h = levels[ni.level * LEVEL_FIELDS + LV_H];
     const double h3 = levels[ni.level * LEVEL_FIELDS + LV_H3];
     const double half = 0.5 * box_size;
+    const int x = threadIdx.x & 7, y = threadIdx.x >> 3;
+    // position from the box centre (the box corner cancels); x, y fixed per thread
+    const double X0 = (8.0 * ni.ix + x + 0.5) * h - half;
+    const double X1 = (8.0 * ni.iy + y + 0.5) * h - half;
+    const double Z0 = (8.0 * ni.iz + 0.5) * h - half;
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     float nf = 0.f, nt = 0.f;
 #pragma unroll
-    for (int r = 0; r < NCELL / kForceThreads; ++r) {
-        const int c = threadIdx.x + r * kForceThreads;
-        const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+    for (int z = 0; z < 8; ++z) {
+        const int c = threadIdx.x + 64 * z;
         const double m = rho[size_t(row) * NCELL + c] * h3;
         phi[size_t(row) * NCELL + c] = L64[(size_t(node) * NCOMP) * NCELL + c];
         double gv[3];
@@ -282,11 +286,9 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
                       dacc[(size_t(node) * 3 + a) * NCELL + c]);
             g[(size_t(row) * 3 + a) * NCELL + c] = gv[a];
         }
-        // position from the box centre (the box corner cancels)
-        const double X[3] = {(8.0 * ni.ix + x + 0.5) * h - half, (8.0 * ni.iy + y + 0.5) * h - half,
-                             (8.0 * ni.iz + z + 0.5) * h - half};
-        const double u[3] = {X[1] * gv[2] - X[2] * gv[1], X[2] * gv[0] - X[0] * gv[2],
-                             X[0] * gv[1] - X[1] * gv[0]};
+        const double X2 = Z0 + z * h;
+        const double u[3] = {X1 * gv[2] - X2 * gv[1], X2 * gv[0] - X0 * gv[2],
+                             X0 * gv[1] - X1 * gv[0]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             v[a] += m * gv[a];          // f = m g

@@ -37,16 +37,20 @@ __global__ void __launch_bounds__(512) p2m_kernel(const NodeInfo *__restrict__ i
 __device__ __forceinline__ void central_from_raw(double m0, const double d[3], const double S2[6],
                                                  const double S3[10], double M2[6], double M3[10])
 {
-    constexpr int I2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-    constexpr int I3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
-                               {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+    // the products m0 d_i d_j serve both orders
+    const double md[3] = {m0 * d[0], m0 * d[1], m0 * d[2]};
+    double mdd[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) M2[q] = S2[q] - m0 * d[I2[q][0]] * d[I2[q][1]];
+    for (int q = 0; q < 6; ++q) mdd[q] = md[i2_at(q, 0)] * d[i2_at(q, 1)];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) M2[q] = S2[q] - mdd[q];
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
-        const int a = I3[q][0], b = I3[q][1], c = I3[q][2];
-        M3[q] = S3[q] - (S2[r2_of(a, b)] * d[c] + S2[r2_of(a, c)] * d[b] + S2[r2_of(b, c)] * d[a]) +
-                2.0 * m0 * d[a] * d[b] * d[c];
+        const int a = i3_at(q, 0), b = i3_at(q, 1), c = i3_at(q, 2);
+        double v = fma(2.0 * mdd[r2_of(a, b)], d[c], S3[q]);
+        v = fma(-S2[r2_of(a, b)], d[c], v);
+        v = fma(-S2[r2_of(a, c)], d[b], v);
+        M3[q] = fma(-S2[r2_of(b, c)], d[a], v);
     }
 }
 

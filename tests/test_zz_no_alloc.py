@@ -21,6 +21,7 @@ from workloads import make_config, leaf_nodes
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
+NORM_TOL = 1e-6
 
 
 def leaf_table(desc):
@@ -52,10 +53,12 @@ def test_forces_noalloc_matches_fmm_forces(name, precision):
         assert torch.equal(phi, ref_phi)
         assert torch.equal(g, ref_g)
         got = tot.cpu().numpy()
-        # net force / torque sums relative to their normalisers, normalisers relative
+        # net force / torque sums relative to their normalisers; the two
+        # normalisers are built from float per-cell magnitudes, so they get the
+        # float tolerance the other force tests give them
         assert np.all(np.abs(got[:, 0:3] - ref_tot[:, 0:3]) <= FP64_TOL * ref_tot[:, 6:7])
         assert np.all(np.abs(got[:, 3:6] - ref_tot[:, 3:6]) <= FP64_TOL * ref_tot[:, 7:8])
-        np.testing.assert_allclose(got[:, 6:8], ref_tot[:, 6:8], rtol=FP64_TOL)
+        np.testing.assert_allclose(got[:, 6:8], ref_tot[:, 6:8], rtol=NORM_TOL)
     s.close()
 
 

@@ -245,7 +245,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------- ours
-def time_graph(torch, solver, steps, warmup, flush, stream, clocks=None):
+def time_graph(torch, solver, steps, warmup, flush, stream, clocks=None, label="timed_steps"):
     """Per-step device ms of graph replays; the L2 flush runs between steps,
     outside the events."""
     for _ in range(warmup):
@@ -256,12 +256,16 @@ def time_graph(torch, solver, steps, warmup, flush, stream, clocks=None):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if clocks:
         clocks.start()
+    # the NVTX range lets a profiler's launch list keep the timed steps only
+    # (ncu --nvtx --nvtx-include "<label>/")
+    torch.cuda.nvtx.range_push(label)
     for k in range(steps):
         flush()
         starts[k].record(stream)
         solver.replay()
         ends[k].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop() if clocks else None
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     return float(np.mean(ms)), ms, clk
@@ -413,7 +417,8 @@ def run_ours(args):
             s64.step()
             autotune.tune(s64)
             s64.capture()
-            ms64, _, _ = time_graph(torch, s64, args.fp64_steps, 1, flush, stream)
+            ms64, _, _ = time_graph(torch, s64, args.fp64_steps, 1, flush, stream,
+                                   label="fp64_steps")
             g64 = s64.g
             err = float((g_mixed - g64).abs().max() / g64.abs().max())
             tot64 = s64.totals.cpu().numpy()

@@ -197,21 +197,25 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
     }
 }
 
+// 64 threads per CTA, 8 CTAs per node, so that the few nodes of a coarse
+// level still spread their FP64 work over many SMs
+constexpr int kSliceThreads = 64;
+
 template <bool MIXED>
-__global__ void __launch_bounds__(512) l2l_kernel(const NodeInfo *__restrict__ info,
-                                                  const int32_t *__restrict__ nodes,
-                                                  const double *__restrict__ levels,
-                                                  const void *__restrict__ Lv,
-                                                  const float *__restrict__ Lc,
-                                                  const double *dL1,  // may alias dacc
-                                                  const double *__restrict__ com,
-                                                  double *__restrict__ L64, double *dacc,
-                                                  float *__restrict__ down, double lo_x,
-                                                  double lo_y, double lo_z)
+__global__ void __launch_bounds__(kSliceThreads) l2l_kernel(const NodeInfo *__restrict__ info,
+                                                            const int32_t *__restrict__ nodes,
+                                                            const double *__restrict__ levels,
+                                                            const void *__restrict__ Lv,
+                                                            const float *__restrict__ Lc,
+                                                            const double *dL1,  // may alias dacc
+                                                            const double *__restrict__ com,
+                                                            double *__restrict__ L64, double *dacc,
+                                                            float *__restrict__ down, double lo_x,
+                                                            double lo_y, double lo_z)
 {
-    const int node = nodes[blockIdx.x];
+    const int node = nodes[blockIdx.x >> 3];
     const NodeInfo ni = info[node];
-    const int c = threadIdx.x;
+    const int c = (blockIdx.x & 7) * kSliceThreads + threadIdx.x;
     if (MIXED) {
         const float *Lhi = static_cast<const float *>(Lv);
         if (ni.leaf_row >= 0)
@@ -336,12 +340,12 @@ cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L, cons
     if (r.count == 0) return cudaSuccess;
     const auto &c = t->cfg;
     if (c.precision == FMM_MIXED)
-        l2l_kernel<true><<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.lists + r.off,
+        l2l_kernel<true><<<unsigned(r.count * 8), kSliceThreads, 0, s>>>(t->dev.info, t->dev.lists + r.off,
                                                            t->dev.levels, L, Lc, dL1, com, L64, dacc,
                                                            t->dev.down, c.box_lo[0], c.box_lo[1],
                                                            c.box_lo[2]);
     else
-        l2l_kernel<false><<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.lists + r.off,
+        l2l_kernel<false><<<unsigned(r.count * 8), kSliceThreads, 0, s>>>(t->dev.info, t->dev.lists + r.off,
                                                             t->dev.levels, L, Lc, dL1, com, L64,
                                                             dacc, nullptr, c.box_lo[0], c.box_lo[1],
                                                             c.box_lo[2]);

@@ -660,9 +660,9 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
 // Level 1 holds one node per tree and every pair is a candidate: a refined
 // root evaluates its well-separated pairs, a leaf root all pairs.  The
 // 512 x 511 pairs of one root are spread over 16 CTAs of 32 targets, each
-// target's 512 sources over 4 warps; the 4 partial sums are folded in a
+// target's 512 sources over 8 warps; the 8 partial sums are folded in a
 // fixed order (deterministic).
-constexpr int kRootSlices = 4;
+constexpr int kRootSlices = 8;
 constexpr int kRootThreads = 32 * kRootSlices;
 constexpr int kRootGroups = NCELL / 32;
 
@@ -724,6 +724,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
     Acc<T, 3> FS;
     F.zero();
     FS.zero();
+#pragma unroll
     for (int k = 0; k < NV; ++k) {
         T hi = T(0), lo = T(0);
         for (int sl = 0; sl < kRootSlices; ++sl) {

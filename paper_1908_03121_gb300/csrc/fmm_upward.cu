@@ -59,16 +59,21 @@ __device__ __forceinline__ void central_from_raw(double m0, const double d[3], c
 //   M0 = sum m_c,  X = sum m_c X_c / M0,  s_c = X_c - X,
 //   M2_ij  = sum (M2c_ij + m_c s_i s_j),
 //   M3_ijk = sum (M3c_ijk + M2c_ij s_k + M2c_ik s_j + M2c_jk s_i + m_c s_i s_j s_k).
-__global__ void __launch_bounds__(512) m2m_kernel(const NodeInfo *__restrict__ info,
-                                                  const int32_t *__restrict__ children,
-                                                  const int32_t *__restrict__ nodes,
-                                                  const double *__restrict__ levels,
-                                                  double *__restrict__ M, double *__restrict__ com,
-                                                  double lo_x, double lo_y, double lo_z)
+// 64 threads per CTA, 8 CTAs per node: coarse levels have few nodes, and
+// spreading each node over 8 SMs keeps their FP64 work off a single SM
+constexpr int kSliceThreads = 64;
+
+__global__ void __launch_bounds__(kSliceThreads) m2m_kernel(const NodeInfo *__restrict__ info,
+                                                            const int32_t *__restrict__ children,
+                                                            const int32_t *__restrict__ nodes,
+                                                            const double *__restrict__ levels,
+                                                            double *__restrict__ M,
+                                                            double *__restrict__ com, double lo_x,
+                                                            double lo_y, double lo_z)
 {
-    const int node = nodes[blockIdx.x];
+    const int node = nodes[blockIdx.x >> 3];
     const NodeInfo ni = info[node];
-    const int c = threadIdx.x;
+    const int c = (blockIdx.x & 7) * kSliceThreads + threadIdx.x;
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
     const int k = (x >> 2) + 2 * (y >> 2) + 4 * (z >> 2);
     const int ch = children[node * 8 + k];
@@ -180,7 +185,8 @@ cudaError_t launch_m2m_level(const fmm_tree_s *t, int level, double *M, double *
 {
     const ListRange &r = t->plan.refined_at[size_t(level)];
     if (r.count == 0) return cudaSuccess;
-    m2m_kernel<<<unsigned(r.count), 512, 0, s>>>(t->dev.info, t->dev.children, t->dev.lists + r.off,
+    m2m_kernel<<<unsigned(r.count * 8), kSliceThreads, 0, s>>>(t->dev.info, t->dev.children,
+                                                               t->dev.lists + r.off,
                                                  t->dev.levels, M, com, t->cfg.box_lo[0],
                                                  t->cfg.box_lo[1], t->cfg.box_lo[2]);
     return cudaGetLastError();

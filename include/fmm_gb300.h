@@ -63,7 +63,17 @@ enum {
     FMM_ERR_NOMEM = -5               /* device or host allocation failed */
 };
 
-enum { FMM_FP64 = 0, FMM_MIXED = 1 };
+/* Precision of the same-level pass (the other passes are FP64 throughout):
+ *   FMM_FP64    double arithmetic;
+ *   FMM_MIXED   float contraction with two-sum compensated accumulation,
+ *               offsets from double centres of mass, the correction finished
+ *               in double; relative force error about 1e-7, net torque about
+ *               1e-9 of the total;
+ *   FMM_DFLOAT  conserving: every same-level operation in double-float
+ *               arithmetic (pairs of floats, about 48 bits, on the FP32
+ *               pipe), so that the pairwise cancellations behind momentum and
+ *               angular-momentum conservation hold to about 1e-13. */
+enum { FMM_FP64 = 0, FMM_MIXED = 1, FMM_DFLOAT = 2 };
 
 enum {
     FMM_FLAG_HOST_ONLY = 1,          /* plan on the host only; no CUDA calls */
@@ -84,7 +94,7 @@ typedef struct {
     double G;                        /* gravitational constant */
     double box_lo[3];                /* lower corner of every tree's domain */
     double box_size;                 /* edge of the cubic domain */
-    int32_t precision;               /* FMM_FP64 or FMM_MIXED (same-level pass) */
+    int32_t precision;               /* FMM_FP64, FMM_MIXED or FMM_DFLOAT */
     int32_t max_level;               /* deepest level allowed (1..20) */
     int32_t flags;                   /* FMM_FLAG_* */
     int32_t reserved;
@@ -110,7 +120,7 @@ typedef struct {
     int64_t M_bytes;                 /* double [n_nodes][20][512] */
     int64_t com_bytes;               /* double [n_nodes][3][512] */
     int64_t L_bytes;                 /* double or float [n_nodes][20][512] */
-    int64_t Lcomp_bytes;             /* float [n_nodes][20][512] (mixed), else 0 */
+    int64_t Lcomp_bytes;             /* float [n_nodes][20][512] (mixed, dfloat), else 0 */
     int64_t dL1_bytes;               /* double [n_nodes][3][512] */
     int64_t L64_bytes;               /* double [n_nodes][20][512] */
     int64_t phi_bytes;               /* double [n_leaf][512] */
@@ -192,17 +202,19 @@ int fmm_upward(fmm_tree_t tree, const double *rho, double *M, double *com,
  * Leaf targets only get orders 0 and 1 (nothing below them needs more).
  *   M, com: as written by fmm_upward (read).
  *   L:      device [n_nodes][20][512], written: double (FMM_FP64) or the
- *           float high part (FMM_MIXED).  Values are in level units: lengths
+ *           float high part (FMM_MIXED, FMM_DFLOAT).  Values are in level units: lengths
  *           in cell widths of the target's level and G factored out, i.e.
  *           L_physical^(n) = G h^-(n+1) L^(n).  Orders 2-3 of leaf nodes are
  *           not written.
- *   L_comp: FMM_MIXED: device float [n_nodes][20][512], the compensation
- *           (low) part, L = L + L_comp; FMM_FP64: ignored, may be NULL.
+ *   L_comp: FMM_MIXED, FMM_DFLOAT: device float [n_nodes][20][512], the
+ *           compensation (low) part, L = L + L_comp; FMM_FP64: ignored, may
+ *           be NULL.
  *   dL1:    device double [n_nodes][3][512], written, level units
  *           (dL1_physical = G h^-2 dL1).
  * Precision: FMM_FP64 evaluates in double; FMM_MIXED forms the offsets in
  * double, contracts in float with two-sum compensated accumulation, and
- * finishes the correction in double.
+ * finishes the correction in double; FMM_DFLOAT evaluates every step (offsets,
+ * derivative tensors, contraction, sums) in double-float.
  */
 int fmm_m2l(fmm_tree_t tree, const double *M, const double *com, void *L,
             float *L_comp, double *dL1, fmm_stream_t stream);
@@ -217,6 +229,9 @@ int fmm_m2l(fmm_tree_t tree, const double *M, const double *com, void *L,
  *            leaf nodes only components 0-3 are written.
  *   dL1_acc: device double [n_nodes][3][512], written, physical units.  It
  *            may be the same buffer as dL1.
+ * FMM_MIXED forms the shift increments (the k >= 1 terms) in float from float
+ * copies of the parent expansion; FMM_FP64 and FMM_DFLOAT shift in double,
+ * FMM_DFLOAT reading L as the double sum L + L_comp.
  */
 int fmm_downward(fmm_tree_t tree, const void *L, const float *L_comp,
                  const double *dL1, const double *com, double *L64,

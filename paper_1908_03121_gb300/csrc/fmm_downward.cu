@@ -59,11 +59,14 @@ __device__ __forceinline__ void shift_increments(const T P[20], const T d[3], T 
     }
 }
 
-// FP64 path: the whole re-centring in double
-template <int NMAX>
+// FP64 path: the whole re-centring in double.  The cell's own same-level
+// result is double (FP64), or the double sum of a (hi, lo) float pair
+// (double-float precision, PAIR).
+template <int NMAX, bool PAIR>
 __device__ __forceinline__ void l2l_cell_fp64(const NodeInfo &ni, int node, int c,
                                               const double *__restrict__ lv,
-                                              const double *__restrict__ Lv, const double *dL1,
+                                              const void *__restrict__ Lv,
+                                              const float *__restrict__ Lc, const double *dL1,
                                               const double *__restrict__ com,
                                               double *__restrict__ L64, double *dacc, double lo_x,
                                               double lo_y, double lo_z)
@@ -74,8 +77,12 @@ __device__ __forceinline__ void l2l_cell_fp64(const NodeInfo &ni, int node, int 
     const double sc[4] = {L[LV_S0], L[LV_S1], L[LV_S2], L[LV_S3]};
     double out[20];
 #pragma unroll
-    for (int k = 0; k < NK; ++k)
-        out[k] = Lv[(size_t(node) * NCOMP + k) * NCELL + c] * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
+    for (int k = 0; k < NK; ++k) {
+        const size_t idx = (size_t(node) * NCOMP + k) * NCELL + c;
+        const double own = PAIR ? double(static_cast<const float *>(Lv)[idx]) + double(Lc[idx])
+                                : static_cast<const double *>(Lv)[idx];
+        out[k] = own * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
+    }
     double corr[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc[1];
@@ -201,7 +208,8 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
 // level still spread their FP64 work over many SMs
 constexpr int kSliceThreads = 64;
 
-template <bool MIXED>
+// MODE: FMM_FP64, FMM_MIXED or FMM_DFLOAT (FP64 shift of a float-pair input)
+template <int MODE>
 __global__ void __launch_bounds__(kSliceThreads) l2l_kernel(const NodeInfo *__restrict__ info,
                                                             const int32_t *__restrict__ nodes,
                                                             const double *__restrict__ levels,
@@ -216,7 +224,7 @@ __global__ void __launch_bounds__(kSliceThreads) l2l_kernel(const NodeInfo *__re
     const int node = nodes[blockIdx.x >> 3];
     const NodeInfo ni = info[node];
     const int c = (blockIdx.x & 7) * kSliceThreads + threadIdx.x;
-    if (MIXED) {
+    if constexpr (MODE == FMM_MIXED) {
         const float *Lhi = static_cast<const float *>(Lv);
         if (ni.leaf_row >= 0)
             l2l_cell_mixed<1>(ni, node, c, info, levels, Lhi, Lc, dL1, com, L64, dacc, down, lo_x,
@@ -225,11 +233,13 @@ __global__ void __launch_bounds__(kSliceThreads) l2l_kernel(const NodeInfo *__re
             l2l_cell_mixed<3>(ni, node, c, info, levels, Lhi, Lc, dL1, com, L64, dacc, down, lo_x,
                               lo_y, lo_z);
     } else {
-        const double *L = static_cast<const double *>(Lv);
+        constexpr bool PAIR = MODE == FMM_DFLOAT;
         if (ni.leaf_row >= 0)
-            l2l_cell_fp64<1>(ni, node, c, levels, L, dL1, com, L64, dacc, lo_x, lo_y, lo_z);
+            l2l_cell_fp64<1, PAIR>(ni, node, c, levels, Lv, Lc, dL1, com, L64, dacc, lo_x, lo_y,
+                                   lo_z);
         else
-            l2l_cell_fp64<3>(ni, node, c, levels, L, dL1, com, L64, dacc, lo_x, lo_y, lo_z);
+            l2l_cell_fp64<3, PAIR>(ni, node, c, levels, Lv, Lc, dL1, com, L64, dacc, lo_x, lo_y,
+                                   lo_z);
     }
 }
 
@@ -339,16 +349,20 @@ cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L, cons
     const ListRange &r = t->plan.nodes_at[size_t(level)];
     if (r.count == 0) return cudaSuccess;
     const auto &c = t->cfg;
+    const unsigned grid = unsigned(r.count * 8);
+    const int32_t *nodes = t->dev.lists + r.off;
     if (c.precision == FMM_MIXED)
-        l2l_kernel<true><<<unsigned(r.count * 8), kSliceThreads, 0, s>>>(t->dev.info, t->dev.lists + r.off,
-                                                           t->dev.levels, L, Lc, dL1, com, L64, dacc,
-                                                           t->dev.down, c.box_lo[0], c.box_lo[1],
-                                                           c.box_lo[2]);
+        l2l_kernel<FMM_MIXED><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, L,
+                                                            Lc, dL1, com, L64, dacc, t->dev.down,
+                                                            c.box_lo[0], c.box_lo[1], c.box_lo[2]);
+    else if (c.precision == FMM_DFLOAT)
+        l2l_kernel<FMM_DFLOAT><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, L,
+                                                             Lc, dL1, com, L64, dacc, nullptr,
+                                                             c.box_lo[0], c.box_lo[1], c.box_lo[2]);
     else
-        l2l_kernel<false><<<unsigned(r.count * 8), kSliceThreads, 0, s>>>(t->dev.info, t->dev.lists + r.off,
-                                                            t->dev.levels, L, Lc, dL1, com, L64,
-                                                            dacc, nullptr, c.box_lo[0], c.box_lo[1],
-                                                            c.box_lo[2]);
+        l2l_kernel<FMM_FP64><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, L,
+                                                           Lc, dL1, com, L64, dacc, nullptr,
+                                                           c.box_lo[0], c.box_lo[1], c.box_lo[2]);
     return cudaGetLastError();
 }
 

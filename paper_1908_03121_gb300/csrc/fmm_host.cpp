@@ -128,8 +128,8 @@ static int validate_config(const fmm_config *cfg)
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(cfg->box_lo[a])) return fail(FMM_ERR_INVALID_ARG, "box_lo not finite");
     if (!std::isfinite(cfg->G)) return fail(FMM_ERR_INVALID_ARG, "G not finite");
-    if (cfg->precision != FMM_FP64 && cfg->precision != FMM_MIXED)
-        return fail(FMM_ERR_INVALID_ARG, "precision must be FMM_FP64 or FMM_MIXED");
+    if (cfg->precision != FMM_FP64 && cfg->precision != FMM_MIXED && cfg->precision != FMM_DFLOAT)
+        return fail(FMM_ERR_INVALID_ARG, "precision must be FMM_FP64, FMM_MIXED or FMM_DFLOAT");
     if (cfg->max_level < 1 || cfg->max_level > 20)
         return fail(FMM_ERR_INVALID_ARG, "max_level must lie in 1..20");
     return FMM_OK;
@@ -248,6 +248,7 @@ static void build_stencils(fmm_tree_s *t)
     t->stencil.assign(size_t(8) * P.ent_stride, StencilEntry{0, 0, 0, 0});
     t->coef32.assign(size_t(8) * P.ent_stride * 4, 0.f);
     t->coef64.assign(size_t(8) * P.ent_stride * 4, 0.0);
+    t->coefdf.assign(size_t(8) * P.ent_stride * 8, 0.f);
     for (int p = 0; p < 8; ++p)
         for (size_t k = 0; k < lists[p].size(); ++k) {
             const StencilEntry &e = lists[p][k];
@@ -258,6 +259,9 @@ static void build_stencils(fmm_tree_s *t)
             for (int j = 0; j < 4; ++j) {
                 t->coef64[idx * 4 + j] = c[j];
                 t->coef32[idx * 4 + j] = float(c[j]);
+                // double-float (hi, lo) pairs
+                t->coefdf[idx * 8 + 2 * j] = float(c[j]);
+                t->coefdf[idx * 8 + 2 * j + 1] = float(c[j] - double(float(c[j])));
             }
         }
     P.stencil_union = 0;
@@ -443,7 +447,7 @@ static void free_device(fmm_tree_s *t)
     for (cudaEvent_t e : t->timer.ev) cudaEventDestroy(e);
     t->timer.ev.clear();
     DeviceTables &d = t->dev;
-    void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64,
+    void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.mass, d.mp, d.counters,
                     d.partials, d.down, d.slot_mask};
     for (void *p : ptrs)
@@ -458,11 +462,14 @@ static int upload_tree(fmm_tree_s *t)
     if ((rc = upload(&d.info, t->info)) || (rc = upload(&d.children, t->children)) ||
         (rc = upload(&d.nbr, t->nbr)) || (rc = upload(&d.lists, t->lists)) ||
         (rc = upload(&d.stencil, t->stencil)) || (rc = upload(&d.coef32, t->coef32)) ||
-        (rc = upload(&d.coef64, t->coef64)) || (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||
+        (rc = upload(&d.coef64, t->coef64)) || (rc = upload(&d.coefdf, t->coefdf)) ||
+        (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||
         (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)) || (rc = upload(&d.levels, t->levels)) ||
         (rc = upload(&d.slot_mask, t->slot_mask)))
         return rc;
-    size_t es = t->cfg.precision == FMM_MIXED ? sizeof(float) : sizeof(double);
+    // packed masses and moments: float (mixed), (hi, lo) float pairs (dfloat), double
+    size_t es = t->cfg.precision == FMM_MIXED ? sizeof(float) : 2 * sizeof(float);
+    static_assert(2 * sizeof(float) == sizeof(double), "packed element sizes");
     size_t mass_b = size_t(t->n) * NCELL * es;
     size_t mp_b = size_t(std::max<int64_t>(t->n_refined, 1)) * NMP * NCELL * es;
     size_t part_b = size_t(std::max<int64_t>(t->n_leaf, 1)) * 8 * sizeof(double);
@@ -598,7 +605,7 @@ int fmm_get_sizes(fmm_tree_t t, fmm_sizes *o)
     o->max_level = t->max_level;
     o->precision = t->cfg.precision;
     int64_t per = int64_t(NCELL) * 8;
-    bool mixed = t->cfg.precision == FMM_MIXED;
+    bool mixed = t->cfg.precision != FMM_FP64;     // float (hi, lo) Taylor coefficients
     o->rho_bytes = t->n_leaf * per;
     o->M_bytes = t->n * NCOMP * per;
     o->com_bytes = t->n * 3 * per;
@@ -685,8 +692,8 @@ int fmm_m2l(fmm_tree_t t, const double *M, const double *com, void *L, float *L_
     int rc = check_device_tree(t);
     if (rc) return rc;
     if (!M || !com || !L || !dL1) return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
-    if (t->cfg.precision == FMM_MIXED && !L_comp)
-        return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED");
+    if (t->cfg.precision != FMM_FP64 && !L_comp)
+        return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED and FMM_DFLOAT");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     timing_begin(t, FMM_K_PACK, s);
     cudaError_t e = launch_pack(t, M, com, s);
@@ -704,8 +711,8 @@ int fmm_downward(fmm_tree_t t, const void *L, const float *L_comp, const double 
     int rc = check_device_tree(t);
     if (rc) return rc;
     if (!L || !dL1 || !com || !L64 || !dL1_acc) return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
-    if (t->cfg.precision == FMM_MIXED && !L_comp)
-        return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED");
+    if (t->cfg.precision != FMM_FP64 && !L_comp)
+        return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED and FMM_DFLOAT");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (int lev = 1; lev <= t->max_level; ++lev) {
         if (t->plan.nodes_at[size_t(lev)].count == 0) continue;

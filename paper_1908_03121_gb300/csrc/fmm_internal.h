@@ -61,6 +61,7 @@ struct DeviceTables {
     StencilEntry *stencil = nullptr; // [8][ent_stride]
     float *coef32 = nullptr;         // [8][ent_stride][4] monopole coefficients
     double *coef64 = nullptr;        // [8][ent_stride][4]
+    float *coefdf = nullptr;         // [8][ent_stride][4][hi, lo]
     int32_t *tree_leaf_off = nullptr;   // [n_trees + 1]
     int32_t *tree_leaf_rows = nullptr;  // [n_leaf]
     double *levels = nullptr;        // [max_level + 1][LEVEL_FIELDS]
@@ -123,6 +124,7 @@ struct fmm_tree_s {
     std::vector<fmm::StencilEntry> stencil;
     std::vector<float> coef32;
     std::vector<double> coef64;
+    std::vector<float> coefdf;
     std::vector<int32_t> tree_leaf_off, tree_leaf_rows;
     std::vector<double> levels;
     std::vector<int32_t> slot_mask;

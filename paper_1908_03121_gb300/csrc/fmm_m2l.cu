@@ -32,7 +32,12 @@
 // (packed as offsets from the cell centre, in cell widths), the contraction
 // runs in float with per-chunk sums folded into (hi, lo) pairs by TwoSum, and
 // the correction's compensated sum is stored and carried down in double.
+// Conserving precision: the same kernels instantiated on dfloat (pairs of
+// floats, fmm_dfloat.cuh) evaluate offsets, derivative tensors, contraction
+// and sums in double-float, so each pair's contributions to A and to B cancel
+// in momentum and angular momentum to about 1e-13, as in FP64.
 #include <cstdio>
+#include <type_traits>
 
 #include "fmm_internal.h"
 #include "fmm_tensor.cuh"
@@ -40,6 +45,22 @@
 namespace fmm {
 
 namespace {
+
+// element types of the three precisions: float (mixed), dfloat (conserving),
+// double (FP64)
+template <typename T> constexpr bool kF32 = std::is_same<T, float>::value;
+template <typename T> constexpr bool kDF = std::is_same<T, dfloat>::value;
+
+template <typename T>
+__device__ __forceinline__ T ldg_t(const T *p)
+{
+    if constexpr (kDF<T>) {
+        const float2 f = __ldg(reinterpret_cast<const float2 *>(p));
+        return dfloat(f.x, f.y);
+    } else {
+        return __ldg(p);
+    }
+}
 
 constexpr int kThreads = 256;   // 8 warps = the 8 child parities
 constexpr int kChunk = 16;      // stencil entries per compensated chunk
@@ -145,7 +166,7 @@ __device__ __forceinline__ void stage_window(T *W, const int *s_nbr, const int *
             const int lz = bz & 7;
             T v = T(0);
             if (s_leaf[slot])
-                v = __ldg(mass + size_t(s_nbr[slot]) * NCELL + pxy + 256 * (lz & 1) + 16 * (lz >> 1));
+                v = ldg_t(mass + size_t(s_nbr[slot]) * NCELL + pxy + 256 * (lz & 1) + 16 * (lz >> 1));
             W[wxy + 4 * (uz & 1) * P.sub_stride + P.pz * (uz >> 1)] = v;
         }
     }
@@ -185,7 +206,7 @@ struct Acc {
     {
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            if constexpr (sizeof(T) == 4) {
+            if constexpr (kF32<T>) {
                 float s, e;
                 two_sum(hi[k], part[k], s, e);
                 hi[k] = s;
@@ -198,50 +219,90 @@ struct Acc {
     }
 };
 
-// store component k of a target cell: level units, (hi, lo) for float
+// double-float: every term already lands in a double-float running sum,
+// so there is nothing to fold
+template <int N>
+struct Acc<dfloat, N> {
+    dfloat part[N];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) part[k] = dfloat(0.f);
+    }
+    __device__ __forceinline__ void flush() {}
+};
+
+// the (hi, lo) value of accumulator k
+template <typename T, int N>
+__device__ __forceinline__ T acc_hi(const Acc<T, N> &a, int k) { return a.hi[k]; }
+template <int N>
+__device__ __forceinline__ dfloat acc_hi(const Acc<dfloat, N> &a, int k) { return a.part[k]; }
+template <typename T, int N>
+__device__ __forceinline__ T acc_lo(const Acc<T, N> &a, int k) { return a.lo[k]; }
+template <int N>
+__device__ __forceinline__ dfloat acc_lo(const Acc<dfloat, N> &, int) { return dfloat(0.f); }
+
+// store component k of a target cell: level units; (hi, lo) float pairs for
+// float (renormalised) and double-float (lo is zero there), else double
 template <typename T>
 __device__ __forceinline__ void store_L(const KParams &P, int node, int k, int cell, T hi, T lo)
 {
     const size_t idx = (size_t(node) * NCOMP + k) * NCELL + cell;
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (kF32<T>) {
         // renormalise so that |lo| <= ulp(hi)/2
         float s = hi + lo;
         float e = lo - (s - hi);
         static_cast<float *>(P.L)[idx] = s;
         P.Lc[idx] = e;
+    } else if constexpr (kDF<T>) {
+        static_cast<float *>(P.L)[idx] = hi.hi;
+        P.Lc[idx] = hi.lo;
     } else {
         static_cast<double *>(P.L)[idx] = hi;
     }
 }
 
 // store -(a + b) for a traceless-dependent component
-template <typename T, int N>
+template <typename T>
 __device__ __forceinline__ void store_neg_sum(const KParams &P, int node, int k, int cell,
-                                              const Acc<T, N> &L, int a, int b)
+                                              const T hi[16], const T lo[16], int a, int b)
 {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (kF32<T>) {
         float s, e;
-        two_sum(L.hi[a], L.hi[b], s, e);
-        store_L<T>(P, node, k, cell, -s, -(L.lo[a] + L.lo[b] + e));
+        two_sum(hi[a], hi[b], s, e);
+        store_L<T>(P, node, k, cell, -s, -(lo[a] + lo[b] + e));
     } else {
-        store_L<T>(P, node, k, cell, -(L.hi[a] + L.hi[b]), T(0));
+        store_L<T>(P, node, k, cell, -(hi[a] + hi[b]), T(0));
     }
 }
 
-// the 16 traceless accumulators of a multipole target -> 20 stored components
-// accumulators: 0 L0 | 1-3 L1 | 4-8 L2 (xx yy xy xz yz) | 9-15 L3 (xxx xxy
+// the 16 traceless values of a multipole target -> 20 stored components
+// values: 0 L0 | 1-3 L1 | 4-8 L2 (xx yy xy xz yz) | 9-15 L3 (xxx xxy
 // xxz xyy xyz yyy yyz)
+template <typename T>
+__device__ __forceinline__ void store_target_values(const KParams &P, int node, int cell,
+                                                    const T hi[16], const T lo[16])
+{
+    constexpr int direct[16] = {0, 1, 2, 3, 4, 7, 5, 6, 8, 10, 11, 12, 13, 14, 16, 17};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) store_L<T>(P, node, direct[k], cell, hi[k], lo[k]);
+    store_neg_sum<T>(P, node, 9, cell, hi, lo, 4, 5);      // zz  = -(xx + yy)
+    store_neg_sum<T>(P, node, 15, cell, hi, lo, 9, 12);    // xzz = -(xxx + xyy)
+    store_neg_sum<T>(P, node, 18, cell, hi, lo, 10, 14);   // yzz = -(xxy + yyy)
+    store_neg_sum<T>(P, node, 19, cell, hi, lo, 11, 15);   // zzz = -(xxz + yyz)
+}
+
 template <typename T>
 __device__ __forceinline__ void store_target(const KParams &P, int node, int cell,
                                              const Acc<T, 16> &L)
 {
-    constexpr int direct[16] = {0, 1, 2, 3, 4, 7, 5, 6, 8, 10, 11, 12, 13, 14, 16, 17};
+    T hi[16], lo[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) store_L<T>(P, node, direct[k], cell, L.hi[k], L.lo[k]);
-    store_neg_sum<T, 16>(P, node, 9, cell, L, 4, 5);      // zz  = -(xx + yy)
-    store_neg_sum<T, 16>(P, node, 15, cell, L, 9, 12);    // xzz = -(xxx + xyy)
-    store_neg_sum<T, 16>(P, node, 18, cell, L, 10, 14);   // yzz = -(xxy + yyy)
-    store_neg_sum<T, 16>(P, node, 19, cell, L, 11, 15);   // zzz = -(xxz + yyz)
+    for (int k = 0; k < 16; ++k) {
+        hi[k] = acc_hi(L, k);
+        lo[k] = acc_lo(L, k);
+    }
+    store_target_values<T>(P, node, cell, hi, lo);
 }
 
 // packed data of one source cell (level units)
@@ -253,9 +314,14 @@ struct Src {
 template <typename T>
 __device__ __forceinline__ void load4(const T *p, T v[4])
 {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (kF32<T>) {
         const float4 f = __ldg(reinterpret_cast<const float4 *>(p));
         v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+    } else if constexpr (kDF<T>) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        v[0] = dfloat(a.x, a.y); v[1] = dfloat(a.z, a.w);
+        v[2] = dfloat(b.x, b.y); v[3] = dfloat(b.z, b.w);
     } else {
         const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
         const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
@@ -383,17 +449,21 @@ __device__ __forceinline__ void load_target(const KParams &P, int row, int pi, T
     for (int q = 0; q < 7; ++q) a3A[q] = own.B3[q] * im0;
 }
 
+__device__ __forceinline__ double to_double(float v) { return double(v); }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(dfloat v) { return v.to_double(); }
+
 template <typename T>
 __device__ __forceinline__ double acc_value(const Acc<T, 3> &S, int i)
 {
-    return double(S.hi[i]) + double(S.lo[i]);
+    return to_double(acc_hi(S, i)) + to_double(acc_lo(S, i));
 }
 
 // ------------------------------------------------------------ mp_kernel
 template <typename T>
 // float: two CTAs per SM (128 registers; the (hi, lo) pairs, touched once per
 // chunk, are what the register budget squeezes)
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) mp_kernel(KParams P)
+__global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *W = reinterpret_cast<T *>(smem_raw);
@@ -480,9 +550,14 @@ __device__ __forceinline__ void mono_entry(const T *W, int wstride, int base0, i
 {
     const int w = __ldg(&ent[e].woff);
     T c[4];
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (kF32<T>) {
         const float4 cc = __ldg(reinterpret_cast<const float4 *>(coef) + e);
         c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
+    } else if constexpr (kDF<T>) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(coef) + 2 * e);
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(coef) + 2 * e + 1);
+        c[0] = dfloat(a.x, a.y); c[1] = dfloat(a.z, a.w);
+        c[2] = dfloat(b.x, b.y); c[3] = dfloat(b.z, b.w);
     } else {
         const double2 c01 = __ldg(reinterpret_cast<const double2 *>(coef) + 2 * e);
         const double2 c23 = __ldg(reinterpret_cast<const double2 *>(coef) + 2 * e + 1);
@@ -561,8 +636,8 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
             B[b].flush();
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                store_L<T>(P, nodes[b], k, cell0, A[b].hi[k], A[b].lo[k]);
-                store_L<T>(P, nodes[b], k, cell1, B[b].hi[k], B[b].lo[k]);
+                store_L<T>(P, nodes[b], k, cell0, acc_hi(A[b], k), acc_lo(A[b], k));
+                store_L<T>(P, nodes[b], k, cell1, acc_hi(B[b], k), acc_lo(B[b], k));
             }
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -638,7 +713,7 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const size_t idx = (size_t(node) * NCOMP + k) * NCELL + cell;
-            if constexpr (sizeof(T) == 4) {
+            if constexpr (kF32<T>) {
                 float *Lh = static_cast<float *>(P.L);
                 float s, e;
                 two_sum(Lh[idx], L.hi[k], s, e);
@@ -646,6 +721,11 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
                 const float s2 = s + lo;
                 Lh[idx] = s2;
                 P.Lc[idx] = lo - (s2 - s);
+            } else if constexpr (kDF<T>) {
+                float *Lh = static_cast<float *>(P.L);
+                const dfloat v = dfloat(Lh[idx], P.Lc[idx]) + L.part[k];
+                Lh[idx] = v.hi;
+                P.Lc[idx] = v.lo;
             } else {
                 static_cast<double *>(P.L)[idx] += L.hi[k];
             }
@@ -671,7 +751,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
 {
     constexpr int NV = 16 + 3;                      // L (traceless), S
     __shared__ T sh_hi[kRootSlices][NV][32];
-    __shared__ T sh_lo[kRootSlices][sizeof(T) == 4 ? NV : 1][32];   // float only
+    __shared__ T sh_lo[kRootSlices][kF32<T> ? NV : 1][32];   // float only
     const int node = P.list[blockIdx.x];
     const NodeInfo ti = P.info[node];
     const bool leaf = ti.leaf_row >= 0;
@@ -711,24 +791,21 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
     L.flush();
     S.flush();
     for (int k = 0; k < 16; ++k) {
-        sh_hi[slice][k][lane] = L.hi[k];
-        if constexpr (sizeof(T) == 4) sh_lo[slice][k][lane] = L.lo[k];
+        sh_hi[slice][k][lane] = acc_hi(L, k);
+        if constexpr (kF32<T>) sh_lo[slice][k][lane] = acc_lo(L, k);
     }
     for (int i = 0; i < 3; ++i) {
-        sh_hi[slice][16 + i][lane] = S.hi[i];
-        if constexpr (sizeof(T) == 4) sh_lo[slice][16 + i][lane] = S.lo[i];
+        sh_hi[slice][16 + i][lane] = acc_hi(S, i);
+        if constexpr (kF32<T>) sh_lo[slice][16 + i][lane] = acc_lo(S, i);
     }
     __syncthreads();
     if (slice != 0) return;
-    Acc<T, 16> F;
-    Acc<T, 3> FS;
-    F.zero();
-    FS.zero();
+    T Fh[NV], Fl[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         T hi = T(0), lo = T(0);
         for (int sl = 0; sl < kRootSlices; ++sl) {
-            if constexpr (sizeof(T) == 4) {
+            if constexpr (kF32<T>) {
                 float sum, err;
                 two_sum(hi, sh_hi[sl][k][lane], sum, err);
                 hi = sum;
@@ -737,15 +814,16 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
                 hi += sh_hi[sl][k][lane];
             }
         }
-        if (k < 16) { F.hi[k] = hi; F.lo[k] = lo; }
-        else { FS.hi[k - 16] = hi; FS.lo[k - 16] = lo; }
+        Fh[k] = hi;
+        Fl[k] = lo;
     }
     if (leaf) {
-        for (int k = 0; k < 4; ++k) store_L<T>(P, node, k, cell, F.hi[k], F.lo[k]);
+        for (int k = 0; k < 4; ++k) store_L<T>(P, node, k, cell, Fh[k], Fl[k]);
     } else {
-        store_target<T>(P, node, cell, F);
+        store_target_values<T>(P, node, cell, Fh, Fl);
     }
-    for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(FS, i);
+    for (int i = 0; i < 3; ++i)
+        P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = to_double(Fh[16 + i]) + to_double(Fl[16 + i]);
 }
 
 // ---------------------------------------------------------- launching
@@ -765,7 +843,7 @@ struct Kernels {
         if ((e = cudaFuncSetAttribute(mono_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(2 * window_bytes))) != cudaSuccess)
             return e;
-        if (sizeof(T) == 4 &&
+        if (kF32<T> &&
             (e = cudaFuncSetAttribute(mono_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(4 * window_bytes))) != cudaSuccess)
             return e;
@@ -806,7 +884,9 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     P.info = d.info;
     P.nbr = d.nbr;
     P.stencil = d.stencil;
-    P.coef = sizeof(T) == 4 ? static_cast<const void *>(d.coef32) : static_cast<const void *>(d.coef64);
+    P.coef = kF32<T> ? static_cast<const void *>(d.coef32)
+             : kDF<T> ? static_cast<const void *>(d.coefdf)
+                      : static_cast<const void *>(d.coef64);
     P.n_far = Pl.n_far[0];
     P.n_near = Pl.n_near[0];
     P.ent_stride = Pl.ent_stride;
@@ -857,12 +937,12 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         K.n_items = int32_t(Pl.work_mono.count);
         K.counter = d.counters + Q_MONO;
         int nb = t->tuning.mono_subgrids;
-        if (nb != 1 && nb != 2 && nb != 4) nb = sizeof(T) == 4 ? 2 : 1;
-        if (sizeof(T) != 4 && nb == 4) nb = 2;
+        if (nb != 1 && nb != 2 && nb != 4) nb = kF32<T> ? 2 : 1;
+        if (!kF32<T> && nb == 4) nb = 2;
         timing_begin(t, FMM_K_MONOPOLE, s);
         e = nb == 1 ? launch_mono<T, 1>(K, wbytes, sms, cap, s)
             : nb == 2 ? launch_mono<T, 2>(K, wbytes, sms, cap, s)
-                      : launch_mono<T, sizeof(T) == 4 ? 4 : 2>(K, wbytes, sms, cap, s);
+                      : launch_mono<T, kF32<T> ? 4 : 2>(K, wbytes, sms, cap, s);
         timing_end(t, s);
         ++nl;
         if (e != cudaSuccess) return e;
@@ -883,27 +963,36 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     return cudaSuccess;
 }
 
+template <typename T>
+void launch_pack_t(const fmm_tree_s *t, const double *M, const double *com, cudaStream_t s)
+{
+    const auto &c = t->cfg;
+    pack_kernel<T><<<unsigned(t->n), 512, 0, s>>>(t->dev.info, t->dev.levels, M, com,
+                                                  static_cast<T *>(t->dev.mass),
+                                                  static_cast<T *>(t->dev.mp), c.box_lo[0],
+                                                  c.box_lo[1], c.box_lo[2]);
+}
+
 }  // namespace
 
 cudaError_t launch_pack(const fmm_tree_s *t, const double *M, const double *com, cudaStream_t s)
 {
-    const auto &c = t->cfg;
-    if (c.precision == FMM_MIXED)
-        pack_kernel<float><<<unsigned(t->n), 512, 0, s>>>(
-            t->dev.info, t->dev.levels, M, com, static_cast<float *>(t->dev.mass),
-            static_cast<float *>(t->dev.mp), c.box_lo[0], c.box_lo[1], c.box_lo[2]);
-    else
-        pack_kernel<double><<<unsigned(t->n), 512, 0, s>>>(
-            t->dev.info, t->dev.levels, M, com, static_cast<double *>(t->dev.mass),
-            static_cast<double *>(t->dev.mp), c.box_lo[0], c.box_lo[1], c.box_lo[2]);
+    switch (t->cfg.precision) {
+    case FMM_MIXED: launch_pack_t<float>(t, M, com, s); break;
+    case FMM_DFLOAT: launch_pack_t<dfloat>(t, M, com, s); break;
+    default: launch_pack_t<double>(t, M, com, s); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2l(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cudaStream_t s,
                        int *n_launches)
 {
-    if (t->cfg.precision == FMM_MIXED) return launch_all<float>(t, L, Lc, dL1, s, n_launches);
-    return launch_all<double>(t, L, Lc, dL1, s, n_launches);
+    switch (t->cfg.precision) {
+    case FMM_MIXED: return launch_all<float>(t, L, Lc, dL1, s, n_launches);
+    case FMM_DFLOAT: return launch_all<dfloat>(t, L, Lc, dL1, s, n_launches);
+    default: return launch_all<double>(t, L, Lc, dL1, s, n_launches);
+    }
 }
 
 }  // namespace fmm

@@ -11,6 +11,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fmm_dfloat.cuh"
+
 namespace fmm {
 
 // number of index orderings of each symmetric component
@@ -58,6 +60,7 @@ __host__ __device__ constexpr int i3_at(int q, int which)
 template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
+template <> __device__ __forceinline__ dfloat rsqrt_t<dfloat>(dfloat v) { return df_rsqrt(v); }
 
 // Derivative tensors of 1/|R| (Cartesian closed forms):
 //   D1_i = d1 R_i,  D2_ij = d2 R_i R_j + d1 delta_ij,

@@ -22,6 +22,8 @@ FMM_ERR_TIMEOUT = -4
 FMM_ERR_NOMEM = -5
 FMM_FP64 = 0
 FMM_MIXED = 1
+FMM_DFLOAT = 2
+PRECISIONS = {"fp64": FMM_FP64, "mixed": FMM_MIXED, "dfloat": FMM_DFLOAT}
 FMM_FLAG_HOST_ONLY = 1
 FMM_FLAG_TIMING = 2
 KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_multi", "l2l",
@@ -170,7 +172,7 @@ def fmm_build_tree(desc, theta, G=1.0, box_lo=(0.0, 0.0, 0.0), box_size=1.0,
     if d.ndim != 2 or d.shape[1] != 14:
         raise ValueError("descriptor array must be (n, 14) int32")
     if isinstance(precision, str):
-        precision = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
+        precision = PRECISIONS[precision]
     flags = (FMM_FLAG_HOST_ONLY if host_only else 0) | (FMM_FLAG_TIMING if timing else 0)
     cfg = FmmConfig(float(theta), float(G), (ctypes.c_double * 3)(*box_lo), float(box_size),
                     int(precision), int(max_level), flags, 0)
@@ -258,11 +260,14 @@ class Solver:
         self.tree = fmm_build_tree(desc, theta, G, box_lo, box_size, precision, timing=timing)
         s = self.tree.sizes
         n, nl, nt = s["n_nodes"], s["n_leaf"], s["n_trees"]
-        self.mixed = s["precision"] == FMM_MIXED
+        self.precision = s["precision"]
+        self.mixed = self.precision == FMM_MIXED
+        # float (hi, lo) Taylor coefficients in the mixed and double-float precisions
+        self.pair = self.precision != FMM_FP64
         f64 = dict(dtype=torch.float64, device=device)
         self.M = torch.zeros((n, NCOMP, NCELL), **f64)
         self.com = torch.zeros((n, 3, NCELL), **f64)
-        if self.mixed:
+        if self.pair:
             self.L = torch.zeros((n, NCOMP, NCELL), dtype=torch.float32, device=device)
             self.Lc = torch.zeros((n, NCOMP, NCELL), dtype=torch.float32, device=device)
         else:

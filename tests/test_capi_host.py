@@ -87,6 +87,12 @@ def test_sizes_report():
     assert s["M_bytes"] == 73 * 20 * 512 * 8
     assert s["L_bytes"] == 73 * 20 * 512 * 4 and s["Lcomp_bytes"] == s["L_bytes"]
     assert s["g_bytes"] == 64 * 3 * 512 * 8 and s["totals_bytes"] == 64
+    # the double-float precision keeps the same (hi, lo) float layout of L
+    s2 = F.fmm_build_tree(c["desc"], 0.5, precision="dfloat", host_only=True).sizes
+    assert s2["precision"] == B.FMM_DFLOAT
+    assert s2["L_bytes"] == s["L_bytes"] and s2["Lcomp_bytes"] == s["Lcomp_bytes"]
+    s3 = F.fmm_build_tree(c["desc"], 0.5, precision="fp64", host_only=True).sizes
+    assert s3["L_bytes"] == 73 * 20 * 512 * 8 and s3["Lcomp_bytes"] == 0
 
 
 def expect_error(code, desc, theta=0.5, **kw):

@@ -4,7 +4,9 @@ Small trees are compared element by element, stage by stage and end to end;
 the full-size workloads (in the launch configuration the benchmark times) are
 compared on sampled cells that the oracle computes one by one.  Bars: the
 FP64 path to relative 1e-12, the mixed path to relative force error 1e-6
-(max |g - g_ref| / max |g_ref|) and net torque 1e-12 of sum |x cross f|.
+(max |g - g_ref| / max |g_ref|), the double-float (conserving) path to
+relative 1e-12 (1e-11 on the full-size samples) with net force and torque
+1e-12 of sum |f| and sum |x cross f|.
 """
 
 import numpy as np
@@ -26,6 +28,15 @@ FORCE_TOL = 1e-6
 # mixed path conserves momentum only to about float epsilon times the pair
 # terms; this bound is that arithmetic's, not the 1e-12 target.
 MIXED_CONSERVATION = 1e-7
+# Double-float carries about 48 bits (unit roundoff 2^-48 ~ 3.6e-15 per
+# operation); a few hundred terms of a hundred operations each put the
+# same-level result near 1e-13 relative (measured up to 1.4e-13 on the small
+# trees).  On the full-size workloads the oracle itself rounds absolute
+# coordinates at 1e-12 (as for the FP64 path), hence the wider sampled bar.
+DFLOAT_TOL = 1e-12
+DFLOAT_TOL_FULL = 1e-11
+# the conservation target of the conserving precision
+DFLOAT_CONSERVATION = 1e-12
 ORDER_SLICES = [slice(0, 1), slice(1, 4), slice(4, 10), slice(10, 20)]
 
 
@@ -188,6 +199,22 @@ def test_m2l_parity_mixed(name):
 
 
 @pytest.mark.parametrize("name", SMALL)
+def test_m2l_parity_dfloat(name):
+    """Double-float precision: every same-level operation on float pairs."""
+    c, ref = oracle_solution(name)
+    s = F.Solver(c["desc"], c["theta"], precision="dfloat")
+    s.M.copy_(dev(ref["M"]))
+    s.com.copy_(dev(ref["com"]))
+    s.m2l()
+    torch.cuda.synchronize()
+    Llev = host(s.L).astype(np.float64) + host(s.Lc).astype(np.float64)
+    assert_L_close(level_to_phys(Llev, c["desc"]), ref["L"], c["desc"], DFLOAT_TOL)
+    h = widths(c["desc"])[:, None, None]
+    assert rel_err(host(s.dL1) * h ** -2, ref["dL1"]) <= DFLOAT_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("name", SMALL)
 def test_downward_and_forces_parity(name):
     """The oracle's same-level result in, GPU downward + forces out (FP64)."""
     c, ref = oracle_solution(name)
@@ -239,7 +266,21 @@ def test_end_to_end_mixed(name):
     s.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", SMALL)
+def test_end_to_end_dfloat(name):
+    """The conserving precision: oracle field to 1e-11, net force and torque
+    to 1e-12 of their normalisers."""
+    c, ref = oracle_solution(name)
+    s = solve_gpu(c, "dfloat")
+    assert rel_err(host(s.g), ref["g"]) <= DFLOAT_TOL
+    assert rel_err(host(s.phi), ref["phi"]) <= DFLOAT_TOL
+    tot = host(s.totals)
+    assert np.all(tree_force(tot) <= DFLOAT_CONSERVATION), tree_force(tot)
+    assert np.all(tree_torque(tot) <= DFLOAT_CONSERVATION), tree_torque(tot)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "dfloat"])
 def test_deterministic_and_graph_replay(precision):
     c, _ = oracle_solution("adaptive4")
     s = solve_gpu(c, precision)
@@ -256,14 +297,14 @@ def test_deterministic_and_graph_replay(precision):
     s.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "dfloat"])
 def test_tunings_agree_bitwise(precision):
     """Launch shapes change scheduling only: every tuning gives the same bits."""
     c, _ = oracle_solution("adaptive4")
     s = solve_gpu(c, precision)
     ref = None
     for nb in (1, 2, 4):
-        if precision == "fp64" and nb == 4:
+        if precision != "mixed" and nb == 4:
             continue
         for cap in (0, 1):
             F.fmm_set_tuning(s.tree, mono_subgrids=nb, ctas_per_sm=cap)
@@ -355,4 +396,11 @@ def test_full_size_sampled(name):
     tot = host(s.totals)
     assert np.all(tree_force(tot) <= MIXED_CONSERVATION), tree_force(tot)
     assert np.all(tree_torque(tot) <= MIXED_CONSERVATION), tree_torque(tot)
+    s.close()
+    # double-float (conserving) path
+    s = solve_gpu(c, "dfloat")
+    assert rel_err(host(s.g)[rows, :, cells], ref["g"]) <= DFLOAT_TOL_FULL
+    tot = host(s.totals)
+    assert np.all(tree_force(tot) <= DFLOAT_CONSERVATION), tree_force(tot)
+    assert np.all(tree_torque(tot) <= DFLOAT_CONSERVATION), tree_torque(tot)
     s.close()

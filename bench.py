@@ -59,6 +59,7 @@ def parse_args():
     p.add_argument("--workload", default="cfg5")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--dfloat-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -428,6 +429,24 @@ def run_ours(args):
                 "net_torque": float(np.max(np.linalg.norm(tot64[:, 3:6], axis=1) / tot64[:, 7]))}
             result["mixed_accuracy"] = {"force_err_vs_fp64_path": err, "net_torque": net_torque,
                                         "net_force": net_force}
+            # the conserving (double-float) precision on the same workload
+            if args.dfloat_steps > 0:
+                sdf = F.Solver(c["desc"], c["theta"], precision="dfloat")
+                sdf.rho.copy_(solver.rho)
+                sdf.step()
+                autotune.tune(sdf)
+                sdf.capture()
+                msdf, _, _ = time_graph(torch, sdf, args.dfloat_steps, 1, flush, stream,
+                                        label="dfloat_steps")
+                totdf = sdf.totals.cpu().numpy()
+                result["conserving_path"] = {
+                    "precision": "dfloat (float pairs on the FP32 pipe)",
+                    "value": interactions / (msdf / 1000.0), "unit": UNIT, "ms_per_step": msdf,
+                    "speedup_over_fp64": ms64 / msdf,
+                    "force_err_vs_fp64_path": float((sdf.g - g64).abs().max() / g64.abs().max()),
+                    "net_force": float(np.max(np.linalg.norm(totdf[:, 0:3], axis=1) / totdf[:, 6])),
+                    "net_torque": float(np.max(np.linalg.norm(totdf[:, 3:6], axis=1) / totdf[:, 7]))}
+                sdf.close()
             s64.close()
 
         if world == 1 and not args.no_cpu_baseline:

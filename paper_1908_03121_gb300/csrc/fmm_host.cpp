@@ -78,6 +78,15 @@ int sm_count_of_current_device()
     return n > 0 ? n : 1;
 }
 
+size_t max_smem_optin_of_current_device()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 48 * 1024;
+    return size_t(n);
+}
+
 static void timing_fold(const fmm_tree_s *t)
 {
     TimerState &T = t->timer;
@@ -199,6 +208,11 @@ static int validate_nodes(const fmm_node_desc *d, int64_t n, const fmm_config *c
 // ------------------------------------------------------------- stencils
 // Per child parity p: all offsets o whose parent offset floor((p+o)/2) is
 // not well separated, split into well-separated (far) and near offsets.
+// Reflecting o along the axes where p is odd maps parity 0's stencil onto
+// parity p's (floor((1+o)/2) = -floor(-o/2), and both tests depend on |.|
+// only), so every parity's list is parity 0's, reflected, in the same order:
+// entry k has the same distance, and the same monopole weights up to the
+// signs of the first-order ones, in every parity.
 static void build_stencils(fmm_tree_s *t)
 {
     Plan &P = t->plan;
@@ -209,39 +223,65 @@ static void build_stencils(fmm_tree_s *t)
     P.py = pad_to(P.sub, 12);
     P.pz = pad_to(P.sub * P.py, 16);
     P.sub_stride = P.sub * P.pz;
+    auto in_stencil = [&](const int pp[3], const int o[3]) {
+        int64_t po[3];
+        for (int a = 0; a < 3; ++a) po[a] = floordiv2(pp[a] + o[a]);
+        return !well_separated(theta, po[0], po[1], po[2]);
+    };
+    // window offset of the source relative to the lane base
+    auto entry = [&](const int pp[3], int ox, int oy, int oz) {
+        const int o[3] = {ox, oy, oz};
+        int u[3], q = 0;
+        for (int a = 0; a < 3; ++a) {
+            u[a] = pp[a] + o[a] + R;       // >= 0
+            q |= (u[a] & 1) << a;
+        }
+        const int woff = q * P.sub_stride + (u[0] >> 1) + P.py * (u[1] >> 1) + P.pz * (u[2] >> 1);
+        return StencilEntry{ox, oy, oz, woff};
+    };
     std::vector<char> in_union(size_t(2 * R + 1) * (2 * R + 1) * (2 * R + 1), 0);
     std::vector<StencilEntry> lists[8];
-    for (int p = 0; p < 8; ++p) {
-        int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
+    {
+        const int p0[3] = {0, 0, 0};
         std::vector<StencilEntry> far, nearv;
         for (int oz = -R; oz <= R; ++oz)
             for (int oy = -R; oy <= R; ++oy)
                 for (int ox = -R; ox <= R; ++ox) {
                     if (!ox && !oy && !oz) continue;
-                    int o[3] = {ox, oy, oz};
-                    int64_t po[3];
-                    for (int a = 0; a < 3; ++a) po[a] = floordiv2(pp[a] + o[a]);
-                    if (well_separated(theta, po[0], po[1], po[2])) continue;
-                    // window offset of the source relative to the lane base
-                    int u[3], q = 0;
-                    for (int a = 0; a < 3; ++a) {
-                        u[a] = pp[a] + o[a] + R;       // >= 0
-                        q |= (u[a] & 1) << a;
-                    }
-                    int woff = q * P.sub_stride + (u[0] >> 1) + P.py * (u[1] >> 1) + P.pz * (u[2] >> 1);
-                    StencilEntry e{ox, oy, oz, woff};
-                    (well_separated(theta, ox, oy, oz) ? far : nearv).push_back(e);
-                    in_union[size_t((oz + R) * (2 * R + 1) + (oy + R)) * (2 * R + 1) + (ox + R)] = 1;
+                    const int o[3] = {ox, oy, oz};
+                    if (!in_stencil(p0, o)) continue;
+                    (well_separated(theta, ox, oy, oz) ? far : nearv).push_back(entry(p0, ox, oy, oz));
                 }
-        P.n_far[p] = int(far.size());
-        P.n_near[p] = int(nearv.size());
-        lists[p] = far;
-        lists[p].insert(lists[p].end(), nearv.begin(), nearv.end());
+        for (int p = 0; p < 8; ++p) {
+            P.n_far[p] = int(far.size());
+            P.n_near[p] = int(nearv.size());
+        }
+        lists[0] = far;
+        lists[0].insert(lists[0].end(), nearv.begin(), nearv.end());
     }
-    // the kernels rely on every parity having the same far/near counts
-    // (a reflection maps one parity's stencil onto another's)
-    for (int p = 1; p < 8; ++p)
-        if (P.n_far[p] != P.n_far[0] || P.n_near[p] != P.n_near[0]) std::abort();
+    for (int p = 0; p < 8; ++p) {
+        const int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
+        if (p > 0) {
+            lists[p].clear();
+            for (const StencilEntry &e : lists[0])
+                lists[p].push_back(entry(pp, pp[0] ? -e.ox : e.ox, pp[1] ? -e.oy : e.oy,
+                                         pp[2] ? -e.oz : e.oz));
+        }
+        // the reflected list is exactly parity p's stencil
+        int64_t members = 0;
+        for (const StencilEntry &e : lists[p]) {
+            const int o[3] = {e.ox, e.oy, e.oz};
+            if (!in_stencil(pp, o)) std::abort();
+            in_union[size_t((e.oz + R) * (2 * R + 1) + (e.oy + R)) * (2 * R + 1) + (e.ox + R)] = 1;
+        }
+        for (int oz = -R; oz <= R; ++oz)
+            for (int oy = -R; oy <= R; ++oy)
+                for (int ox = -R; ox <= R; ++ox) {
+                    const int o[3] = {ox, oy, oz};
+                    if ((ox || oy || oz) && in_stencil(pp, o)) ++members;
+                }
+        if (members != int64_t(lists[p].size())) std::abort();
+    }
     int stride = 0;
     for (int p = 0; p < 8; ++p) stride = std::max(stride, int(lists[p].size()));
     P.ent_stride = (stride + 3) & ~3;

@@ -154,6 +154,7 @@ cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *
                           cudaStream_t s);
 
 int sm_count_of_current_device();
+size_t max_smem_optin_of_current_device();
 
 // set the calling thread's fmm_last_error() message
 void record_error(const std::string &msg);

@@ -145,14 +145,29 @@ __device__ __forceinline__ int pull_item(int32_t *counter, int *s_item)
 // cell u in [0, 8 + 2R)^3 holds the source at node-local position u - R, or 0
 // when that source is refined or absent.  Layout: parity sub-window
 // q = (ux&1) + 2(uy&1) + 4(uz&1), then (ux>>1) + py (uy>>1) + pz (uz>>1).
+// One (ux, uy) column per thread pass, z innermost; the parity index and the
+// window address both split into an (x, y) part and a z part.  The copies go
+// through cp.async (global -> shared without registers; sources that are
+// refined or absent are zero-filled by a zero source size), so every load of
+// the window is in flight at once.  The caller commits and waits.
 template <typename T>
-__device__ __forceinline__ void stage_window(T *W, const int *s_nbr, const int *s_leaf,
-                                             const T *__restrict__ mass, const KParams &P)
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element size");
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src),
+                 "n"(int(sizeof(T))), "r"(valid ? int(sizeof(T)) : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void stage_window_async(T *W, const int *s_nbr, const int *s_leaf,
+                                                   const T *__restrict__ mass, const KParams &P)
 {
     const int R = P.reach;
     const int E = 8 + 2 * R;
-    // one (ux, uy) column per thread pass, z innermost; the parity index and
-    // the window address both split into an (x, y) part and a z part
     for (int t = threadIdx.x; t < E * E; t += blockDim.x) {
         const int ux = t % E, uy = t / E;
         const int bx = ux - R + 8, by = uy - R + 8;           // >= 1
@@ -164,10 +179,10 @@ __device__ __forceinline__ void stage_window(T *W, const int *s_nbr, const int *
             const int bz = uz - R + 8;
             const int slot = sxy + 9 * (bz >> 3);
             const int lz = bz & 7;
-            T v = T(0);
-            if (s_leaf[slot])
-                v = ldg_t(mass + size_t(s_nbr[slot]) * NCELL + pxy + 256 * (lz & 1) + 16 * (lz >> 1));
-            W[wxy + 4 * (uz & 1) * P.sub_stride + P.pz * (uz >> 1)] = v;
+            const bool ok = s_leaf[slot] != 0;
+            const T *src = ok ? mass + size_t(s_nbr[slot]) * NCELL + pxy + 256 * (lz & 1) + 16 * (lz >> 1)
+                              : mass;
+            cp_async_elem<T>(W + wxy + 4 * (uz & 1) * P.sub_stride + P.pz * (uz >> 1), src, ok);
         }
     }
 }
@@ -481,7 +496,9 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P
         const NodeInfo ti = P.info[node];
         load_slots(node, P, s_nbr, s_leaf, s_row);
         __syncthreads();
-        stage_window<T>(W, s_nbr, s_leaf, mass, P);
+        stage_window_async<T>(W, s_nbr, s_leaf, mass, P);
+        cp_async_commit();
+        cp_async_wait_all();
         __syncthreads();
         for (int half = 0; half < 2; ++half) {
             const int cz = cz0 + 2 * half;
@@ -540,29 +557,42 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P
 // ---------------------------------------------------------- mono_kernel
 // Leaf target, leaf sources: R = -o exactly, so L0 += c0(o) m and
 // L1 += c1(o) m with per-offset weights c0 = -1/|o|, c1 = -o/|o|^3.
+// Every parity's stencil is parity 0's reflected along its odd axes, entry by
+// entry, so one weight table (parity 0's) serves all eight warps: a warp of
+// parity p accumulates with parity 0's first-order weights and flips the
+// signs of its L1 components along p's odd axes at the end (exact).  The
+// table and the per-parity window offsets sit in shared memory, loaded once
+// per CTA; every access to them is a warp-uniform broadcast.
 // Each pass takes NB sub-grids (consecutive in the cost-sorted queue), each
-// with its own staged window; every thread holds two target cells (z and
-// z+4 of one parity) per sub-grid, so each loaded weight feeds 2 NB cells.
+// with its own halo window, staged by cp.async so that every load of the
+// window is in flight at once; every thread holds two target cells (z and
+// z+4 of one parity) per sub-grid, so each weight feeds 2 NB cells.
+template <typename T>
+__device__ __forceinline__ void load4_shared(const T *p, T v[4])
+{
+    if constexpr (kF32<T>) {
+        const float4 f = *reinterpret_cast<const float4 *>(p);
+        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+    } else if constexpr (kDF<T>) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[0];
+        const float4 b = reinterpret_cast<const float4 *>(p)[1];
+        v[0] = dfloat(a.x, a.y); v[1] = dfloat(a.z, a.w);
+        v[2] = dfloat(b.x, b.y); v[3] = dfloat(b.z, b.w);
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
 template <typename T, int NB>
 __device__ __forceinline__ void mono_entry(const T *W, int wstride, int base0, int base1,
-                                           const StencilEntry *ent, const T *coef, int e,
+                                           const int *woff, const T *coef, int e,
                                            Acc<T, 4> (&A)[NB], Acc<T, 4> (&B)[NB])
 {
-    const int w = __ldg(&ent[e].woff);
+    const int w = woff[e];
     T c[4];
-    if constexpr (kF32<T>) {
-        const float4 cc = __ldg(reinterpret_cast<const float4 *>(coef) + e);
-        c[0] = cc.x; c[1] = cc.y; c[2] = cc.z; c[3] = cc.w;
-    } else if constexpr (kDF<T>) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(coef) + 2 * e);
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(coef) + 2 * e + 1);
-        c[0] = dfloat(a.x, a.y); c[1] = dfloat(a.z, a.w);
-        c[2] = dfloat(b.x, b.y); c[3] = dfloat(b.z, b.w);
-    } else {
-        const double2 c01 = __ldg(reinterpret_cast<const double2 *>(coef) + 2 * e);
-        const double2 c23 = __ldg(reinterpret_cast<const double2 *>(coef) + 2 * e + 1);
-        c[0] = c01.x; c[1] = c01.y; c[2] = c23.x; c[3] = c23.y;
-    }
+    load4_shared<T>(coef + 4 * e, c);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const T m0 = W[b * wstride + base0 + w];
@@ -575,21 +605,36 @@ __device__ __forceinline__ void mono_entry(const T *W, int wstride, int base0, i
     }
 }
 
+// dynamic shared memory of mono_kernel<T, NB>: NB windows, the weight table
+// of parity 0 and the window offsets of all parities
+template <typename T>
+size_t mono_smem_bytes(int nb, size_t window_bytes, int ent_stride)
+{
+    return nb * window_bytes + size_t(ent_stride) * 4 * sizeof(T) + size_t(8) * ent_stride * sizeof(int);
+}
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wstride = 8 * P.sub_stride;
     T *W = reinterpret_cast<T *>(smem_raw);
+    T *s_coef = W + NB * wstride;
+    int *s_woff = reinterpret_cast<int *>(s_coef + 4 * P.ent_stride);
     __shared__ int s_nbr[NB][27], s_leaf[NB][27], s_row[NB][27], s_item;
+    const int n_ent = P.n_far + P.n_near;
+    {
+        const T *gcoef = static_cast<const T *>(P.coef);          // parity 0 first
+        for (int i = threadIdx.x; i < 4 * n_ent; i += blockDim.x) s_coef[i] = ldg_t(gcoef + i);
+        for (int i = threadIdx.x; i < 8 * P.ent_stride; i += blockDim.x)
+            s_woff[i] = __ldg(&P.stencil[i].woff);
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = warp;
     const int px = p & 1, py = (p >> 1) & 1, pz = p >> 2;
     const int cx = lane & 3, cy = (lane >> 2) & 3, cz = lane >> 4;
-    const StencilEntry *ent = P.stencil + p * P.ent_stride;
-    const T *coef = static_cast<const T *>(P.coef) + size_t(p) * P.ent_stride * 4;
+    const int *woff = s_woff + p * P.ent_stride;
     const T *mass = static_cast<const T *>(P.mass);
-    const int n_ent = P.n_far + P.n_near;
-    const int wstride = 8 * P.sub_stride;
     const int base0 = cx + P.py * cy + P.pz * cz;
     const int base1 = base0 + 2 * P.pz;
     for (;;) {
@@ -606,7 +651,9 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
         __syncthreads();
 #pragma unroll
         for (int b = 0; b < NB; ++b)
-            if (nodes[b] >= 0) stage_window<T>(W + b * wstride, s_nbr[b], s_leaf[b], mass, P);
+            if (nodes[b] >= 0) stage_window_async<T>(W + b * wstride, s_nbr[b], s_leaf[b], mass, P);
+        cp_async_commit();
+        cp_async_wait_all();
         __syncthreads();
         Acc<T, 4> A[NB], B[NB];
 #pragma unroll
@@ -618,14 +665,14 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
         for (; e + kChunk <= n_ent; e += kChunk) {
 #pragma unroll
             for (int j = 0; j < kChunk; ++j)
-                mono_entry<T, NB>(W, wstride, base0, base1, ent, coef, e + j, A, B);
+                mono_entry<T, NB>(W, wstride, base0, base1, woff, s_coef, e + j, A, B);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 A[b].flush();
                 B[b].flush();
             }
         }
-        for (; e < n_ent; ++e) mono_entry<T, NB>(W, wstride, base0, base1, ent, coef, e, A, B);
+        for (; e < n_ent; ++e) mono_entry<T, NB>(W, wstride, base0, base1, woff, s_coef, e, A, B);
         const int ax = 2 * cx + px, ay = 2 * cy + py;
         const int cell0 = ax + 8 * ay + 64 * (2 * cz + pz);
         const int cell1 = cell0 + 64 * 4;
@@ -636,8 +683,12 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
             B[b].flush();
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                store_L<T>(P, nodes[b], k, cell0, acc_hi(A[b], k), acc_lo(A[b], k));
-                store_L<T>(P, nodes[b], k, cell1, acc_hi(B[b], k), acc_lo(B[b], k));
+                // first-order weights were parity 0's: undo the reflection
+                const bool flip = k > 0 && ((p >> (k - 1)) & 1);
+                const T ah = acc_hi(A[b], k), al = acc_lo(A[b], k);
+                const T bh = acc_hi(B[b], k), bl = acc_lo(B[b], k);
+                store_L<T>(P, nodes[b], k, cell0, flip ? -ah : ah, flip ? -al : al);
+                store_L<T>(P, nodes[b], k, cell1, flip ? -bh : bh, flip ? -bl : bl);
             }
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -827,28 +878,29 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
 }
 
 // ---------------------------------------------------------- launching
+// opt-in dynamic shared memory of a kernel, raised once to the largest size
+// asked for so far
+template <typename Kern>
+cudaError_t allow_smem(Kern k, size_t bytes, size_t &done)
+{
+    if (bytes <= done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) done = bytes;
+    return e;
+}
+
 template <typename T>
 struct Kernels {
-    static cudaError_t configure(size_t window_bytes)
+    static cudaError_t mp(size_t bytes)
     {
-        static size_t done_bytes = 0;
-        if (done_bytes >= window_bytes) return cudaSuccess;
-        cudaError_t e;
-        if ((e = cudaFuncSetAttribute(mp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(window_bytes))) != cudaSuccess)
-            return e;
-        if ((e = cudaFuncSetAttribute(mono_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(window_bytes))) != cudaSuccess)
-            return e;
-        if ((e = cudaFuncSetAttribute(mono_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(2 * window_bytes))) != cudaSuccess)
-            return e;
-        if (kF32<T> &&
-            (e = cudaFuncSetAttribute(mono_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(4 * window_bytes))) != cudaSuccess)
-            return e;
-        done_bytes = window_bytes;
-        return cudaSuccess;
+        static size_t done = 0;
+        return allow_smem(mp_kernel<T>, bytes, done);
+    }
+    template <int NB>
+    static cudaError_t mono(size_t bytes)
+    {
+        static size_t done = 0;
+        return allow_smem(mono_kernel<T, NB>, bytes, done);
     }
 };
 
@@ -868,9 +920,12 @@ int persistent_grid(Kern k, size_t smem, int64_t items, int sms, int cap_per_sm)
 template <typename T, int NB>
 cudaError_t launch_mono(const KParams &K, size_t wbytes, int sms, int cap, cudaStream_t s)
 {
+    const size_t bytes = mono_smem_bytes<T>(NB, wbytes, K.ent_stride);
+    cudaError_t e = Kernels<T>::template mono<NB>(bytes);
+    if (e != cudaSuccess) return e;
     const int64_t passes = (K.n_items + NB - 1) / NB;
-    const int g = persistent_grid(mono_kernel<T, NB>, NB * wbytes, passes, sms, cap);
-    mono_kernel<T, NB><<<g, kThreads, NB * wbytes, s>>>(K);
+    const int g = persistent_grid(mono_kernel<T, NB>, bytes, passes, sms, cap);
+    mono_kernel<T, NB><<<g, kThreads, bytes, s>>>(K);
     return cudaGetLastError();
 }
 
@@ -903,7 +958,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     P.slot_mask = d.slot_mask;
     const int cap = t->tuning.ctas_per_sm;
     const size_t wbytes = size_t(8) * Pl.sub_stride * sizeof(T);
-    cudaError_t e = Kernels<T>::configure(wbytes);
+    cudaError_t e = Kernels<T>::mp(wbytes);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d.counters, 0, 4 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
@@ -939,6 +994,9 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         int nb = t->tuning.mono_subgrids;
         if (nb != 1 && nb != 2 && nb != 4) nb = kF32<T> ? 2 : 1;
         if (!kF32<T> && nb == 4) nb = 2;
+        // fewer sub-grids per pass where their windows do not fit
+        const size_t smem_max = max_smem_optin_of_current_device();
+        while (nb > 1 && mono_smem_bytes<T>(nb, wbytes, Pl.ent_stride) > smem_max) nb /= 2;
         timing_begin(t, FMM_K_MONOPOLE, s);
         e = nb == 1 ? launch_mono<T, 1>(K, wbytes, sms, cap, s)
             : nb == 2 ? launch_mono<T, 2>(K, wbytes, sms, cap, s)

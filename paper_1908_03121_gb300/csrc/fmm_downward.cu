@@ -12,6 +12,7 @@
 // forces_kernel: phi = L0, g = -(L1 + dL1), f = m g, and fixed-order FP64
 // block sums of f and x cross f (plus the |f|, |x cross f| normalisers) per
 // leaf node; reduce_kernel folds those per tree.
+#include "fmm_convert.cuh"
 #include "fmm_internal.h"
 #include "fmm_tensor.cuh"
 
@@ -79,7 +80,7 @@ __device__ __forceinline__ void l2l_cell_fp64(const NodeInfo &ni, int node, int 
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
         const size_t idx = (size_t(node) * NCOMP + k) * NCELL + c;
-        const double own = PAIR ? double(static_cast<const float *>(Lv)[idx]) + double(Lc[idx])
+        const double own = PAIR ? pair_to_double(static_cast<const float *>(Lv)[idx], Lc[idx])
                                 : static_cast<const double *>(Lv)[idx];
         out[k] = own * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
     }
@@ -150,14 +151,12 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
     float offc[3] = {0.f, 0.f, 0.f};          // own centre-of-mass offset
     if (NMAX == 3) {
         const double h = L[LV_H];
-        offc[0] = float(com[(size_t(node) * 3 + 0) * NCELL + c] - (lo_x + (8.0 * ni.ix + x + 0.5) * h));
-        offc[1] = float(com[(size_t(node) * 3 + 1) * NCELL + c] - (lo_y + (8.0 * ni.iy + y + 0.5) * h));
-        offc[2] = float(com[(size_t(node) * 3 + 2) * NCELL + c] - (lo_z + (8.0 * ni.iz + z + 0.5) * h));
+        offc[0] = d2f_trunc(com[(size_t(node) * 3 + 0) * NCELL + c] - (lo_x + (8.0 * ni.ix + x + 0.5) * h));
+        offc[1] = d2f_trunc(com[(size_t(node) * 3 + 1) * NCELL + c] - (lo_y + (8.0 * ni.iy + y + 0.5) * h));
+        offc[2] = d2f_trunc(com[(size_t(node) * 3 + 2) * NCELL + c] - (lo_z + (8.0 * ni.iz + z + 0.5) * h));
     }
     double out[20];
     double corr[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc[1];
     if (ni.parent >= 0) {
         const int pc = (4 * (ni.ix & 1) + (x >> 1)) + 8 * (4 * (ni.iy & 1) + (y >> 1)) +
                        64 * (4 * (ni.iz & 1) + (z >> 1));
@@ -166,13 +165,14 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
         float Pf[20];
 #pragma unroll
         for (int k = 0; k < 20; ++k) Pf[k] = pd[k * NCELL];
-        const float hc = float(L[LV_H]);
+        const float hc = d2f_trunc(L[LV_H]);
         const float d[3] = {(float(x & 1) - 0.5f) * hc + offc[0] - pd[20 * NCELL],
                             (float(y & 1) - 0.5f) * hc + offc[1] - pd[21 * NCELL],
                             (float(z & 1) - 0.5f) * hc + offc[2] - pd[22 * NCELL]};
         float inc[20];
         shift_increments<float, NMAX>(Pf, d, inc);
-        const float rs[4] = {float(L[LV_R0]), float(L[LV_R1]), float(L[LV_R2]), float(L[LV_R3])};
+        const float rs[4] = {d2f_trunc(L[LV_R0]), d2f_trunc(L[LV_R1]), d2f_trunc(L[LV_R2]),
+                             d2f_trunc(L[LV_R3])};
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             float s, e;
@@ -182,14 +182,18 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
         }
 #pragma unroll
         for (int k = 0; k < NK; ++k)
-            out[k] = fma(double(hi[k]) + double(lo[k]), sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3],
+            out[k] = fma(pair_to_double(hi[k], lo[k]), sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3],
                          L64[(size_t(ni.parent) * NCOMP + k) * NCELL + pc]);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) corr[a] += dacc[(size_t(ni.parent) * 3 + a) * NCELL + pc];
+        for (int a = 0; a < 3; ++a)
+            corr[a] = fma(dL1[(size_t(node) * 3 + a) * NCELL + c], sc[1],
+                          dacc[(size_t(ni.parent) * 3 + a) * NCELL + pc]);
     } else {
 #pragma unroll
         for (int k = 0; k < NK; ++k)
-            out[k] = (double(hi[k]) + double(lo[k])) * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
+            out[k] = pair_to_double(hi[k], lo[k]) * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc[1];
     }
 #pragma unroll
     for (int k = 0; k < NK; ++k) L64[(size_t(node) * NCOMP + k) * NCELL + c] = out[k];
@@ -198,7 +202,7 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
     if (NMAX == 3) {
         float *od = down + size_t(ni.mp_row) * 23 * NCELL + c;
 #pragma unroll
-        for (int k = 0; k < 20; ++k) od[k * NCELL] = float(out[k]);
+        for (int k = 0; k < 20; ++k) od[k * NCELL] = d2f_trunc(out[k]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) od[(20 + a) * NCELL] = offc[a];
     }
@@ -243,30 +247,37 @@ __global__ void __launch_bounds__(kSliceThreads) l2l_kernel(const NodeInfo *__re
     }
 }
 
-// block sum of 8 doubles, fixed order; result in thread 0
-template <int THREADS>
-__device__ __forceinline__ void block_sum8(double v[8], double (*sh)[8])
+// 64 threads per leaf node, one (x, y) column of 8 cells each.
+// The torque sum uses that x and y are fixed along a column, X2 = Z0 + z h:
+//   sum m (X x g) = (X1 F2 - S1, S0 - X0 F2, X0 F1 - X1 F0),
+//   F = sum m g,  S_a = sum m X2 g_a = Z0 F_a + h sum z m g_a  (a = 0, 1),
+// which takes 6 FP64 operations per cell instead of 12 (GB300's FP64 unit
+// bounds this pass).  The normalisers need float precision only and are
+// formed and summed in float, with the double -> float conversions on the
+// integer pipe.
+constexpr int kForceThreads = 64;
+
+// block sum of NV values of type V, fixed order; result in thread 0
+template <int THREADS, typename V, int NV>
+__device__ __forceinline__ void block_sum(V v[NV], V (*sh)[NV])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sh[warp][k] = v[k];
+        for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 8; ++k) {
-            double s = 0.0;
+        for (int k = 0; k < NV; ++k) {
+            V s = V(0);
             for (int w = 0; w < THREADS / 32; ++w) s += sh[w][k];
             v[k] = s;
         }
     }
 }
-
-// 64 threads per leaf node, one (x, y) column of 8 cells each
-constexpr int kForceThreads = 64;
 
 __global__ void __launch_bounds__(kForceThreads) forces_kernel(
     const NodeInfo *__restrict__ info, const int32_t *__restrict__ leaves,
@@ -274,7 +285,8 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
     const double *__restrict__ dacc, const double *__restrict__ rho, double *__restrict__ phi,
     double *__restrict__ g, double *__restrict__ partials, double box_size)
 {
-    __shared__ double sh[kForceThreads / 32][8];
+    __shared__ double sh[kForceThreads / 32][6];
+    __shared__ float shf[kForceThreads / 32][2];
     const int node = leaves[blockIdx.x];
     const NodeInfo ni = info[node];
     const int row = ni.leaf_row;
@@ -286,7 +298,8 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
     const double X0 = (8.0 * ni.ix + x + 0.5) * h - half;
     const double X1 = (8.0 * ni.iy + y + 0.5) * h - half;
     const double Z0 = (8.0 * ni.iz + 0.5) * h - half;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const float X0f = d2f_trunc(X0), X1f = d2f_trunc(X1), Z0f = d2f_trunc(Z0), hf = d2f_trunc(h);
+    double F[3] = {0.0, 0.0, 0.0}, T[2] = {0.0, 0.0};
     float nf = 0.f, nt = 0.f;
 #pragma unroll
     for (int z = 0; z < 8; ++z) {
@@ -299,29 +312,34 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
             gv[a] = -(L64[(size_t(node) * NCOMP + 1 + a) * NCELL + c] +
                       dacc[(size_t(node) * 3 + a) * NCELL + c]);
             g[(size_t(row) * 3 + a) * NCELL + c] = gv[a];
+            F[a] = fma(m, gv[a], F[a]);                 // f = m g
         }
-        const double X2 = Z0 + z * h;
-        const double u[3] = {X1 * gv[2] - X2 * gv[1], X2 * gv[0] - X0 * gv[2],
-                             X0 * gv[1] - X1 * gv[0]};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            v[a] += m * gv[a];          // f = m g
-            v[3 + a] += m * u[a];       // x cross f = m (x cross g)
+        if (z > 0) {
+            const double mz = z == 1 ? m : m * double(z);
+            T[0] = fma(mz, gv[0], T[0]);
+            T[1] = fma(mz, gv[1], T[1]);
         }
-        // the normalisers sum |f| = m |g| and |x cross f| = m |x cross g|
-        // need no more than float precision per cell (g and x are O(1), so
-        // float does not underflow where the cell mass is tiny)
-        const float mf = float(m);
-        const float gf[3] = {float(gv[0]), float(gv[1]), float(gv[2])};
-        const float uf[3] = {float(u[0]), float(u[1]), float(u[2])};
+        // normalisers |f| = m |g| and |x cross f| = m |x cross g|, in float
+        // (g and x are O(1), so float does not underflow where m is tiny)
+        const float mf = d2f_trunc(m);
+        const float gf[3] = {d2f_trunc(gv[0]), d2f_trunc(gv[1]), d2f_trunc(gv[2])};
+        const float X2f = fmaf(float(z), hf, Z0f);
+        const float uf[3] = {X1f * gf[2] - X2f * gf[1], X2f * gf[0] - X0f * gf[2],
+                             X0f * gf[1] - X1f * gf[0]};
         nf += mf * sqrtf(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
         nt += mf * sqrtf(uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
     }
-    v[6] = double(nf);
-    v[7] = double(nt);
-    block_sum8<kForceThreads>(v, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 8; ++k) partials[size_t(row) * 8 + k] = v[k];
+    const double S0 = fma(h, T[0], Z0 * F[0]), S1 = fma(h, T[1], Z0 * F[1]);
+    double v[6] = {F[0], F[1], F[2], fma(X1, F[2], -S1), fma(-X0, F[2], S0),
+                   fma(X0, F[1], -X1 * F[0])};
+    float vf[2] = {nf, nt};
+    block_sum<kForceThreads, double, 6>(v, sh);
+    block_sum<kForceThreads, float, 2>(vf, shf);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) partials[size_t(row) * 8 + k] = v[k];
+        partials[size_t(row) * 8 + 6] = double(vf[0]);
+        partials[size_t(row) * 8 + 7] = double(vf[1]);
+    }
 }
 
 __global__ void __launch_bounds__(512) reduce_kernel(const int32_t *__restrict__ off,
@@ -335,7 +353,7 @@ __global__ void __launch_bounds__(512) reduce_kernel(const int32_t *__restrict__
     for (int i = off[tree] + threadIdx.x; i < off[tree + 1]; i += blockDim.x)
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] += partials[size_t(rows[i]) * 8 + k];
-    block_sum8<512>(v, sh);
+    block_sum<512, double, 8>(v, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < 8; ++k) totals[size_t(tree) * 8 + k] = v[k];
 }

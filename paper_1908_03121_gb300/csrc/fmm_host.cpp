@@ -207,12 +207,14 @@ static int validate_nodes(const fmm_node_desc *d, int64_t n, const fmm_config *c
 
 // ------------------------------------------------------------- stencils
 // Per child parity p: all offsets o whose parent offset floor((p+o)/2) is
-// not well separated, split into well-separated (far) and near offsets.
+// not well separated, split into well-separated (far) and near offsets, each
+// in lexicographic order (neighbouring warps then walk the halo in the same
+// spatial order, which keeps the multipole kernel's source reads in L1).
 // Reflecting o along the axes where p is odd maps parity 0's stencil onto
 // parity p's (floor((1+o)/2) = -floor(-o/2), and both tests depend on |.|
-// only), so every parity's list is parity 0's, reflected, in the same order:
-// entry k has the same distance, and the same monopole weights up to the
-// signs of the first-order ones, in every parity.
+// only); the monopole kernel walks every parity in parity 0's order,
+// reflected, so that one weight table (parity 0's) serves all parities, and
+// gets its own table of window offsets in that order.
 static void build_stencils(fmm_tree_s *t)
 {
     Plan &P = t->plan;
@@ -241,69 +243,60 @@ static void build_stencils(fmm_tree_s *t)
     };
     std::vector<char> in_union(size_t(2 * R + 1) * (2 * R + 1) * (2 * R + 1), 0);
     std::vector<StencilEntry> lists[8];
-    {
-        const int p0[3] = {0, 0, 0};
+    for (int p = 0; p < 8; ++p) {
+        const int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
         std::vector<StencilEntry> far, nearv;
         for (int oz = -R; oz <= R; ++oz)
             for (int oy = -R; oy <= R; ++oy)
                 for (int ox = -R; ox <= R; ++ox) {
                     if (!ox && !oy && !oz) continue;
                     const int o[3] = {ox, oy, oz};
-                    if (!in_stencil(p0, o)) continue;
-                    (well_separated(theta, ox, oy, oz) ? far : nearv).push_back(entry(p0, ox, oy, oz));
+                    if (!in_stencil(pp, o)) continue;
+                    (well_separated(theta, ox, oy, oz) ? far : nearv).push_back(entry(pp, ox, oy, oz));
+                    in_union[size_t((oz + R) * (2 * R + 1) + (oy + R)) * (2 * R + 1) + (ox + R)] = 1;
                 }
-        for (int p = 0; p < 8; ++p) {
-            P.n_far[p] = int(far.size());
-            P.n_near[p] = int(nearv.size());
-        }
-        lists[0] = far;
-        lists[0].insert(lists[0].end(), nearv.begin(), nearv.end());
+        P.n_far[p] = int(far.size());
+        P.n_near[p] = int(nearv.size());
+        lists[p] = far;
+        lists[p].insert(lists[p].end(), nearv.begin(), nearv.end());
     }
-    for (int p = 0; p < 8; ++p) {
-        const int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
-        if (p > 0) {
-            lists[p].clear();
-            for (const StencilEntry &e : lists[0])
-                lists[p].push_back(entry(pp, pp[0] ? -e.ox : e.ox, pp[1] ? -e.oy : e.oy,
-                                         pp[2] ? -e.oz : e.oz));
-        }
-        // the reflected list is exactly parity p's stencil
-        int64_t members = 0;
-        for (const StencilEntry &e : lists[p]) {
-            const int o[3] = {e.ox, e.oy, e.oz};
-            if (!in_stencil(pp, o)) std::abort();
-            in_union[size_t((e.oz + R) * (2 * R + 1) + (e.oy + R)) * (2 * R + 1) + (e.ox + R)] = 1;
-        }
-        for (int oz = -R; oz <= R; ++oz)
-            for (int oy = -R; oy <= R; ++oy)
-                for (int ox = -R; ox <= R; ++ox) {
-                    const int o[3] = {ox, oy, oz};
-                    if ((ox || oy || oz) && in_stencil(pp, o)) ++members;
-                }
-        if (members != int64_t(lists[p].size())) std::abort();
-    }
+    // the kernels rely on every parity having the same far/near counts
+    // (the reflection above maps one parity's stencil onto another's)
+    for (int p = 1; p < 8; ++p)
+        if (P.n_far[p] != P.n_far[0] || P.n_near[p] != P.n_near[0]) std::abort();
     int stride = 0;
     for (int p = 0; p < 8; ++p) stride = std::max(stride, int(lists[p].size()));
     P.ent_stride = (stride + 3) & ~3;
     t->stencil.assign(size_t(8) * P.ent_stride, StencilEntry{0, 0, 0, 0});
-    t->coef32.assign(size_t(8) * P.ent_stride * 4, 0.f);
-    t->coef64.assign(size_t(8) * P.ent_stride * 4, 0.0);
-    t->coefdf.assign(size_t(8) * P.ent_stride * 8, 0.f);
     for (int p = 0; p < 8; ++p)
-        for (size_t k = 0; k < lists[p].size(); ++k) {
-            const StencilEntry &e = lists[p][k];
-            size_t idx = size_t(p) * P.ent_stride + k;
-            t->stencil[idx] = e;
-            double c[4];
-            mono_coef(e.ox, e.oy, e.oz, c);
-            for (int j = 0; j < 4; ++j) {
-                t->coef64[idx * 4 + j] = c[j];
-                t->coef32[idx * 4 + j] = float(c[j]);
-                // double-float (hi, lo) pairs
-                t->coefdf[idx * 8 + 2 * j] = float(c[j]);
-                t->coefdf[idx * 8 + 2 * j + 1] = float(c[j] - double(float(c[j])));
-            }
+        for (size_t k = 0; k < lists[p].size(); ++k) t->stencil[size_t(p) * P.ent_stride + k] = lists[p][k];
+    // monopole kernel: parity 0's weights, every parity in parity 0's order
+    t->coef32.assign(size_t(P.ent_stride) * 4, 0.f);
+    t->coef64.assign(size_t(P.ent_stride) * 4, 0.0);
+    t->coefdf.assign(size_t(P.ent_stride) * 8, 0.f);
+    t->mono_woff.assign(size_t(8) * P.ent_stride, 0);
+    for (size_t k = 0; k < lists[0].size(); ++k) {
+        const StencilEntry &e = lists[0][k];
+        double c[4];
+        mono_coef(e.ox, e.oy, e.oz, c);
+        for (int j = 0; j < 4; ++j) {
+            t->coef64[k * 4 + j] = c[j];
+            t->coef32[k * 4 + j] = float(c[j]);
+            // double-float (hi, lo) pairs
+            t->coefdf[k * 8 + 2 * j] = float(c[j]);
+            t->coefdf[k * 8 + 2 * j + 1] = float(c[j] - double(float(c[j])));
         }
+        for (int p = 0; p < 8; ++p) {
+            const int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
+            const int o[3] = {pp[0] ? -e.ox : e.ox, pp[1] ? -e.oy : e.oy, pp[2] ? -e.oz : e.oz};
+            // the reflected entry is in parity p's stencil, on the same side
+            // of the far/near split
+            if (!in_stencil(pp, o) ||
+                well_separated(theta, o[0], o[1], o[2]) != (int(k) < P.n_far[0]))
+                std::abort();
+            t->mono_woff[size_t(p) * P.ent_stride + k] = entry(pp, o[0], o[1], o[2]).woff;
+        }
+    }
     P.stencil_union = 0;
     for (char c : in_union) P.stencil_union += c;
     // slots reachable by each entry from each half (z-cells 0-3 / 4-7) of a node
@@ -487,7 +480,7 @@ static void free_device(fmm_tree_s *t)
     for (cudaEvent_t e : t->timer.ev) cudaEventDestroy(e);
     t->timer.ev.clear();
     DeviceTables &d = t->dev;
-    void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf,
+    void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf, d.mono_woff,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.mass, d.mp, d.counters,
                     d.partials, d.down, d.slot_mask};
     for (void *p : ptrs)
@@ -503,6 +496,7 @@ static int upload_tree(fmm_tree_s *t)
         (rc = upload(&d.nbr, t->nbr)) || (rc = upload(&d.lists, t->lists)) ||
         (rc = upload(&d.stencil, t->stencil)) || (rc = upload(&d.coef32, t->coef32)) ||
         (rc = upload(&d.coef64, t->coef64)) || (rc = upload(&d.coefdf, t->coefdf)) ||
+        (rc = upload(&d.mono_woff, t->mono_woff)) ||
         (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||
         (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)) || (rc = upload(&d.levels, t->levels)) ||
         (rc = upload(&d.slot_mask, t->slot_mask)))
@@ -572,6 +566,12 @@ int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config
     }
     t->n_leaf = leaf_rows;
     t->n_refined = mp_rows;
+    // the same-level kernels address packed moments with 32-bit offsets
+    // (row * 8192 elements)
+    if (mp_rows > (int64_t(1) << 31) / (4 * NCELL * 4) - 1) {
+        delete t;
+        return fail(FMM_ERR_INVALID_ARG, "more than 262143 refined nodes in one tree handle");
+    }
     // neighbours, and the nesting rule for refined nodes
     t->nbr.assign(size_t(n_nodes) * 27, -1);
     for (int64_t i = 0; i < n_nodes; ++i) {

@@ -59,9 +59,10 @@ struct DeviceTables {
     int32_t *nbr = nullptr;          // [n][27], slot (dx+1)+3(dy+1)+9(dz+1)
     int32_t *lists = nullptr;        // all node-index lists, see Plan offsets
     StencilEntry *stencil = nullptr; // [8][ent_stride]
-    float *coef32 = nullptr;         // [8][ent_stride][4] monopole coefficients
-    double *coef64 = nullptr;        // [8][ent_stride][4]
-    float *coefdf = nullptr;         // [8][ent_stride][4][hi, lo]
+    float *coef32 = nullptr;         // [ent_stride][4] monopole weights of parity 0
+    double *coef64 = nullptr;        // [ent_stride][4]
+    float *coefdf = nullptr;         // [ent_stride][4][hi, lo]
+    int32_t *mono_woff = nullptr;    // [8][ent_stride] window offsets, parity 0's order reflected
     int32_t *tree_leaf_off = nullptr;   // [n_trees + 1]
     int32_t *tree_leaf_rows = nullptr;  // [n_leaf]
     double *levels = nullptr;        // [max_level + 1][LEVEL_FIELDS]
@@ -125,6 +126,7 @@ struct fmm_tree_s {
     std::vector<float> coef32;
     std::vector<double> coef64;
     std::vector<float> coefdf;
+    std::vector<int32_t> mono_woff;
     std::vector<int32_t> tree_leaf_off, tree_leaf_rows;
     std::vector<double> levels;
     std::vector<int32_t> slot_mask;

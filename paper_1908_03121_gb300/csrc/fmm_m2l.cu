@@ -73,13 +73,15 @@ struct KParams {
     int32_t n_items;
     int32_t *counter;
     const StencilEntry *stencil;
-    const void *coef;
+    const void *coef;        // monopole weights of parity 0
+    const int32_t *mono_woff;  // [8][ent_stride] window offsets in parity 0's order, reflected
     int n_far, n_near;       // identical for every parity
     int ent_stride;          // entries reserved per parity
     const int32_t *slot_mask;  // [8][2][ent_stride] neighbour slots an entry can reach
     int reach, py, pz, sub_stride;
     const void *mass;
     const void *mp;
+    int mp_limit;            // elements of mp: decoded window offsets below it only
     void *L;
     float *Lc;
     double *dL1;
@@ -162,9 +164,44 @@ __device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// With s_row given (the multipole-target kernel), a refined source's cell
+// holds instead the offset of its packed moments (row and parity index),
+// encoded by window_index as a value with the sign bit set (masses are not
+// negative); without, it holds 0.  The kernels use a decoded offset only
+// below mp_limit, so an invalid negative density can give wrong results but
+// no access outside the packed moments.
+template <typename T>
+__device__ __forceinline__ T window_index(int idx)
+{
+    if constexpr (kF32<T>) {
+        return __int_as_float(-1 - idx);
+    } else if constexpr (kDF<T>) {
+        return dfloat(__int_as_float(-1 - idx), 0.f);
+    } else {
+        return __longlong_as_double(-1ll - idx);
+    }
+}
+
+// the moment offset encoded in a window cell, or -1 for a mass
+template <typename T>
+__device__ __forceinline__ int window_decode(T v)
+{
+    if constexpr (kF32<T>) {
+        const int b = __float_as_int(v);
+        return b < 0 ? -1 - b : -1;
+    } else if constexpr (kDF<T>) {
+        const int b = __float_as_int(v.hi);
+        return b < 0 ? -1 - b : -1;
+    } else {
+        const long long b = __double_as_longlong(v);
+        return b < 0 ? int(-1ll - b) : -1;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void stage_window_async(T *W, const int *s_nbr, const int *s_leaf,
-                                                   const T *__restrict__ mass, const KParams &P)
+                                                   const T *__restrict__ mass, const KParams &P,
+                                                   const int *s_row = nullptr)
 {
     const int R = P.reach;
     const int E = 8 + 2 * R;
@@ -180,9 +217,14 @@ __device__ __forceinline__ void stage_window_async(T *W, const int *s_nbr, const
             const int slot = sxy + 9 * (bz >> 3);
             const int lz = bz & 7;
             const bool ok = s_leaf[slot] != 0;
-            const T *src = ok ? mass + size_t(s_nbr[slot]) * NCELL + pxy + 256 * (lz & 1) + 16 * (lz >> 1)
-                              : mass;
-            cp_async_elem<T>(W + wxy + 4 * (uz & 1) * P.sub_stride + P.pz * (uz >> 1), src, ok);
+            const int pi = pxy + 256 * (lz & 1) + 16 * (lz >> 1);
+            const T *src = ok ? mass + size_t(s_nbr[slot]) * NCELL + pi : mass;
+            const int wi = wxy + 4 * (uz & 1) * P.sub_stride + P.pz * (uz >> 1);
+            const int row = s_row ? s_row[slot] : -1;
+            if (row >= 0)
+                W[wi] = window_index<T>((row * 4 * NCELL + pi) * 4);
+            else
+                cp_async_elem<T>(W + wi, src, ok);
         }
     }
 }
@@ -345,9 +387,8 @@ __device__ __forceinline__ void load4(const T *p, T v[4])
 }
 
 template <typename T>
-__device__ __forceinline__ void load_source(const KParams &P, int row, int pi, Src<T> &s)
+__device__ __forceinline__ void load_source_at(const T *base, Src<T> &s)
 {
-    const T *base = static_cast<const T *>(P.mp) + (size_t(row) * 4 * NCELL + pi) * 4;
     T v[16];
 #pragma unroll
     for (int g = 0; g < 4; ++g) load4<T>(base + size_t(g) * NCELL * 4, v + 4 * g);
@@ -360,6 +401,12 @@ __device__ __forceinline__ void load_source(const KParams &P, int row, int pi, S
 }
 
 template <typename T>
+__device__ __forceinline__ void load_source(const KParams &P, int row, int pi, Src<T> &s)
+{
+    load_source_at<T>(static_cast<const T *>(P.mp) + (size_t(row) * 4 * NCELL + pi) * 4, s);
+}
+
+template <typename T>
 __device__ __forceinline__ void zero_moments(Src<T> &s)
 {
     s.d[0] = s.d[1] = s.d[2] = T(0);
@@ -369,49 +416,58 @@ __device__ __forceinline__ void zero_moments(Src<T> &s)
     for (int q = 0; q < 7; ++q) s.B3[q] = T(0);
 }
 
+// a * b + c in the element type (fused in float and double)
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ dfloat fmadd(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+
 // One source (multipole if SRC_MP, else a point mass m0 = s.m0) into a
 // multipole target's 16 traceless accumulators and the correction sum
 //   S_i += sum_q (B3_B - M0_B a3_A)_q D4[i, q],  a3_A = B3_A / M0_A,
 // with the sign of L folded in:
 //   L0 -= M0 D0 + B2.D2 - B3.D3,  L1_i -= M0 D1_i + B2.D3[i,.],
 //   L2 -= M0 D2,  L3 -= M0 D3.
+// Orders 0 and 1 (potential and field) sum each source's terms first and
+// add that sum to the chunk sum once, so every source costs one rounding at
+// the chunk sum's magnitude; orders 2-3 and the correction take each product
+// straight into their sums as one fused multiply-add.
 template <typename T, bool SRC_MP>
 __device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const T a3A[7],
                                        Acc<T, 16> &L, Acc<T, 3> &S)
 {
     DTraceless<T> D;
     D.template eval<true>(Rx, Ry, Rz);
-    const T m0 = s.m0;
-    T l0 = m0 * D.D0;
+    const T nm0 = -s.m0;
+    T a = nm0 * D.D0;
     if (SRC_MP) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) l0 += s.B2[k] * D.D2[k];
+        for (int k = 0; k < 5; ++k) a = fmadd(-s.B2[k], D.D2[k], a);
 #pragma unroll
-        for (int q = 0; q < 7; ++q) l0 -= s.B3[q] * D.D3[q];
+        for (int q = 0; q < 7; ++q) a = fmadd(s.B3[q], D.D3[q], a);
     }
-    L.part[0] -= l0;
+    L.part[0] += a;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        T l1 = m0 * D.D1[i];
+        T b = nm0 * D.D1[i];
         if (SRC_MP) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) l1 += s.B2[k] * D.d3slice(i, k);
+            for (int k = 0; k < 5; ++k) b = fmadd(-s.B2[k], D.d3slice(i, k), b);
         }
-        L.part[1 + i] -= l1;
+        L.part[1 + i] += b;
     }
 #pragma unroll
-    for (int k = 0; k < 5; ++k) L.part[4 + k] -= m0 * D.D2[k];
+    for (int k = 0; k < 5; ++k) L.part[4 + k] = fmadd(nm0, D.D2[k], L.part[4 + k]);
 #pragma unroll
-    for (int q = 0; q < 7; ++q) L.part[9 + q] -= m0 * D.D3[q];
+    for (int q = 0; q < 7; ++q) L.part[9 + q] = fmadd(nm0, D.D3[q], L.part[9 + q]);
     T w[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) w[q] = SRC_MP ? s.B3[q] - m0 * a3A[q] : -m0 * a3A[q];
+    for (int q = 0; q < 7; ++q) w[q] = SRC_MP ? fmadd(nm0, a3A[q], s.B3[q]) : nm0 * a3A[q];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        T acc = T(0);
+        T c = S.part[i];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) acc += w[q] * D.U[i][q];
-        S.part[i] += acc;
+        for (int q = 0; q < 7; ++q) c = fmadd(w[q], D.U[i][q], c);
+        S.part[i] = c;
     }
 }
 
@@ -423,22 +479,22 @@ __device__ __forceinline__ void acc_mx(T Rx, T Ry, T Rz, const Src<T> &s, Acc<T,
 {
     DTraceless<T> D;
     D.template eval<true>(Rx, Ry, Rz);
-    T l0 = s.m0 * D.D0;
+    T a = -s.m0 * D.D0;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) l0 += s.B2[k] * D.D2[k];
+    for (int k = 0; k < 5; ++k) a = fmadd(-s.B2[k], D.D2[k], a);
 #pragma unroll
-    for (int q = 0; q < 7; ++q) l0 -= s.B3[q] * D.D3[q];
-    L.part[0] -= l0;
+    for (int q = 0; q < 7; ++q) a = fmadd(s.B3[q], D.D3[q], a);
+    L.part[0] += a;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        T l1 = s.m0 * D.D1[i];
+        T b = -s.m0 * D.D1[i];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) l1 += s.B2[k] * D.d3slice(i, k);
-        L.part[1 + i] -= l1;
-        T acc = T(0);
+        for (int k = 0; k < 5; ++k) b = fmadd(-s.B2[k], D.d3slice(i, k), b);
+        L.part[1 + i] += b;
+        T c = S.part[i];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) acc += s.B3[q] * D.U[i][q];
-        S.part[i] += acc;
+        for (int q = 0; q < 7; ++q) c = fmadd(s.B3[q], D.U[i][q], c);
+        S.part[i] = c;
     }
 }
 
@@ -489,6 +545,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P
     const int cx = lane & 3, cy = (lane >> 2) & 3, cz0 = lane >> 4;
     const StencilEntry *ent = P.stencil + p * P.ent_stride;
     const T *mass = static_cast<const T *>(P.mass);
+    const T *mp = static_cast<const T *>(P.mp);
     for (;;) {
         const int item = pull_item(P.counter, &s_item);
         if (item >= P.n_items) break;
@@ -496,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P
         const NodeInfo ti = P.info[node];
         load_slots(node, P, s_nbr, s_leaf, s_row);
         __syncthreads();
-        stage_window_async<T>(W, s_nbr, s_leaf, mass, P);
+        stage_window_async<T>(W, s_nbr, s_leaf, mass, P, s_row);
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
@@ -515,14 +572,13 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P
                 const int e1 = min(e0 + kChunk, P.n_far);
                 for (int e = e0; e < e1; ++e) {
                     const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + e));
-                    int slot, pi;
-                    source_cell(ax, ay, az, E.x, E.y, E.z, slot, pi);
-                    const int row = s_row[slot];
+                    const T wv = W[base + E.w];
+                    const int idx = window_decode<T>(wv);
                     Src<T> src;
-                    if (row >= 0) {
-                        load_source<T>(P, row, pi, src);
+                    if (idx >= 0 && idx < P.mp_limit) {
+                        load_source_at<T>(mp + idx, src);
                     } else {
-                        src.m0 = W[base + E.w];
+                        src.m0 = wv;
                         zero_moments<T>(src);
                     }
                     acc_mp<T, true>(dA[0] - src.d[0] - T(E.x), dA[1] - src.d[1] - T(E.y),
@@ -531,13 +587,15 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P
                 L.flush();
                 S.flush();
             }
-            // near sources: leaf cells only (the window holds 0 elsewhere)
+            // near sources: leaf cells only (refined ones contribute nothing
+            // here: their children interact one level down)
             for (int e0 = P.n_far; e0 < P.n_far + P.n_near; e0 += kChunk) {
                 const int e1 = min(e0 + kChunk, P.n_far + P.n_near);
                 for (int e = e0; e < e1; ++e) {
                     const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + e));
+                    const T wv = W[base + E.w];
                     Src<T> src;
-                    src.m0 = W[base + E.w];
+                    src.m0 = window_decode<T>(wv) >= 0 ? T(0) : wv;
                     acc_mp<T, false>(dA[0] - T(E.x), dA[1] - T(E.y), dA[2] - T(E.z), src, a3A,
                                      L, S);
                 }
@@ -557,12 +615,13 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P
 // ---------------------------------------------------------- mono_kernel
 // Leaf target, leaf sources: R = -o exactly, so L0 += c0(o) m and
 // L1 += c1(o) m with per-offset weights c0 = -1/|o|, c1 = -o/|o|^3.
-// Every parity's stencil is parity 0's reflected along its odd axes, entry by
-// entry, so one weight table (parity 0's) serves all eight warps: a warp of
-// parity p accumulates with parity 0's first-order weights and flips the
-// signs of its L1 components along p's odd axes at the end (exact).  The
-// table and the per-parity window offsets sit in shared memory, loaded once
-// per CTA; every access to them is a warp-uniform broadcast.
+// Every parity's stencil is parity 0's reflected along its odd axes, so a
+// warp of parity p walks parity 0's entries, reflected (mono_woff holds
+// their window offsets), and one weight table (parity 0's) serves all eight
+// warps: the warp accumulates with parity 0's first-order weights and flips
+// the signs of its L1 components along p's odd axes at the end (exact).  The
+// table and the window offsets sit in shared memory, loaded once per CTA;
+// every access to them is a warp-uniform broadcast.
 // Each pass takes NB sub-grids (consecutive in the cost-sorted queue), each
 // with its own halo window, staged by cp.async so that every load of the
 // window is in flight at once; every thread holds two target cells (z and
@@ -627,7 +686,7 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
         const T *gcoef = static_cast<const T *>(P.coef);          // parity 0 first
         for (int i = threadIdx.x; i < 4 * n_ent; i += blockDim.x) s_coef[i] = ldg_t(gcoef + i);
         for (int i = threadIdx.x; i < 8 * P.ent_stride; i += blockDim.x)
-            s_woff[i] = __ldg(&P.stencil[i].woff);
+            s_woff[i] = __ldg(P.mono_woff + i);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = warp;
@@ -951,14 +1010,19 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     P.sub_stride = Pl.sub_stride;
     P.mass = d.mass;
     P.mp = d.mp;
+    P.mp_limit = int(t->n_refined * 4 * NCELL * 4);
     P.L = L;
     P.Lc = Lc;
     P.dL1 = dL1;
     P.theta2 = t->cfg.theta * t->cfg.theta;
     P.slot_mask = d.slot_mask;
+    P.mono_woff = d.mono_woff;
     const int cap = t->tuning.ctas_per_sm;
     const size_t wbytes = size_t(8) * Pl.sub_stride * sizeof(T);
-    cudaError_t e = Kernels<T>::mp(wbytes);
+    // mp_kernel: one window (masses of leaf sources, moment offsets of
+    // refined ones)
+    const size_t mp_bytes = wbytes;
+    cudaError_t e = Kernels<T>::mp(mp_bytes);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d.counters, 0, 4 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
@@ -979,9 +1043,9 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         K.list = d.lists + Pl.work_mp.off;
         K.n_items = int32_t(Pl.work_mp.count);
         K.counter = d.counters + Q_MP;
-        int g = persistent_grid(mp_kernel<T>, wbytes, Pl.work_mp.count, sms, cap);
+        int g = persistent_grid(mp_kernel<T>, mp_bytes, Pl.work_mp.count, sms, cap);
         timing_begin(t, FMM_K_MULTIPOLE, s);
-        mp_kernel<T><<<g, kThreads, wbytes, s>>>(K);
+        mp_kernel<T><<<g, kThreads, mp_bytes, s>>>(K);
         timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

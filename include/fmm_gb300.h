@@ -294,6 +294,23 @@ int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int32_t n_tree
                        const double *rho, double *phi, double *g, double *totals,
                        fmm_stream_t stream);
 
+/*
+ * fmm_check_conversions -- diagnostic, no counterpart in the paper.  The
+ * downward and force passes convert between float and double through the
+ * IEEE-754 bit fields on the integer pipe (GB300's FP64 unit, which also runs
+ * the conversion instructions, bounds those passes).  This checks those
+ * conversions against the hardware's on caller-chosen values:
+ *   values:   device double [n] (read).
+ *   mismatch: device int32 [1], written asynchronously: 0 when every value
+ *             converts bit for bit as the hardware does (within the
+ *             helpers' domain: normal magnitudes, zeros, infinities, NaNs),
+ *             else a bit mask: 1 rounding to nearest, 2 truncation, 4 the
+ *             exact widening of a float.
+ * Errors: FMM_ERR_INVALID_ARG (NULL buffer, n < 0), FMM_ERR_CUDA.
+ */
+int fmm_check_conversions(const double *values, int64_t n, int32_t *mismatch,
+                          fmm_stream_t stream);
+
 /* Release the tree's host and device memory (synchronises the device first). */
 void fmm_destroy_tree(fmm_tree_t tree);
 

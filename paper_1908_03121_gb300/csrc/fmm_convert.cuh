@@ -47,13 +47,38 @@ __device__ __forceinline__ float d2f_trunc(double d)
     const int e = e64 - (1023 - 127);
     unsigned u;
     if (e64 == 0x7FF)
-        u = sign | 0x7F800000u | (m ? 0x400000u : 0u);
+        u = sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u);
     else if (e <= 0)
         u = sign;
     else if (e >= 0xFF)
         u = sign | 0x7F800000u;
     else
         u = sign | (unsigned(e) << 23) | m;
+    return __uint_as_float(u);
+}
+
+// rounded to nearest (ties to even): the 23 leading mantissa bits plus one
+// when the 29 dropped bits exceed half an ulp (or equal it and the kept bits
+// are odd); a carry out of the mantissa lands in the exponent, which is
+// exactly the rounded value, and overflows to infinity
+__device__ __forceinline__ float d2f_rn(double d)
+{
+    const unsigned hi = unsigned(__double2hiint(d)), lo = unsigned(__double2loint(d));
+    const unsigned sign = hi & 0x80000000u;
+    const int e64 = int((hi >> 20) & 0x7FFu);
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    const int e = e64 - (1023 - 127);
+    unsigned u;
+    if (e64 == 0x7FF)
+        u = sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u);
+    else if (e <= 0)
+        u = sign;
+    else if (e >= 0xFF)
+        u = sign | 0x7F800000u;
+    else
+        u = sign | ((unsigned(e) << 23) + m + up);
     return __uint_as_float(u);
 }
 

@@ -39,6 +39,7 @@
 #include <cstdio>
 #include <type_traits>
 
+#include "fmm_convert.cuh"
 #include "fmm_internal.h"
 #include "fmm_tensor.cuh"
 
@@ -89,6 +90,42 @@ struct KParams {
 };
 
 // ------------------------------------------------------------------ pack
+// Mixed precision: everything but the centre-of-mass offset in float, with
+// the double -> float conversions on the integer pipe (GB300's FP64 unit,
+// which also runs conversions, would otherwise bound this pass); the
+// moments' float rounding is the contraction's own precision.
+__device__ __forceinline__ void pack_float(const NodeInfo &ni, const double *__restrict__ levels,
+                                           const double *__restrict__ Mn,
+                                           const double *__restrict__ comc, int x, int y, int z,
+                                           int pi, float *__restrict__ mass_node,
+                                           float *__restrict__ mp, double lo_x, double lo_y,
+                                           double lo_z)
+{
+    mass_node[pi] = d2f_rn(Mn[0]);
+    if (ni.mp_row < 0) return;
+    const double h = levels[ni.level * LEVEL_FIELDS + LV_H];
+    const float ih = d2f_rn(levels[ni.level * LEVEL_FIELDS + LV_IH]);
+    const double ctr[3] = {lo_x + (8.0 * ni.ix + x + 0.5) * h, lo_y + (8.0 * ni.iy + y + 0.5) * h,
+                           lo_z + (8.0 * ni.iz + z + 0.5) * h};
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = d2f_rn(comc[a * NCELL] - ctr[a]) * ih;
+    const float w2 = 0.5f * ih * ih, w3 = (1.0f / 6.0f) * ih * ih * ih;
+    float A2[6], A3[10];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) A2[q] = d2f_rn(Mn[(4 + q) * NCELL]) * (float(mult2(q)) * w2);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) A3[q] = d2f_rn(Mn[(10 + q) * NCELL]) * (float(mult3(q)) * w3);
+    const float v[16] = {mass_node[pi], d[0],          d[1],          d[2],
+                         A2[0] - A2[5], A2[3] - A2[5], A2[1],         A2[2],
+                         A2[4],         A3[0] - A3[5], A3[1] - A3[8], A3[2] - A3[9],
+                         A3[3] - A3[5], A3[4],         A3[6] - A3[8], A3[7] - A3[9]};
+    float4 *out = reinterpret_cast<float4 *>(mp + (size_t(ni.mp_row) * 4 * NCELL + pi) * 4);
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        out[size_t(g) * NCELL] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+}
+
 // mass[node][pi] = M0 for every node.  Refined nodes also get, in level
 // units, four groups of four values at mp[row][g][pi][0..3]:
 //   g0 = (M0, delta), delta = (X - centre) / h,
@@ -108,6 +145,11 @@ __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ 
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
     const int pi = parity_index(x, y, z);
     const double *Mn = M + size_t(node) * NCOMP * NCELL + c;
+    if constexpr (kF32<T>) {
+        pack_float(ni, levels, Mn, com + size_t(node) * 3 * NCELL + c, x, y, z, pi, mass + size_t(node) * NCELL,
+                   mp, lo_x, lo_y, lo_z);
+        return;
+    }
     mass[size_t(node) * NCELL + pi] = T(Mn[0]);
     if (ni.mp_row < 0) return;
     const double h = levels[ni.level * LEVEL_FIELDS + LV_H];

@@ -31,7 +31,7 @@ KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_mul
 
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
             "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_set_tuning", "fmm_get_tuning",
-            "fmm_forces_noalloc", "fmm_destroy_tree", "fmm_last_error")
+            "fmm_forces_noalloc", "fmm_check_conversions", "fmm_destroy_tree", "fmm_last_error")
 
 NCELL = 512
 NCOMP = 20
@@ -104,6 +104,7 @@ def load(build=True):
         lib.fmm_destroy_tree.restype = None
         lib.fmm_forces_noalloc.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                            P, P, P, P, P, P, P]
+        lib.fmm_check_conversions.argtypes = [P, ctypes.c_int64, P, P]
         lib.fmm_set_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_get_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_last_error.argtypes = []
@@ -229,6 +230,14 @@ def fmm_forces_noalloc(leaf_table, n_leaf, n_trees, box_size, L64, dL1_acc, rho,
     _check(load().fmm_forces_noalloc(_ptr(leaf_table), int(n_leaf), int(n_trees),
                                      float(box_size), _ptr(L64), _ptr(dL1_acc), _ptr(rho),
                                      _ptr(phi), _ptr(g), _ptr(totals), _stream(stream)))
+
+
+def fmm_check_conversions(values, mismatch, stream=None):
+    """Diagnostic: the library's integer-pipe float/double conversions against
+    the hardware's on the device doubles ``values``; ``mismatch`` (device int32
+    [1]) receives 0 when all agree, else a bit mask."""
+    _check(load().fmm_check_conversions(_ptr(values), int(values.numel()), _ptr(mismatch),
+                                        _stream(stream)))
 
 
 def fmm_set_tuning(tree, mono_subgrids=0, ctas_per_sm=0):

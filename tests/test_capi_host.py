@@ -32,6 +32,10 @@ def test_library_exports_every_declared_symbol():
     assert set(B.EXPORTED) == set(names)
     for name in names:
         assert hasattr(lib, name), name
+        # every binding declares its C argument types: without them ctypes
+        # passes Python ints as 32-bit C ints, and an int64_t parameter would
+        # see undefined upper bits
+        assert getattr(lib, name).argtypes is not None, name
 
 
 def test_struct_layouts_match_header():

@@ -12,6 +12,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fmm_dfloat.cuh"
+
 namespace fmm {
 
 // exact: a normal float is a double with the same sign, the exponent
@@ -81,5 +83,16 @@ __device__ __forceinline__ float d2f_rn(double d)
         u = sign | ((unsigned(e) << 23) + m + up);
     return __uint_as_float(u);
 }
+
+// double -> double-float: the rounded float and the rounded remainder (one
+// double subtraction, exact; the two conversions on the integer pipe)
+__device__ __forceinline__ dfloat df_from_double(double v)
+{
+    const float hi = d2f_rn(v);
+    return dfloat(hi, d2f_rn(v - f2d_bits(hi)));
+}
+
+// double-float -> double: both parts converted exactly, one double add
+__device__ __forceinline__ double df_to_double(dfloat v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
 
 }  // namespace fmm

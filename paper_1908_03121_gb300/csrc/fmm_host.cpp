@@ -482,7 +482,7 @@ static void free_device(fmm_tree_s *t)
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf, d.mono_woff,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.mass, d.mp, d.counters,
-                    d.partials, d.down, d.slot_mask};
+                    d.partials, d.up, d.down, d.slot_mask};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceTables{};
@@ -514,6 +514,12 @@ static int upload_tree(fmm_tree_s *t)
         (e = cudaMalloc(reinterpret_cast<void **>(&d.partials), part_b)) != cudaSuccess)
         return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
     d.workspace_bytes = mass_b + mp_b + part_b + 64 * sizeof(int32_t);
+    if (t->cfg.precision != FMM_FP64) {
+        size_t up_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 20 * NCELL * 2 * sizeof(float);
+        if ((e = cudaMalloc(reinterpret_cast<void **>(&d.up), up_b)) != cudaSuccess)
+            return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+        d.workspace_bytes += up_b;
+    }
     if (t->cfg.precision == FMM_MIXED) {
         size_t down_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 23 * NCELL * sizeof(float);
         if ((e = cudaMalloc(reinterpret_cast<void **>(&d.down), down_b)) != cudaSuccess)

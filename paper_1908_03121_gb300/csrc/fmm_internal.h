@@ -70,9 +70,12 @@ struct DeviceTables {
                                      // slot) an entry reaches from a node half
     // workspace
     void *mass = nullptr;            // [n][512] float or double
-    void *mp = nullptr;              // [n_refined][19][512] float or double
+    void *mp = nullptr;              // [n_refined][4][512][4] packed sources: float,
+                                     // double-float pairs or double
     int32_t *counters = nullptr;     // work-queue heads
     double *partials = nullptr;      // [n_leaf][8]
+    float *up = nullptr;             // mixed, dfloat: [n_refined][20][512] double-float
+                                     // (hi, lo) results of the upward pass per refined cell
     float *down = nullptr;           // mixed only: [n_refined][23][512] float copy
                                      // of each refined cell's final expansion (20)
                                      // and centre-of-mass offset from its centre (3)

@@ -136,7 +136,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fmm_m2l.cu", "fmm_tensor.cuh"):
+    for f in ("fmm_m2l.cu", "fmm_tensor.cuh", "fmm_dfloat.cuh", "fmm_convert.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1908_03121_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -11,7 +11,7 @@
 // component.
 // forces_kernel: phi = L0, g = -(L1 + dL1), f = m g, and fixed-order FP64
 // block sums of f and x cross f (plus the |f|, |x cross f| normalisers) per
-// leaf node; reduce_kernel folds those per tree.
+// leaf node; reduce_chunk_kernel and reduce_final_kernel fold those per tree.
 #include "fmm_convert.cuh"
 #include "fmm_internal.h"
 #include "fmm_tensor.cuh"
@@ -342,20 +342,35 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
     }
 }
 
-__global__ void __launch_bounds__(512) reduce_kernel(const int32_t *__restrict__ off,
-                                                     const int32_t *__restrict__ rows,
-                                                     const double *__restrict__ partials,
-                                                     double *__restrict__ totals)
+// Per-tree sums of the per-leaf-node partials in two fixed-order stages, so
+// the FP64 adds spread over many SMs: chunks of kReduceRows leaf rows per CTA,
+// then one warp per tree over its chunks.
+__global__ void __launch_bounds__(512) reduce_chunk_kernel(const int32_t *__restrict__ off,
+                                                           const int32_t *__restrict__ rows,
+                                                           const double *__restrict__ partials,
+                                                           double *__restrict__ chunk_sums)
 {
     __shared__ double sh[16][8];
-    const int tree = blockIdx.x;
+    const int tree = blockIdx.x, chunk = blockIdx.y;
+    const int lo = off[tree] + chunk * kReduceRows;
+    const int hi = min(lo + kReduceRows, off[tree + 1]);
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = off[tree] + threadIdx.x; i < off[tree + 1]; i += blockDim.x)
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] += partials[size_t(rows[i]) * 8 + k];
     block_sum<512, double, 8>(v, sh);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 8; ++k) totals[size_t(tree) * 8 + k] = v[k];
+        for (int k = 0; k < 8; ++k) chunk_sums[(size_t(tree) * gridDim.y + chunk) * 8 + k] = v[k];
+}
+
+__global__ void __launch_bounds__(32) reduce_final_kernel(const double *__restrict__ chunk_sums,
+                                                          int chunks, double *__restrict__ totals)
+{
+    const int tree = blockIdx.x, k = threadIdx.x;
+    if (k >= 8) return;
+    double v = 0.0;
+    for (int c = 0; c < chunks; ++c) v += chunk_sums[(size_t(tree) * chunks + c) * 8 + k];
+    totals[size_t(tree) * 8 + k] = v;
 }
 
 }  // namespace
@@ -399,8 +414,12 @@ cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *
         if (e != cudaSuccess) return e;
     }
     timing_begin(t, FMM_K_REDUCE, s);
-    reduce_kernel<<<unsigned(t->n_trees), 512, 0, s>>>(t->dev.tree_leaf_off, t->dev.tree_leaf_rows,
-                                                       t->dev.partials, totals);
+    const int chunks = t->plan.reduce_chunks;
+    reduce_chunk_kernel<<<dim3(unsigned(t->n_trees), unsigned(chunks)), 512, 0, s>>>(
+        t->dev.tree_leaf_off, t->dev.tree_leaf_rows, t->dev.partials, t->dev.chunk_sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_final_kernel<<<unsigned(t->n_trees), 32, 0, s>>>(t->dev.chunk_sums, chunks, totals);
     timing_end(t, s);
     return cudaGetLastError();
 }

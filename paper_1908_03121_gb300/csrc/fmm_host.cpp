@@ -299,6 +299,11 @@ static void build_stencils(fmm_tree_s *t)
     }
     P.stencil_union = 0;
     for (char c : in_union) P.stencil_union += c;
+    // the opening test on an integer squared offset n, as a threshold: the
+    // smallest n that is well separated (kernels compare integers only)
+    // (the same expression as well_separated on o2 = far_o2)
+    P.far_o2 = 1;
+    while (!(theta * theta * double(P.far_o2) > 1.0)) ++P.far_o2;
     // slots reachable by each entry from each half (z-cells 0-3 / 4-7) of a node
     t->slot_mask.assign(size_t(16) * P.ent_stride, 0);
     for (int p = 0; p < 8; ++p) {
@@ -482,7 +487,7 @@ static void free_device(fmm_tree_s *t)
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf, d.mono_woff,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.mass, d.mp, d.counters,
-                    d.partials, d.up, d.down, d.slot_mask};
+                    d.partials, d.chunk_sums, d.up, d.down, d.slot_mask};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceTables{};
@@ -507,13 +512,15 @@ static int upload_tree(fmm_tree_s *t)
     size_t mass_b = size_t(t->n) * NCELL * es;
     size_t mp_b = size_t(std::max<int64_t>(t->n_refined, 1)) * NMP * NCELL * es;
     size_t part_b = size_t(std::max<int64_t>(t->n_leaf, 1)) * 8 * sizeof(double);
+    size_t chunk_b = size_t(t->n_trees) * t->plan.reduce_chunks * 8 * sizeof(double);
     cudaError_t e;
     if ((e = cudaMalloc(&d.mass, mass_b)) != cudaSuccess ||
         (e = cudaMalloc(&d.mp, mp_b)) != cudaSuccess ||
         (e = cudaMalloc(reinterpret_cast<void **>(&d.counters), 64 * sizeof(int32_t))) != cudaSuccess ||
-        (e = cudaMalloc(reinterpret_cast<void **>(&d.partials), part_b)) != cudaSuccess)
+        (e = cudaMalloc(reinterpret_cast<void **>(&d.partials), part_b)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void **>(&d.chunk_sums), chunk_b)) != cudaSuccess)
         return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
-    d.workspace_bytes = mass_b + mp_b + part_b + 64 * sizeof(int32_t);
+    d.workspace_bytes = mass_b + mp_b + part_b + chunk_b + 64 * sizeof(int32_t);
     if (t->cfg.precision != FMM_FP64) {
         size_t up_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 20 * NCELL * 2 * sizeof(float);
         if ((e = cudaMalloc(reinterpret_cast<void **>(&d.up), up_b)) != cudaSuccess)
@@ -604,6 +611,10 @@ int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config
     for (int64_t i = 0; i < n_nodes; ++i)
         if (t->info[size_t(i)].leaf_row >= 0) t->tree_leaf_off[size_t(t->info[size_t(i)].tree) + 1]++;
     for (int32_t k = 0; k < t->n_trees; ++k) t->tree_leaf_off[size_t(k) + 1] += t->tree_leaf_off[size_t(k)];
+    int64_t most = 1;
+    for (int32_t k = 0; k < t->n_trees; ++k)
+        most = std::max<int64_t>(most, t->tree_leaf_off[size_t(k) + 1] - t->tree_leaf_off[size_t(k)]);
+    t->plan.reduce_chunks = int((most + kReduceRows - 1) / kReduceRows);
     t->tree_leaf_rows.assign(size_t(t->n_leaf), 0);
     {
         std::vector<int32_t> fill(t->tree_leaf_off.begin(), t->tree_leaf_off.end() - 1);
@@ -691,7 +702,7 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     int down = 0;
     for (int lev = 1; lev <= t->max_level; ++lev) down += P.nodes_at[size_t(lev)].count > 0;
     o->launches_m2l = m2l;
-    o->launches_step = up + m2l + down + 2;
+    o->launches_step = up + m2l + down + 3;
     if ((t->cfg.flags & FMM_FLAG_TIMING) && !t->host_only) {
         o->timing = 1;
         timing_fold(t);

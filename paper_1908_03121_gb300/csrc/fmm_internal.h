@@ -31,6 +31,7 @@ constexpr int NSIDE = 8;
 constexpr int NCELL = 512;
 constexpr int NCOMP = 20;
 constexpr int NMP = 16;          // packed same-level values per refined cell
+constexpr int kReduceRows = 1024;   // leaf rows per CTA of the first force-sum stage
 
 // per-level geometry table (device, [level][LEVEL_FIELDS] doubles), filled on
 // the host so that no kernel divides: h, 1/h, h^3, the level-unit ->
@@ -74,6 +75,7 @@ struct DeviceTables {
                                      // double-float pairs or double
     int32_t *counters = nullptr;     // work-queue heads
     double *partials = nullptr;      // [n_leaf][8]
+    double *chunk_sums = nullptr;    // [n_trees][reduce_chunks][8]
     float *up = nullptr;             // mixed, dfloat: [n_refined][20][512] double-float
                                      // (hi, lo) results of the upward pass per refined cell
     float *down = nullptr;           // mixed only: [n_refined][23][512] float copy
@@ -90,6 +92,8 @@ struct ListRange {
 struct Plan {
     // window geometry
     int reach = 5;                   // largest per-axis offset
+    int far_o2 = 5;                  // smallest well-separated squared offset
+    int reduce_chunks = 1;           // leaf-row chunks per tree of the force sums
     int sub = 9;                     // parity sub-window edge = 4 + reach
     int py = 12, pz = 112;           // padded pitches of a sub-window
     int sub_stride = 1008;           // elements per sub-window

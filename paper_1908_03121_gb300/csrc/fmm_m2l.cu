@@ -86,7 +86,7 @@ struct KParams {
     void *L;
     float *Lc;
     double *dL1;
-    double theta2;
+    int far_o2;              // cells at squared offset >= far_o2 are well separated
 };
 
 // ------------------------------------------------------------------ pack
@@ -921,8 +921,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
     const int b0 = slice * (NCELL / kRootSlices);
     for (int b = b0; b < b0 + NCELL / kRootSlices; ++b) {
         const int ox = (b & 7) - ax, oy = ((b >> 3) & 7) - ay, oz = (b >> 6) - az;
-        const double o2 = double(ox * ox + oy * oy + oz * oz);
-        const bool far = P.theta2 * o2 > 1.0;
+        const bool far = ox * ox + oy * oy + oz * oz >= P.far_o2;
         if (b == cell || !(far || leaf)) continue;
         const int pi = parity_index(b & 7, (b >> 3) & 7, b >> 6);
         Src<T> src;
@@ -1056,7 +1055,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     P.L = L;
     P.Lc = Lc;
     P.dL1 = dL1;
-    P.theta2 = t->cfg.theta * t->cfg.theta;
+    P.far_o2 = t->plan.far_o2;
     P.slot_mask = d.slot_mask;
     P.mono_woff = d.mono_woff;
     const int cap = t->tuning.ctas_per_sm;

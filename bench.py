@@ -60,6 +60,7 @@ def parse_args():
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--dfloat-steps", type=int, default=5)
+    p.add_argument("--theta035-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -448,6 +449,28 @@ def run_ours(args):
                     "net_torque": float(np.max(np.linalg.norm(totdf[:, 3:6], axis=1) / totdf[:, 7]))}
                 sdf.close()
             s64.close()
+
+        # the paper's production opening angle (theta = 0.35, the 1074-point
+        # stencil of Sec. 4.3) on the same tree and density, mixed precision
+        if args.precision == "mixed" and args.theta035_steps > 0:
+            s35 = F.Solver(c["desc"], 0.35, precision="mixed")
+            s35.rho.copy_(solver.rho)
+            s35.step()
+            autotune.tune(s35)
+            s35.capture()
+            ms35, _, _ = time_graph(torch, s35, args.theta035_steps, 1, flush, stream,
+                                    label="theta035_steps")
+            st35 = s35.tree.stats
+            inter35 = int(sum(st35["interactions"]))
+            target_cells = int(s35.tree.sizes["n_nodes"]) * 512
+            result["theta_0.35"] = {
+                "value": inter35 / (ms35 / 1000.0), "unit": UNIT, "ms_per_step": ms35,
+                "interactions_per_step": inter35,
+                "stencil_union": int(st35["stencil_union"]),
+                "paper_equivalent_stencil_evaluations_per_s":
+                    int(st35["stencil_union"]) * target_cells / (ms35 / 1000.0),
+                "note": "paper-equivalent = 1074-point stencil x all target cells / step time"}
+            s35.close()
 
         if world == 1 and not args.no_cpu_baseline:
             rate, info = oracle_rate(c, args.cpu_seconds)

@@ -18,7 +18,7 @@ if ROOT not in sys.path:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cfg5")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "dfloat", "fp64"])
     ap.add_argument("--pass", dest="which", default="m2l",
                     choices=["upward", "m2l", "downward", "forces", "step"])
     ap.add_argument("--reps", type=int, default=2)

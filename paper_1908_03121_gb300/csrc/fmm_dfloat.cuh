@@ -89,6 +89,21 @@ __device__ __forceinline__ dfloat operator/(dfloat a, dfloat b)
     return df_fast(q1, q2);
 }
 
+// a * b + c in one pass: the product's error terms join the sum's low part
+// before a single renormalisation (one Fast2Sum fewer than a product then a
+// sum)
+__device__ __forceinline__ dfloat fmadd(dfloat a, dfloat b, dfloat c)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    float s, t;
+    df_two_sum(p, c.hi, s, t);
+    t += e + c.lo;
+    return df_fast(s, t);
+}
+
 __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
 __device__ __forceinline__ dfloat &operator-=(dfloat &a, dfloat b) { return a = a - b; }
 __device__ __forceinline__ dfloat &operator*=(dfloat &a, dfloat b) { return a = a * b; }

@@ -27,32 +27,33 @@ __device__ __forceinline__ void shift_increments(const T P[20], const T d[3], T 
 {
     const T dd[6] = {d[0] * d[0], d[0] * d[1], d[0] * d[2], d[1] * d[1], d[1] * d[2], d[2] * d[2]};
     // order 0: P1.d + 1/2 P2:dd + 1/6 P3:ddd
-    T v0 = T(0);
+    T v0 = P[1] * d[0];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v0 += P[1 + i] * d[i];
+    for (int i = 1; i < 3; ++i) v0 = fmadd(P[1 + i], d[i], v0);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) v0 += T(0.5 * mult2(q)) * P[4 + q] * dd[q];
+    for (int q = 0; q < 6; ++q) v0 = fmadd(T(0.5 * mult2(q)) * P[4 + q], dd[q], v0);
 #pragma unroll
     for (int q = 0; q < 10; ++q)
-        v0 += T(mult3(q) / 6.0) * P[10 + q] * dd[r2_of(i3_at(q, 0), i3_at(q, 1))] * d[i3_at(q, 2)];
+        v0 = fmadd(T(mult3(q) / 6.0) * P[10 + q], dd[r2_of(i3_at(q, 0), i3_at(q, 1))] * d[i3_at(q, 2)],
+                   v0);
     out[0] = v0;
     // order 1: P2_ij d_j + 1/2 P3_ijk d_j d_k
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        T v = T(0);
+        T v = P[4 + r2_of(i, 0)] * d[0];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) v += P[4 + r2_of(i, j)] * d[j];
+        for (int j = 1; j < 3; ++j) v = fmadd(P[4 + r2_of(i, j)], d[j], v);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) v += T(0.5 * mult2(q)) * P[10 + r3_of(i, q)] * dd[q];
+        for (int q = 0; q < 6; ++q) v = fmadd(T(0.5 * mult2(q)) * P[10 + r3_of(i, q)], dd[q], v);
         out[1 + i] = v;
     }
     if (NMAX >= 2) {
         // order 2: P3_ijk d_k ; order 3: nothing
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            T v = T(0);
+            T v = P[10 + r3_ijk(i2_at(q, 0), i2_at(q, 1), 0)] * d[0];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) v += P[10 + r3_ijk(i2_at(q, 0), i2_at(q, 1), k)] * d[k];
+            for (int k = 1; k < 3; ++k) v = fmadd(P[10 + r3_ijk(i2_at(q, 0), i2_at(q, 1), k)], d[k], v);
             out[4 + q] = v;
         }
 #pragma unroll
@@ -60,14 +61,11 @@ __device__ __forceinline__ void shift_increments(const T P[20], const T d[3], T 
     }
 }
 
-// FP64 path: the whole re-centring in double.  The cell's own same-level
-// result is double (FP64), or the double sum of a (hi, lo) float pair
-// (double-float precision, PAIR).
-template <int NMAX, bool PAIR>
+// FP64 path: the whole re-centring in double.
+template <int NMAX>
 __device__ __forceinline__ void l2l_cell_fp64(const NodeInfo &ni, int node, int c,
                                               const double *__restrict__ lv,
-                                              const void *__restrict__ Lv,
-                                              const float *__restrict__ Lc, const double *dL1,
+                                              const void *__restrict__ Lv, const double *dL1,
                                               const double *__restrict__ com,
                                               double *__restrict__ L64, double *dacc, double lo_x,
                                               double lo_y, double lo_z)
@@ -80,8 +78,7 @@ __device__ __forceinline__ void l2l_cell_fp64(const NodeInfo &ni, int node, int 
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
         const size_t idx = (size_t(node) * NCOMP + k) * NCELL + c;
-        const double own = PAIR ? pair_to_double(static_cast<const float *>(Lv)[idx], Lc[idx])
-                                : static_cast<const double *>(Lv)[idx];
+        const double own = static_cast<const double *>(Lv)[idx];
         out[k] = own * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
     }
     double corr[3];
@@ -208,6 +205,91 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
     }
 }
 
+// Double-float precision: the shift increments are formed in double-float
+// (about 48 bits, FP32 pipe) from double-float copies of the parent's final
+// expansion and centre-of-mass offset (`down`, written by the parent level),
+// folded into the cell's own (hi, lo) level-unit pair, and the one FP64
+// operation per component is again the final accumulation
+// L64 = (own + increments) G h^-(n+1) + L64_parent.
+template <int NMAX>
+__device__ __forceinline__ void l2l_cell_df(const NodeInfo &ni, int node, int c,
+                                            const NodeInfo *__restrict__ info,
+                                            const double *__restrict__ lv,
+                                            const dfloat *__restrict__ lvdf,
+                                            const float *__restrict__ Lhi,
+                                            const float *__restrict__ Llo, const double *dL1,
+                                            const double *__restrict__ com,
+                                            double *__restrict__ L64, double *dacc,
+                                            dfloat *__restrict__ down, double lo_x, double lo_y,
+                                            double lo_z)
+{
+    constexpr int NK = NMAX == 1 ? 4 : 20;
+    const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+    const double *L = lv + ni.level * LEVEL_FIELDS;
+    const dfloat *Ld = lvdf + ni.level * LEVEL_DF_FIELDS;
+    const double sc[4] = {L[LV_S0], L[LV_S1], L[LV_S2], L[LV_S3]};
+    dfloat own[20];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const size_t idx = (size_t(node) * NCOMP + k) * NCELL + c;
+        own[k] = dfloat(Lhi[idx], Llo[idx]);
+    }
+    dfloat offc[3] = {dfloat(0.f), dfloat(0.f), dfloat(0.f)};   // own centre-of-mass offset
+    if (NMAX == 3) {
+        const double h = L[LV_H];
+        offc[0] = df_from_double(com[(size_t(node) * 3 + 0) * NCELL + c] -
+                                 fma(f2d_bits(float(8 * ni.ix + x) + 0.5f), h, lo_x));
+        offc[1] = df_from_double(com[(size_t(node) * 3 + 1) * NCELL + c] -
+                                 fma(f2d_bits(float(8 * ni.iy + y) + 0.5f), h, lo_y));
+        offc[2] = df_from_double(com[(size_t(node) * 3 + 2) * NCELL + c] -
+                                 fma(f2d_bits(float(8 * ni.iz + z) + 0.5f), h, lo_z));
+    }
+    double out[20];
+    double corr[3];
+    if (ni.parent >= 0) {
+        const int pc = (4 * (ni.ix & 1) + (x >> 1)) + 8 * (4 * (ni.iy & 1) + (y >> 1)) +
+                       64 * (4 * (ni.iz & 1) + (z >> 1));
+        const int prow = info[ni.parent].mp_row;
+        const dfloat *pd = down + size_t(prow) * 23 * NCELL + pc;
+        dfloat Pd[20];
+#pragma unroll
+        for (int k = 0; k < 20; ++k) Pd[k] = pd[k * NCELL];
+        const dfloat hc = Ld[0];
+        const dfloat d[3] = {(x & 1 ? 0.5f : -0.5f) * hc + offc[0] - pd[20 * NCELL],
+                             (y & 1 ? 0.5f : -0.5f) * hc + offc[1] - pd[21 * NCELL],
+                             (z & 1 ? 0.5f : -0.5f) * hc + offc[2] - pd[22 * NCELL]};
+        dfloat inc[20];
+        shift_increments<dfloat, NMAX>(Pd, d, inc);
+#pragma unroll
+        for (int k = 0; k < NK; ++k) own[k] += inc[k] * Ld[1 + (k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3)];
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            out[k] = fma(df_to_double(own[k]), sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3],
+                         L64[(size_t(ni.parent) * NCOMP + k) * NCELL + pc]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            corr[a] = fma(dL1[(size_t(node) * 3 + a) * NCELL + c], sc[1],
+                          dacc[(size_t(ni.parent) * 3 + a) * NCELL + pc]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            out[k] = df_to_double(own[k]) * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc[1];
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) L64[(size_t(node) * NCOMP + k) * NCELL + c] = out[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dacc[(size_t(node) * 3 + a) * NCELL + c] = corr[a];
+    if (NMAX == 3) {
+        dfloat *od = down + size_t(ni.mp_row) * 23 * NCELL + c;
+#pragma unroll
+        for (int k = 0; k < 20; ++k) od[k * NCELL] = df_from_double(out[k]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) od[(20 + a) * NCELL] = offc[a];
+    }
+}
+
 // 64 threads per CTA, 8 CTAs per node, so that the few nodes of a coarse
 // level still spread their FP64 work over many SMs
 constexpr int kSliceThreads = 64;
@@ -217,6 +299,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kSliceThreads) l2l_kernel(const NodeInfo *__restrict__ info,
                                                             const int32_t *__restrict__ nodes,
                                                             const double *__restrict__ levels,
+                                                            const dfloat *__restrict__ levels_df,
                                                             const void *__restrict__ Lv,
                                                             const float *__restrict__ Lc,
                                                             const double *dL1,  // may alias dacc
@@ -236,14 +319,22 @@ __global__ void __launch_bounds__(kSliceThreads) l2l_kernel(const NodeInfo *__re
         else
             l2l_cell_mixed<3>(ni, node, c, info, levels, Lhi, Lc, dL1, com, L64, dacc, down, lo_x,
                               lo_y, lo_z);
-    } else {
-        constexpr bool PAIR = MODE == FMM_DFLOAT;
+    } else if constexpr (MODE == FMM_DFLOAT) {
+        const float *Lhi = static_cast<const float *>(Lv);
+        dfloat *dd = reinterpret_cast<dfloat *>(down);
         if (ni.leaf_row >= 0)
-            l2l_cell_fp64<1, PAIR>(ni, node, c, levels, Lv, Lc, dL1, com, L64, dacc, lo_x, lo_y,
-                                   lo_z);
+            l2l_cell_df<1>(ni, node, c, info, levels, levels_df, Lhi, Lc, dL1, com, L64, dacc, dd,
+                           lo_x, lo_y, lo_z);
         else
-            l2l_cell_fp64<3, PAIR>(ni, node, c, levels, Lv, Lc, dL1, com, L64, dacc, lo_x, lo_y,
-                                   lo_z);
+            l2l_cell_df<3>(ni, node, c, info, levels, levels_df, Lhi, Lc, dL1, com, L64, dacc, dd,
+                           lo_x, lo_y, lo_z);
+    } else {
+        if (ni.leaf_row >= 0)
+            l2l_cell_fp64<1>(ni, node, c, levels, Lv, dL1, com, L64, dacc, lo_x, lo_y,
+                                    lo_z);
+        else
+            l2l_cell_fp64<3>(ni, node, c, levels, Lv, dL1, com, L64, dacc, lo_x, lo_y,
+                                    lo_z);
     }
 }
 
@@ -384,16 +475,17 @@ cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L, cons
     const auto &c = t->cfg;
     const unsigned grid = unsigned(r.count * 8);
     const int32_t *nodes = t->dev.lists + r.off;
+    const dfloat *ldf = reinterpret_cast<const dfloat *>(t->dev.levels_df);
     if (c.precision == FMM_MIXED)
-        l2l_kernel<FMM_MIXED><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, L,
+        l2l_kernel<FMM_MIXED><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, ldf, L,
                                                             Lc, dL1, com, L64, dacc, t->dev.down,
                                                             c.box_lo[0], c.box_lo[1], c.box_lo[2]);
     else if (c.precision == FMM_DFLOAT)
-        l2l_kernel<FMM_DFLOAT><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, L,
-                                                             Lc, dL1, com, L64, dacc, nullptr,
+        l2l_kernel<FMM_DFLOAT><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, ldf, L,
+                                                             Lc, dL1, com, L64, dacc, t->dev.down,
                                                              c.box_lo[0], c.box_lo[1], c.box_lo[2]);
     else
-        l2l_kernel<FMM_FP64><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, L,
+        l2l_kernel<FMM_FP64><<<grid, kSliceThreads, 0, s>>>(t->dev.info, nodes, t->dev.levels, ldf, L,
                                                            Lc, dL1, com, L64, dacc, nullptr,
                                                            c.box_lo[0], c.box_lo[1], c.box_lo[2]);
     return cudaGetLastError();

@@ -486,7 +486,7 @@ static void free_device(fmm_tree_s *t)
     t->timer.ev.clear();
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf, d.mono_woff,
-                    d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.mass, d.mp, d.counters,
+                    d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.levels_df, d.mass, d.mp, d.counters,
                     d.partials, d.chunk_sums, d.up, d.down, d.slot_mask};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -504,6 +504,7 @@ static int upload_tree(fmm_tree_s *t)
         (rc = upload(&d.mono_woff, t->mono_woff)) ||
         (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||
         (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)) || (rc = upload(&d.levels, t->levels)) ||
+        (rc = upload(&d.levels_df, t->levels_df)) ||
         (rc = upload(&d.slot_mask, t->slot_mask)))
         return rc;
     // packed masses and moments: float (mixed), (hi, lo) float pairs (dfloat), double
@@ -527,8 +528,10 @@ static int upload_tree(fmm_tree_s *t)
             return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
         d.workspace_bytes += up_b;
     }
-    if (t->cfg.precision == FMM_MIXED) {
-        size_t down_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 23 * NCELL * sizeof(float);
+    if (t->cfg.precision != FMM_FP64) {
+        // float copies (mixed) or (hi, lo) pairs (double-float)
+        size_t down_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 23 * NCELL * sizeof(float) *
+                        (t->cfg.precision == FMM_DFLOAT ? 2 : 1);
         if ((e = cudaMalloc(reinterpret_cast<void **>(&d.down), down_b)) != cudaSuccess)
             return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
         d.workspace_bytes += down_b;
@@ -638,6 +641,17 @@ int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config
         L[LV_S2] = L[LV_S1] / h;
         L[LV_S3] = L[LV_S2] / h;
         for (int k = 0; k < 4; ++k) L[LV_R0 + k] = 1.0 / L[LV_S0 + k];
+    }
+    // the same h and inverse scales as (hi, lo) float pairs
+    t->levels_df.assign(size_t(t->max_level + 1) * LEVEL_DF_FIELDS * 2, 0.f);
+    for (int lev = 1; lev <= t->max_level; ++lev) {
+        const double *L = &t->levels[size_t(lev) * LEVEL_FIELDS];
+        const double v[LEVEL_DF_FIELDS] = {L[LV_H], L[LV_R0], L[LV_R1], L[LV_R2], L[LV_R3]};
+        for (int k = 0; k < LEVEL_DF_FIELDS; ++k) {
+            float *o = &t->levels_df[(size_t(lev) * LEVEL_DF_FIELDS + k) * 2];
+            o[0] = float(v[k]);
+            o[1] = float(v[k] - double(o[0]));
+        }
     }
     if (!t->host_only) {
         if (cudaGetDevice(&t->device) != cudaSuccess) {

@@ -38,6 +38,9 @@ constexpr int kReduceRows = 1024;   // leaf rows per CTA of the first force-sum 
 // physical scales G h^-(n+1) of orders n = 0..3 and their inverses
 constexpr int LEVEL_FIELDS = 12;
 enum { LV_H = 0, LV_IH, LV_H3, LV_S0, LV_S1, LV_S2, LV_S3, LV_R0, LV_R1, LV_R2, LV_R3 };
+// the same h and inverse scales R0..R3 as double-float (hi, lo) pairs,
+// [level][LEVEL_DF_FIELDS][2] floats
+constexpr int LEVEL_DF_FIELDS = 5;
 
 // per-node table row (device and host)
 struct NodeInfo {
@@ -67,6 +70,7 @@ struct DeviceTables {
     int32_t *tree_leaf_off = nullptr;   // [n_trees + 1]
     int32_t *tree_leaf_rows = nullptr;  // [n_leaf]
     double *levels = nullptr;        // [max_level + 1][LEVEL_FIELDS]
+    float *levels_df = nullptr;      // [max_level + 1][LEVEL_DF_FIELDS][2]
     int32_t *slot_mask = nullptr;    // [8][2][ent_stride]: neighbour slots (bit per
                                      // slot) an entry reaches from a node half
     // workspace
@@ -78,9 +82,10 @@ struct DeviceTables {
     double *chunk_sums = nullptr;    // [n_trees][reduce_chunks][8]
     float *up = nullptr;             // mixed, dfloat: [n_refined][20][512] double-float
                                      // (hi, lo) results of the upward pass per refined cell
-    float *down = nullptr;           // mixed only: [n_refined][23][512] float copy
-                                     // of each refined cell's final expansion (20)
-                                     // and centre-of-mass offset from its centre (3)
+    float *down = nullptr;           // mixed: [n_refined][23][512] float copy, double-
+                                     // float: the same as (hi, lo) pairs, of each refined
+                                     // cell's final expansion (20) and centre-of-mass
+                                     // offset from its centre (3)
     size_t workspace_bytes = 0;
 };
 
@@ -136,6 +141,7 @@ struct fmm_tree_s {
     std::vector<int32_t> mono_woff;
     std::vector<int32_t> tree_leaf_off, tree_leaf_rows;
     std::vector<double> levels;
+    std::vector<float> levels_df;
     std::vector<int32_t> slot_mask;
     fmm::Plan plan;
     fmm_tuning tuning{};

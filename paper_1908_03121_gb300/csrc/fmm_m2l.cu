@@ -90,6 +90,15 @@ struct KParams {
 };
 
 // ------------------------------------------------------------------ pack
+// a double as the element type (double-float: split with the conversions on
+// the integer pipe)
+template <typename T>
+__device__ __forceinline__ T elem_from_double(double v)
+{
+    if constexpr (kDF<T>) return df_from_double(v);
+    else return T(v);
+}
+
 // Mixed precision: everything but the centre-of-mass offset in float, with
 // the double -> float conversions on the integer pipe (GB300's FP64 unit,
 // which also runs conversions, would otherwise bound this pass); the
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ 
                    mp, lo_x, lo_y, lo_z);
         return;
     }
-    mass[size_t(node) * NCELL + pi] = T(Mn[0]);
+    mass[size_t(node) * NCELL + pi] = elem_from_double<T>(Mn[0]);
     if (ni.mp_row < 0) return;
     const double h = levels[ni.level * LEVEL_FIELDS + LV_H];
     const double ih = levels[ni.level * LEVEL_FIELDS + LV_IH];
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ 
 #pragma unroll
     for (int g = 0; g < 4; ++g)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) out[size_t(g) * NCELL * 4 + j] = T(v[4 * g + j]);
+        for (int j = 0; j < 4; ++j) out[size_t(g) * NCELL * 4 + j] = elem_from_double<T>(v[4 * g + j]);
 }
 
 // ------------------------------------------------------------ common bits
@@ -458,11 +467,6 @@ __device__ __forceinline__ void zero_moments(Src<T> &s)
     for (int q = 0; q < 7; ++q) s.B3[q] = T(0);
 }
 
-// a * b + c in the element type (fused in float and double)
-__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ dfloat fmadd(dfloat a, dfloat b, dfloat c) { return a * b + c; }
-
 // One source (multipole if SRC_MP, else a point mass m0 = s.m0) into a
 // multipole target's 16 traceless accumulators and the correction sum
 //   S_i += sum_q (B3_B - M0_B a3_A)_q D4[i, q],  a3_A = B3_A / M0_A,
@@ -700,8 +704,8 @@ __device__ __forceinline__ void mono_entry(const T *W, int wstride, int base0, i
         const T m1 = W[b * wstride + base1 + w];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            A[b].part[k] += c[k] * m0;
-            B[b].part[k] += c[k] * m1;
+            A[b].part[k] = fmadd(c[k], m0, A[b].part[k]);
+            B[b].part[k] = fmadd(c[k], m1, B[b].part[k]);
         }
     }
 }

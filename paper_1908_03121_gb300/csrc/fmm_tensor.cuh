@@ -57,6 +57,11 @@ __host__ __device__ constexpr int i3_at(int q, int which)
     return t[q][which];
 }
 
+// a * b + c in the element type (fused in float and double; fmm_dfloat.cuh
+// has the double-float one)
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+
 template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
@@ -144,44 +149,44 @@ struct DTraceless {
     template <bool WITH_D4>
     __device__ __forceinline__ void eval(T x, T y, T z)
     {
-        const T r2 = x * x + y * y + z * z;
+        const T r2 = fmadd(x, x, fmadd(y, y, z * z));
         const T ri = rsqrt_t<T>(r2);
         const T ri2 = ri * ri;
         const T d1 = -ri * ri2;
-        const T d2 = T(-3) * d1 * ri2;
-        const T d3 = T(-5) * d2 * ri2;
+        const T d2 = d1 * (T(-3) * ri2);
+        const T d3 = d2 * (T(-5) * ri2);
         D0 = ri;
         D1[0] = d1 * x; D1[1] = d1 * y; D1[2] = d1 * z;
         const T xx = x * x, yy = y * y, xy = x * y, xz = x * z, yz = y * z;
-        D2[0] = d2 * xx + d1;
-        D2[1] = d2 * yy + d1;
+        D2[0] = fmadd(d2, xx, d1);
+        D2[1] = fmadd(d2, yy, d1);
         D2[2] = d2 * xy;
         D2[3] = d2 * xz;
         D2[4] = d2 * yz;
         const T d3x = d3 * x, d3y = d3 * y;
         const T t2 = T(3) * d2;
-        D3[0] = d3x * xx + t2 * x;      // xxx
-        D3[1] = d3x * xy + d2 * y;      // xxy
-        D3[2] = d3x * xz + d2 * z;      // xxz
-        D3[3] = d3x * yy + d2 * x;      // xyy
-        D3[4] = d3x * yz;               // xyz
-        D3[5] = d3y * yy + t2 * y;      // yyy
-        D3[6] = d3y * yz + d2 * z;      // yyz
-        D3[7] = -(D3[0] + D3[3]);       // xzz
-        D3[8] = -(D3[1] + D3[5]);       // yzz
+        D3[0] = fmadd(d3x, xx, t2 * x);      // xxx
+        D3[1] = fmadd(d3x, xy, d2 * y);      // xxy
+        D3[2] = fmadd(d3x, xz, d2 * z);      // xxz
+        D3[3] = fmadd(d3x, yy, d2 * x);      // xyy
+        D3[4] = d3x * yz;                    // xyz
+        D3[5] = fmadd(d3y, yy, t2 * y);      // yyy
+        D3[6] = fmadd(d3y, yz, d2 * z);      // yyz
+        D3[7] = -(D3[0] + D3[3]);            // xzz
+        D3[8] = -(D3[1] + D3[5]);            // yzz
         if (WITH_D4) {
-            const T d4 = T(-7) * d3 * ri2;
+            const T d4 = d3 * (T(-7) * ri2);
             const T t3 = T(3) * d3, t6 = T(6) * d3;
             const T d4xx = d4 * xx, d4yy = d4 * yy, d4xy = d4 * xy;
-            const T xxxx = d4xx * xx + t6 * xx + t2;
-            const T xxxy = d4xx * xy + t3 * xy;
-            const T xxxz = d4xx * xz + t3 * xz;
-            const T xxyy = d4xx * yy + d3 * (xx + yy) + d2;
-            const T xxyz = d4xx * yz + d3 * yz;
-            const T xyyy = d4xy * yy + t3 * xy;
-            const T xyyz = d4xy * yz + d3 * xz;
-            const T yyyy = d4yy * yy + t6 * yy + t2;
-            const T yyyz = d4yy * yz + t3 * yz;
+            const T xxxx = fmadd(d4xx, xx, fmadd(t6, xx, t2));
+            const T xxxy = fmadd(d4xx, xy, t3 * xy);
+            const T xxxz = fmadd(d4xx, xz, t3 * xz);
+            const T xxyy = fmadd(d4xx, yy, fmadd(d3, xx + yy, d2));
+            const T xxyz = fmadd(d4xx, yz, d3 * yz);
+            const T xyyy = fmadd(d4xy, yy, t3 * xy);
+            const T xyyz = fmadd(d4xy, yz, d3 * xz);
+            const T yyyy = fmadd(d4yy, yy, fmadd(t6, yy, t2));
+            const T yyyz = fmadd(d4yy, yz, t3 * yz);
             const T xxzz = -(xxxx + xxyy), xyzz = -(xxxy + xyyy), yyzz = -(xxyy + yyyy);
             // slices in the B3 basis (xxx xxy xxz xyy xyz yyy yyz)
             U[0][0] = xxxx; U[0][1] = xxxy; U[0][2] = xxxz; U[0][3] = xxyy;

@@ -367,25 +367,28 @@ def run_ours(args):
 
     if rank == 0:
         # per-kernel device times, measured live with events on the launch stream
-        tsolver = F.Solver(c["desc"], c["theta"], precision=args.precision, timing=True)
-        F.fmm_set_tuning(tsolver.tree, **best)
-        tsolver.rho.copy_(solver.rho)
-        for _ in range(2):
-            flush()
-            tsolver.step()
-        tsolver.kernel_times()          # discard warm-up timings
-        nrep = max(3, min(args.steps, 20))
-        for _ in range(nrep):
-            flush()
-            tsolver.step()
-        kt = tsolver.kernel_times()
-        tsolver.close()
-        per_kernel = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0,
-                          "ms_per_step": v[0] / nrep, "launches_per_step": v[1] / nrep}
-                      for k, v in kt.items() if v[1]}
-        step_kernel_ms = sum(v["ms_per_step"] for v in per_kernel.values())
-        for v in per_kernel.values():
-            v["share"] = v["ms_per_step"] / step_kernel_ms if step_kernel_ms else 0.0
+        def kernel_times(precision, tuning, nrep):
+            tsolver = F.Solver(c["desc"], c["theta"], precision=precision, timing=True)
+            F.fmm_set_tuning(tsolver.tree, **tuning)
+            tsolver.rho.copy_(solver.rho)
+            for _ in range(2):
+                flush()
+                tsolver.step()
+            tsolver.kernel_times()          # discard warm-up timings
+            for _ in range(nrep):
+                flush()
+                tsolver.step()
+            kt = tsolver.kernel_times()
+            tsolver.close()
+            out = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0,
+                       "ms_per_step": v[0] / nrep, "launches_per_step": v[1] / nrep}
+                   for k, v in kt.items() if v[1]}
+            total = sum(v["ms_per_step"] for v in out.values())
+            for v in out.values():
+                v["share"] = v["ms_per_step"] / total if total else 0.0
+            return out
+
+        per_kernel = kernel_times(args.precision, best, max(3, min(args.steps, 20)))
         result["kernels"] = per_kernel
         inter = stats["interactions"]
         kin = stats["kernel_interactions"]
@@ -435,7 +438,7 @@ def run_ours(args):
                 sdf = F.Solver(c["desc"], c["theta"], precision="dfloat")
                 sdf.rho.copy_(solver.rho)
                 sdf.step()
-                autotune.tune(sdf)
+                best_df = autotune.tune(sdf)[0]
                 sdf.capture()
                 msdf, _, _ = time_graph(torch, sdf, args.dfloat_steps, 1, flush, stream,
                                         label="dfloat_steps")
@@ -448,6 +451,8 @@ def run_ours(args):
                     "net_force": float(np.max(np.linalg.norm(totdf[:, 0:3], axis=1) / totdf[:, 6])),
                     "net_torque": float(np.max(np.linalg.norm(totdf[:, 3:6], axis=1) / totdf[:, 7]))}
                 sdf.close()
+                result["conserving_path"]["kernels"] = {
+                    k: round(v["ms_per_step"], 4) for k, v in kernel_times("dfloat", best_df, 3).items()}
             s64.close()
 
         # the paper's production opening angle (theta = 0.35, the 1074-point

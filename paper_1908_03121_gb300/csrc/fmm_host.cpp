@@ -44,12 +44,6 @@ bool well_separated(double theta, int64_t ox, int64_t oy, int64_t oz)
 }
 
 // pad a pitch up to the next value congruent to want (mod 32)
-int pad_to(int min_value, int want)
-{
-    int v = min_value;
-    while (((v % 32) + 32) % 32 != want) ++v;
-    return v;
-}
 
 // Monopole-monopole coefficients of one offset o (target minus source
 // position is -o cell widths): L0 += c0 m, L1 += c1 m in level units.

@@ -33,6 +33,16 @@ constexpr int NCOMP = 20;
 constexpr int NMP = 16;          // packed same-level values per refined cell
 constexpr int kReduceRows = 1024;   // leaf rows per CTA of the first force-sum stage
 
+// pad a pitch up to the next value congruent to want (mod 32): the halo
+// window's row and plane pitches, chosen so that the 32 lanes of a warp hit
+// distinct shared-memory banks
+__host__ __device__ constexpr int pad_to(int min_value, int want)
+{
+    int v = min_value;
+    while (((v % 32) + 32) % 32 != want) ++v;
+    return v;
+}
+
 // per-level geometry table (device, [level][LEVEL_FIELDS] doubles), filled on
 // the host so that no kernel divides: h, 1/h, h^3, the level-unit ->
 // physical scales G h^-(n+1) of orders n = 0..3 and their inverses

@@ -249,20 +249,32 @@ __device__ __forceinline__ int window_decode(T v)
     }
 }
 
-template <typename T>
+// Window geometry of reach R: the host's pitches (same pad_to), as
+// compile-time constants; RR = 0 takes them from the kernel parameters.
+template <int RR>
+struct WinGeo {
+    static constexpr int R = RR, SUB = 4 + RR, E = 8 + 2 * RR;
+    static constexpr int PY = pad_to(SUB, 12), PZ = pad_to(SUB * PY, 16), SUB_STRIDE = SUB * PZ;
+};
+
+template <typename T, int RR = 0>
 __device__ __forceinline__ void stage_window_async(T *W, const int *s_nbr, const int *s_leaf,
                                                    const T *__restrict__ mass, const KParams &P,
                                                    const int *s_row = nullptr)
 {
-    const int R = P.reach;
-    const int E = 8 + 2 * R;
+    using G = WinGeo<RR>;
+    const int R = RR ? G::R : P.reach;
+    const int E = RR ? G::E : 8 + 2 * R;
+    const int py = RR ? G::PY : P.py, pz = RR ? G::PZ : P.pz;
+    const int sub_stride = RR ? G::SUB_STRIDE : P.sub_stride;
     for (int t = threadIdx.x; t < E * E; t += blockDim.x) {
         const int ux = t % E, uy = t / E;
         const int bx = ux - R + 8, by = uy - R + 8;           // >= 1
         const int sxy = (bx >> 3) + 3 * (by >> 3);
         const int lx = bx & 7, ly = by & 7;
         const int pxy = ((lx & 1) + 2 * (ly & 1)) * 64 + (lx >> 1) + 4 * (ly >> 1);
-        const int wxy = ((ux & 1) + 2 * (uy & 1)) * P.sub_stride + (ux >> 1) + P.py * (uy >> 1);
+        const int wxy = ((ux & 1) + 2 * (uy & 1)) * sub_stride + (ux >> 1) + py * (uy >> 1);
+#pragma unroll 4
         for (int uz = 0; uz < E; ++uz) {
             const int bz = uz - R + 8;
             const int slot = sxy + 9 * (bz >> 3);
@@ -270,7 +282,7 @@ __device__ __forceinline__ void stage_window_async(T *W, const int *s_nbr, const
             const bool ok = s_leaf[slot] != 0;
             const int pi = pxy + 256 * (lz & 1) + 16 * (lz >> 1);
             const T *src = ok ? mass + size_t(s_nbr[slot]) * NCELL + pi : mass;
-            const int wi = wxy + 4 * (uz & 1) * P.sub_stride + P.pz * (uz >> 1);
+            const int wi = wxy + 4 * (uz & 1) * sub_stride + pz * (uz >> 1);
             const int row = s_row ? s_row[slot] : -1;
             if (row >= 0)
                 W[wi] = window_index<T>((row * 4 * NCELL + pi) * 4);
@@ -690,18 +702,20 @@ __device__ __forceinline__ void load4_shared(const T *p, T v[4])
     }
 }
 
-template <typename T, int NB>
-__device__ __forceinline__ void mono_entry(const T *W, int wstride, int base0, int base1,
-                                           const int *woff, const T *coef, int e,
+// Wb = the window at this thread's first target cell; the NB windows are
+// WSTRIDE apart and the second target cell DZ1 further on (compile-time
+// offsets, folded into the shared-memory loads)
+template <typename T, int NB, int WSTRIDE, int DZ1>
+__device__ __forceinline__ void mono_entry(const T *Wb, const int *woff, const T *coef, int e,
                                            Acc<T, 4> (&A)[NB], Acc<T, 4> (&B)[NB])
 {
-    const int w = woff[e];
+    const T *src = Wb + woff[e];
     T c[4];
     load4_shared<T>(coef + 4 * e, c);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const T m0 = W[b * wstride + base0 + w];
-        const T m1 = W[b * wstride + base1 + w];
+        const T m0 = src[b * WSTRIDE];
+        const T m1 = src[b * WSTRIDE + DZ1];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             A[b].part[k] = fmadd(c[k], m0, A[b].part[k]);
@@ -710,7 +724,7 @@ __device__ __forceinline__ void mono_entry(const T *W, int wstride, int base0, i
     }
 }
 
-// dynamic shared memory of mono_kernel<T, NB>: NB windows, the weight table
+// dynamic shared memory of mono_kernel<T, NB, R>: NB windows, the weight table
 // of parity 0 and the window offsets of all parities
 template <typename T>
 size_t mono_smem_bytes(int nb, size_t window_bytes, int ent_stride)
@@ -718,11 +732,12 @@ size_t mono_smem_bytes(int nb, size_t window_bytes, int ent_stride)
     return nb * window_bytes + size_t(ent_stride) * 4 * sizeof(T) + size_t(8) * ent_stride * sizeof(int);
 }
 
-template <typename T, int NB>
+template <typename T, int NB, int RR>
 __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
 {
+    using G = WinGeo<RR>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int wstride = 8 * P.sub_stride;
+    constexpr int wstride = 8 * G::SUB_STRIDE;
     T *W = reinterpret_cast<T *>(smem_raw);
     T *s_coef = W + NB * wstride;
     int *s_woff = reinterpret_cast<int *>(s_coef + 4 * P.ent_stride);
@@ -740,8 +755,8 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
     const int cx = lane & 3, cy = (lane >> 2) & 3, cz = lane >> 4;
     const int *woff = s_woff + p * P.ent_stride;
     const T *mass = static_cast<const T *>(P.mass);
-    const int base0 = cx + P.py * cy + P.pz * cz;
-    const int base1 = base0 + 2 * P.pz;
+    const int base0 = cx + G::PY * cy + G::PZ * cz;
+    constexpr int dz1 = 2 * G::PZ;              // the second target cell, z + 4
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(P.counter, NB);
         __syncthreads();
@@ -756,7 +771,7 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
         __syncthreads();
 #pragma unroll
         for (int b = 0; b < NB; ++b)
-            if (nodes[b] >= 0) stage_window_async<T>(W + b * wstride, s_nbr[b], s_leaf[b], mass, P);
+            if (nodes[b] >= 0) stage_window_async<T, RR>(W + b * wstride, s_nbr[b], s_leaf[b], mass, P);
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
@@ -770,14 +785,14 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
         for (; e + kChunk <= n_ent; e += kChunk) {
 #pragma unroll
             for (int j = 0; j < kChunk; ++j)
-                mono_entry<T, NB>(W, wstride, base0, base1, woff, s_coef, e + j, A, B);
+                mono_entry<T, NB, wstride, dz1>(W + base0, woff, s_coef, e + j, A, B);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 A[b].flush();
                 B[b].flush();
             }
         }
-        for (; e < n_ent; ++e) mono_entry<T, NB>(W, wstride, base0, base1, woff, s_coef, e, A, B);
+        for (; e < n_ent; ++e) mono_entry<T, NB, wstride, dz1>(W + base0, woff, s_coef, e, A, B);
         const int ax = 2 * cx + px, ay = 2 * cy + py;
         const int cell0 = ax + 8 * ay + 64 * (2 * cz + pz);
         const int cell1 = cell0 + 64 * 4;
@@ -1000,11 +1015,11 @@ struct Kernels {
         static size_t done = 0;
         return allow_smem(mp_kernel<T>, bytes, done);
     }
-    template <int NB>
+    template <int NB, int RR>
     static cudaError_t mono(size_t bytes)
     {
         static size_t done = 0;
-        return allow_smem(mono_kernel<T, NB>, bytes, done);
+        return allow_smem(mono_kernel<T, NB, RR>, bytes, done);
     }
 };
 
@@ -1021,16 +1036,32 @@ int persistent_grid(Kern k, size_t smem, int64_t items, int sms, int cap_per_sm)
     return int(items < g ? items : g);
 }
 
+template <typename T, int NB, int RR>
+cudaError_t launch_mono_r(const KParams &K, size_t wbytes, int sms, int cap, cudaStream_t s)
+{
+    // the compile-time window geometry must be the host's
+    using G = WinGeo<RR>;
+    if (K.reach != G::R || K.py != G::PY || K.pz != G::PZ || K.sub_stride != G::SUB_STRIDE)
+        return cudaErrorInvalidValue;
+    const size_t bytes = mono_smem_bytes<T>(NB, wbytes, K.ent_stride);
+    cudaError_t e = Kernels<T>::template mono<NB, RR>(bytes);
+    if (e != cudaSuccess) return e;
+    const int64_t passes = (K.n_items + NB - 1) / NB;
+    const int g = persistent_grid(mono_kernel<T, NB, RR>, bytes, passes, sms, cap);
+    mono_kernel<T, NB, RR><<<g, kThreads, bytes, s>>>(K);
+    return cudaGetLastError();
+}
+
+// theta in (0.25, 1/sqrt(3)] gives reach 2 floor(1/theta) + 1 = 3, 5 or 7
 template <typename T, int NB>
 cudaError_t launch_mono(const KParams &K, size_t wbytes, int sms, int cap, cudaStream_t s)
 {
-    const size_t bytes = mono_smem_bytes<T>(NB, wbytes, K.ent_stride);
-    cudaError_t e = Kernels<T>::template mono<NB>(bytes);
-    if (e != cudaSuccess) return e;
-    const int64_t passes = (K.n_items + NB - 1) / NB;
-    const int g = persistent_grid(mono_kernel<T, NB>, bytes, passes, sms, cap);
-    mono_kernel<T, NB><<<g, kThreads, bytes, s>>>(K);
-    return cudaGetLastError();
+    switch (K.reach) {
+    case 3: return launch_mono_r<T, NB, 3>(K, wbytes, sms, cap, s);
+    case 5: return launch_mono_r<T, NB, 5>(K, wbytes, sms, cap, s);
+    case 7: return launch_mono_r<T, NB, 7>(K, wbytes, sms, cap, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>

@@ -362,7 +362,7 @@ def run_ours(args):
                              parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                              tuning=best)}
     result["e2e"] = e2e
-    result["gpu_launches"] = int(stats["launches_step"]) * args.steps
+    result["gpu_launches"] = int(stats["launches_fused"]) * args.steps
     result["clocks"] = clk
 
     if rank == 0:

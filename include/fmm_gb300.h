@@ -145,6 +145,8 @@ typedef struct {
     int32_t launches_m2l;            /* kernel launches per fmm_m2l call */
     int32_t launches_step;           /* kernel launches per upward+m2l+downward+forces */
     int32_t timing;                  /* 1 if the tree was built with FMM_FLAG_TIMING */
+    int32_t launches_fused;          /* kernel launches per fmm_step */
+    int32_t reserved;
     /* FMM_FLAG_TIMING only: device time (ms) and launch count per kernel slot
      * (FMM_K_*), summed over the launches since the previous fmm_get_stats
      * call, which waits for those launches and then resets the sums. */
@@ -266,6 +268,22 @@ typedef struct {
  * Errors: FMM_ERR_INVALID_ARG for NULL or out-of-range values. */
 int fmm_set_tuning(fmm_tree_t tree, const fmm_tuning *tuning);
 int fmm_get_tuning(fmm_tree_t tree, fmm_tuning *tuning);
+
+/*
+ * The whole step in one call: fmm_upward, fmm_m2l, fmm_downward and
+ * fmm_forces on the arguments they take (rho as for fmm_upward and
+ * fmm_forces), with the same kernels, arithmetic and results.  The passes'
+ * independent work is overlapped: the monopole<-monopole kernel (it needs
+ * only leaf masses) runs beside the upward pass of the refined levels, the
+ * refined levels' downward shifts beside the monopole<-multipole kernel, on a
+ * second stream that the tree owns and that forks from and joins back into
+ * `stream` through events, so the call can be captured into a CUDA graph.
+ * With FMM_FLAG_TIMING the four passes run in sequence on `stream` instead.
+ * Errors: as the four calls.
+ */
+int fmm_step(fmm_tree_t tree, const double *rho, double *M, double *com, void *L,
+             float *L_comp, double *dL1, double *L64, double *dL1_acc, double *phi,
+             double *g, double *totals, fmm_stream_t stream);
 
 /*
  * fmm_forces_noalloc -- the leaf-force pass for callers that cannot allocate

@@ -470,7 +470,15 @@ cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L, cons
                              const double *dL1, const double *com, double *L64, double *dacc,
                              cudaStream_t s)
 {
-    const ListRange &r = t->plan.nodes_at[size_t(level)];
+    return launch_l2l_nodes(t, t->plan.nodes_at[size_t(level)], L, Lc, dL1, com, L64, dacc, s);
+}
+
+// any list of nodes whose parents are done (one level, the refined nodes of
+// one level, or every leaf once every refined node is done)
+cudaError_t launch_l2l_nodes(const fmm_tree_s *t, const ListRange &r, const void *L,
+                             const float *Lc, const double *dL1, const double *com, double *L64,
+                             double *dacc, cudaStream_t s)
+{
     if (r.count == 0) return cudaSuccess;
     const auto &c = t->cfg;
     const unsigned grid = unsigned(r.count * 8);

@@ -427,11 +427,12 @@ static void plan_work(fmm_tree_s *t)
         std::stable_sort(v.begin(), v.end(),
                          [&](int32_t a, int32_t b) { return cost[size_t(a)] > cost[size_t(b)]; });
     };
-    std::vector<int32_t> leaves, mp, mono, mx, roots;
+    std::vector<int32_t> leaves, mp, mono, mx, roots, refined;
     for (int64_t i = 0; i < n; ++i) {
         const NodeInfo &x = t->info[size_t(i)];
         bool leaf = x.leaf_row >= 0;
         if (leaf) leaves.push_back(int32_t(i));
+        else refined.push_back(int32_t(i));
         if (x.level == 1) { roots.push_back(int32_t(i)); continue; }
         if (!leaf) mp.push_back(int32_t(i));
         else {
@@ -447,6 +448,7 @@ static void plan_work(fmm_tree_s *t)
     P.work_mono = push_range(mono);
     P.work_mx = push_range(mx);
     P.roots = push_range(roots);
+    P.refined = push_range(refined);
     P.refined_at.assign(size_t(t->max_level) + 2, {});
     P.nodes_at.assign(size_t(t->max_level) + 2, {});
     for (int lev = 1; lev <= t->max_level; ++lev) {
@@ -478,6 +480,15 @@ static void free_device(fmm_tree_s *t)
 {
     for (cudaEvent_t e : t->timer.ev) cudaEventDestroy(e);
     t->timer.ev.clear();
+    for (cudaEvent_t &e : t->step_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (t->aux) {
+        cudaStreamDestroy(t->aux);
+        t->aux = nullptr;
+    }
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf, d.mono_woff,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.levels_df, d.mass, d.mp, d.counters,
@@ -530,6 +541,12 @@ static int upload_tree(fmm_tree_s *t)
             return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
         d.workspace_bytes += down_b;
     }
+    // fmm_step's second stream and events (no timing: they only order work)
+    if ((e = cudaStreamCreateWithFlags(&t->aux, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreateWithFlags");
+    for (cudaEvent_t &ev : t->step_ev)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
     if (t->cfg.flags & FMM_FLAG_TIMING) {
         const int records = 256;
         t->timer.ev.resize(size_t(2 * records));
@@ -711,6 +728,12 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     for (int lev = 1; lev <= t->max_level; ++lev) down += P.nodes_at[size_t(lev)].count > 0;
     o->launches_m2l = m2l;
     o->launches_step = up + m2l + down + 3;
+    // fmm_step: pack in two launches (leaves, refined), the refined levels'
+    // shifts per level and every leaf's in one launch
+    int refined_levels = 0;
+    for (int lev = 1; lev <= t->max_level; ++lev) refined_levels += P.refined_at[size_t(lev)].count > 0;
+    o->launches_fused = up + (m2l - 1) + (P.leaves.count > 0) + (P.refined.count > 0) +
+                        refined_levels + (P.leaves.count > 0) + 3;
     if ((t->cfg.flags & FMM_FLAG_TIMING) && !t->host_only) {
         o->timing = 1;
         timing_fold(t);
@@ -799,6 +822,74 @@ int fmm_forces(fmm_tree_t t, const double *L64, const double *dL1_acc, const dou
     cudaError_t e = launch_forces(t, L64, dL1_acc, rho, phi, g, totals,
                                   static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "forces launch");
+    return FMM_OK;
+}
+
+// The whole step as one call, with the passes' independent work overlapped on
+// two streams: the monopole<-monopole kernel needs only leaf masses, so it
+// runs beside the upward pass of the refined levels; the refined levels'
+// shifts need only the multipole-target results, so they run beside the
+// monopole<-multipole kernel; the leaf shifts (all levels in one launch) and
+// the forces follow both.  Same kernels, same arithmetic, same results as
+// fmm_upward, fmm_m2l, fmm_downward and fmm_forces in sequence.
+int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, float *L_comp,
+             double *dL1, double *L64, double *dL1_acc, double *phi, double *g, double *totals,
+             fmm_stream_t stream)
+{
+    int rc = check_device_tree(t);
+    if (rc) return rc;
+    if (!rho || !M || !com || !L || !dL1 || !L64 || !dL1_acc || !phi || !g || !totals)
+        return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
+    if (t->cfg.precision != FMM_FP64 && !L_comp)
+        return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED and FMM_DFLOAT");
+    if (t->cfg.flags & FMM_FLAG_TIMING) {
+        // per-kernel events on one stream: the passes in sequence
+        if ((rc = fmm_upward(t, rho, M, com, stream)) || (rc = fmm_m2l(t, M, com, L, L_comp, dL1, stream)) ||
+            (rc = fmm_downward(t, L, L_comp, dL1, com, L64, dL1_acc, stream)))
+            return rc;
+        return fmm_forces(t, L64, dL1_acc, rho, phi, g, totals, stream);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream), a = t->aux;
+    cudaEvent_t *ev = t->step_ev;
+    const Plan &P = t->plan;
+    cudaError_t e;
+    int nl = 0;
+#define FMM_STEP_TRY(call, what) \
+    if ((e = (call)) != cudaSuccess) return cuda_fail(e, what)
+    // main: reset the work queues, P2M, fork
+    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_RESET), "queue reset");
+    FMM_STEP_TRY(launch_p2m(t, rho, M, s), "p2m launch");
+    FMM_STEP_TRY(cudaEventRecord(ev[0], s), "cudaEventRecord");
+    // aux: leaf masses, monopole<-monopole
+    FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[0], 0), "cudaStreamWaitEvent");
+    FMM_STEP_TRY(launch_pack(t, M, com, a, PACK_LEAVES), "pack launch");
+    FMM_STEP_TRY(cudaEventRecord(ev[4], a), "cudaEventRecord");
+    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_MONO), "m2l launch");
+    // main: M2M, refined sources, root and multipole targets
+    for (int lev = t->max_level - 1; lev >= 1; --lev)
+        if (P.refined_at[size_t(lev)].count)
+            FMM_STEP_TRY(launch_m2m_level(t, lev, M, com, s), "m2m launch");
+    FMM_STEP_TRY(launch_pack(t, M, com, s, PACK_REFINED), "pack launch");
+    FMM_STEP_TRY(cudaEventRecord(ev[1], s), "cudaEventRecord");
+    // the multipole targets' leaf sources read the leaf masses packed on aux
+    FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[4], 0), "cudaStreamWaitEvent");
+    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_ROOT | M2L_MP), "m2l launch");
+    // aux: monopole<-multipole once the refined sources are packed (it adds
+    // to what the monopole kernel stored, on the same stream)
+    FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[1], 0), "cudaStreamWaitEvent");
+    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_MX), "m2l launch");
+    // main: shifts of the refined nodes, root level first
+    for (int lev = 1; lev <= t->max_level; ++lev)
+        FMM_STEP_TRY(launch_l2l_nodes(t, P.refined_at[size_t(lev)], L, L_comp, dL1, com, L64,
+                                      dL1_acc, s), "l2l launch");
+    FMM_STEP_TRY(cudaEventRecord(ev[2], s), "cudaEventRecord");
+    // aux: every leaf's shift, forces and sums; join
+    FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[2], 0), "cudaStreamWaitEvent");
+    FMM_STEP_TRY(launch_l2l_nodes(t, P.leaves, L, L_comp, dL1, com, L64, dL1_acc, a), "l2l launch");
+    FMM_STEP_TRY(launch_forces(t, L64, dL1_acc, rho, phi, g, totals, a), "forces launch");
+    FMM_STEP_TRY(cudaEventRecord(ev[3], a), "cudaEventRecord");
+    FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[3], 0), "cudaStreamWaitEvent");
+#undef FMM_STEP_TRY
     return FMM_OK;
 }
 

@@ -120,6 +120,7 @@ struct Plan {
     std::vector<ListRange> refined_at;   // [level] refined nodes (M2M)
     std::vector<ListRange> nodes_at;     // [level] all nodes (L2L)
     ListRange work_mp, work_mono, work_mx, roots;
+    ListRange refined;                    // every refined node (roots included)
     int64_t interactions[4] = {0, 0, 0, 0};
     int64_t kernel_interactions[4] = {0, 0, 0, 0};  // multipole, monopole, mono<-multi, root
 };
@@ -159,6 +160,9 @@ struct fmm_tree_s {
     int device = -1;
     fmm::DeviceTables dev;
     mutable fmm::TimerState timer;
+    // fmm_step's second stream and its fork/join events (device trees only)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t step_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace fmm {
@@ -167,11 +171,18 @@ namespace fmm {
 cudaError_t launch_p2m(const fmm_tree_s *t, const double *rho, double *M, cudaStream_t s);
 cudaError_t launch_m2m_level(const fmm_tree_s *t, int level, double *M, double *com,
                              cudaStream_t s);
+// which nodes a pack launch covers
+enum { PACK_ALL = 0, PACK_LEAVES = 1, PACK_REFINED = 2 };
 cudaError_t launch_pack(const fmm_tree_s *t, const double *M, const double *com,
-                        cudaStream_t s);
+                        cudaStream_t s, int which = PACK_ALL);
+// parts of the same-level pass (bits; M2L_ALL = all, counters reset first)
+enum { M2L_RESET = 1, M2L_ROOT = 2, M2L_MP = 4, M2L_MONO = 8, M2L_MX = 16, M2L_ALL = 31 };
 cudaError_t launch_m2l(const fmm_tree_s *t, void *L, float *Lc, double *dL1,
-                       cudaStream_t s, int *n_launches);
+                       cudaStream_t s, int *n_launches, int parts = M2L_ALL);
 cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L,
+                             const float *Lc, const double *dL1, const double *com,
+                             double *L64, double *dacc, cudaStream_t s);
+cudaError_t launch_l2l_nodes(const fmm_tree_s *t, const ListRange &r, const void *L,
                              const float *Lc, const double *dL1, const double *com,
                              double *L64, double *dacc, cudaStream_t s);
 cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *dacc,

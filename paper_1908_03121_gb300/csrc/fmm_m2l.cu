@@ -142,13 +142,14 @@ __device__ __forceinline__ void pack_float(const NodeInfo &ni, const double *__r
 // the traceless projections of A2 = mult M2 / (2 h^2), A3 = mult M3 / (6 h^3).
 template <typename T>
 __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ info,
+                                                   const int32_t *__restrict__ nodes,
                                                    const double *__restrict__ levels,
                                                    const double *__restrict__ M,
                                                    const double *__restrict__ com,
                                                    T *__restrict__ mass, T *__restrict__ mp,
                                                    double lo_x, double lo_y, double lo_z)
 {
-    const int node = blockIdx.x;
+    const int node = nodes ? nodes[blockIdx.x] : int(blockIdx.x);   // a list, or every node
     const NodeInfo ni = info[node];
     const int c = threadIdx.x;
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
@@ -1066,7 +1067,7 @@ cudaError_t launch_mono(const KParams &K, size_t wbytes, int sms, int cap, cudaS
 
 template <typename T>
 cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cudaStream_t s,
-                       int *n_launches)
+                       int *n_launches, int parts)
 {
     const Plan &Pl = t->plan;
     const DeviceTables &d = t->dev;
@@ -1100,11 +1101,13 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     const size_t mp_bytes = wbytes;
     cudaError_t e = Kernels<T>::mp(mp_bytes);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(d.counters, 0, 4 * sizeof(int32_t), s);
-    if (e != cudaSuccess) return e;
+    if (parts & M2L_RESET) {
+        e = cudaMemsetAsync(d.counters, 0, 4 * sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+    }
     const int sms = sm_count_of_current_device();
     int nl = 0;
-    if (Pl.roots.count) {
+    if ((parts & M2L_ROOT) && Pl.roots.count) {
         KParams R = P;
         R.list = d.lists + Pl.roots.off;
         R.n_items = int32_t(Pl.roots.count);
@@ -1114,7 +1117,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (Pl.work_mp.count) {
+    if ((parts & M2L_MP) && Pl.work_mp.count) {
         KParams K = P;
         K.list = d.lists + Pl.work_mp.off;
         K.n_items = int32_t(Pl.work_mp.count);
@@ -1126,7 +1129,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (Pl.work_mono.count) {
+    if ((parts & M2L_MONO) && Pl.work_mono.count) {
         KParams K = P;
         K.list = d.lists + Pl.work_mono.off;
         K.n_items = int32_t(Pl.work_mono.count);
@@ -1145,7 +1148,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         ++nl;
         if (e != cudaSuccess) return e;
     }
-    if (Pl.work_mx.count) {
+    if ((parts & M2L_MX) && Pl.work_mx.count) {
         KParams K = P;
         K.list = d.lists + Pl.work_mx.off;
         K.n_items = int32_t(2 * Pl.work_mx.count);       // node halves
@@ -1162,34 +1165,46 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
 }
 
 template <typename T>
-void launch_pack_t(const fmm_tree_s *t, const double *M, const double *com, cudaStream_t s)
+void launch_pack_t(const fmm_tree_s *t, const double *M, const double *com, cudaStream_t s,
+                   const int32_t *nodes, int64_t count)
 {
     const auto &c = t->cfg;
-    pack_kernel<T><<<unsigned(t->n), 512, 0, s>>>(t->dev.info, t->dev.levels, M, com,
-                                                  static_cast<T *>(t->dev.mass),
-                                                  static_cast<T *>(t->dev.mp), c.box_lo[0],
-                                                  c.box_lo[1], c.box_lo[2]);
+    pack_kernel<T><<<unsigned(count), 512, 0, s>>>(t->dev.info, nodes, t->dev.levels, M, com,
+                                                   static_cast<T *>(t->dev.mass),
+                                                   static_cast<T *>(t->dev.mp), c.box_lo[0],
+                                                   c.box_lo[1], c.box_lo[2]);
 }
 
 }  // namespace
 
-cudaError_t launch_pack(const fmm_tree_s *t, const double *M, const double *com, cudaStream_t s)
+cudaError_t launch_pack(const fmm_tree_s *t, const double *M, const double *com, cudaStream_t s,
+                        int which)
 {
+    const int32_t *nodes = nullptr;
+    int64_t count = t->n;
+    if (which == PACK_LEAVES) {
+        nodes = t->dev.lists + t->plan.leaves.off;
+        count = t->plan.leaves.count;
+    } else if (which == PACK_REFINED) {
+        nodes = t->dev.lists + t->plan.refined.off;
+        count = t->plan.refined.count;
+    }
+    if (count == 0) return cudaSuccess;
     switch (t->cfg.precision) {
-    case FMM_MIXED: launch_pack_t<float>(t, M, com, s); break;
-    case FMM_DFLOAT: launch_pack_t<dfloat>(t, M, com, s); break;
-    default: launch_pack_t<double>(t, M, com, s); break;
+    case FMM_MIXED: launch_pack_t<float>(t, M, com, s, nodes, count); break;
+    case FMM_DFLOAT: launch_pack_t<dfloat>(t, M, com, s, nodes, count); break;
+    default: launch_pack_t<double>(t, M, com, s, nodes, count); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2l(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cudaStream_t s,
-                       int *n_launches)
+                       int *n_launches, int parts)
 {
     switch (t->cfg.precision) {
-    case FMM_MIXED: return launch_all<float>(t, L, Lc, dL1, s, n_launches);
-    case FMM_DFLOAT: return launch_all<dfloat>(t, L, Lc, dL1, s, n_launches);
-    default: return launch_all<double>(t, L, Lc, dL1, s, n_launches);
+    case FMM_MIXED: return launch_all<float>(t, L, Lc, dL1, s, n_launches, parts);
+    case FMM_DFLOAT: return launch_all<dfloat>(t, L, Lc, dL1, s, n_launches, parts);
+    default: return launch_all<double>(t, L, Lc, dL1, s, n_launches, parts);
     }
 }
 

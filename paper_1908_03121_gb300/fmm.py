@@ -30,7 +30,7 @@ KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_mul
                 "forces", "reduce")
 
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
-            "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_set_tuning", "fmm_get_tuning",
+            "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_step", "fmm_set_tuning", "fmm_get_tuning",
             "fmm_forces_noalloc", "fmm_check_conversions", "fmm_destroy_tree", "fmm_last_error")
 
 NCELL = 512
@@ -66,7 +66,8 @@ class FmmStats(ctypes.Structure):
                 ("work_items", ctypes.c_int64 * 4), ("kernel_interactions", ctypes.c_int64 * 4),
                 ("reach", ctypes.c_int32),
                 ("launches_m2l", ctypes.c_int32), ("launches_step", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("kernel_ms", ctypes.c_double * 16),
+                ("timing", ctypes.c_int32), ("launches_fused", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("kernel_ms", ctypes.c_double * 16),
                 ("kernel_launches", ctypes.c_int64 * 16)]
 
 
@@ -100,6 +101,7 @@ def load(build=True):
         lib.fmm_m2l.argtypes = [P, P, P, P, P, P, P]
         lib.fmm_downward.argtypes = [P, P, P, P, P, P, P, P]
         lib.fmm_forces.argtypes = [P, P, P, P, P, P, P, P]
+        lib.fmm_step.argtypes = [P] * 13
         lib.fmm_destroy_tree.argtypes = [P]
         lib.fmm_destroy_tree.restype = None
         lib.fmm_forces_noalloc.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
@@ -218,6 +220,15 @@ def fmm_forces(tree, L64, dL1_acc, rho, phi, g, totals, stream=None):
                              _ptr(g), _ptr(totals), _stream(stream)))
 
 
+def fmm_step(tree, rho, M, com, L, L_comp, dL1, L64, dL1_acc, phi, g, totals, stream=None):
+    """The whole step in one call (upward, same-level, downward, forces), with
+    the passes' independent work overlapped on two streams; same results as
+    the four calls in sequence."""
+    _check(load().fmm_step(tree.handle, _ptr(rho), _ptr(M), _ptr(com), _ptr(L), _ptr(L_comp),
+                           _ptr(dL1), _ptr(L64), _ptr(dL1_acc), _ptr(phi), _ptr(g), _ptr(totals),
+                           _stream(stream)))
+
+
 def fmm_destroy_tree(tree):
     load().fmm_destroy_tree(tree.handle)
 
@@ -305,6 +316,12 @@ class Solver:
                    self.g, self.totals, stream)
 
     def step(self, rho=None, stream=None):
+        """One solve step through fmm_step (the passes overlapped on two streams)."""
+        fmm_step(self.tree, self.rho if rho is None else rho, self.M, self.com, self.L, self.Lc,
+                 self.dL1, self.L64, self.dacc, self.phi, self.g, self.totals, stream)
+
+    def step_passes(self, rho=None, stream=None):
+        """The same step as the four pass calls in sequence on one stream."""
         self.upward(rho, stream)
         self.m2l(stream)
         self.downward(stream)

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(B.FmmConfig) == 8 * 6 + 4 * 4
     assert ctypes.sizeof(B.FmmSizes) == 8 * 4 + 4 * 2 + 8 * 11
-    assert ctypes.sizeof(B.FmmStats) == 8 * 4 + 8 * 3 + 8 * 4 + 8 * 4 + 8 * 4 + 4 * 4 + 8 * 16 + 8 * 16
+    assert ctypes.sizeof(B.FmmStats) == 8 * 4 + 8 * 3 + 8 * 4 + 8 * 4 + 8 * 4 + 4 * 6 + 8 * 16 + 8 * 16
 
 
 def plan(desc, theta):

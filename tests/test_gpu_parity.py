@@ -298,6 +298,40 @@ def test_deterministic_and_graph_replay(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "dfloat"])
+@pytest.mark.parametrize("name", ["adaptive4", "batch3", "cfg2"])
+def test_fused_step_matches_passes(name, precision):
+    """fmm_step (passes overlapped on two streams) gives the same bits as the
+    four pass calls in sequence."""
+    c, _ = oracle_solution(name)
+    s = F.Solver(c["desc"], c["theta"], precision=precision, G=c["G"], box_lo=c["box_lo"],
+                 box_size=c["box_size"])
+    s.rho.copy_(dev(c["rho"]))
+    s.step_passes()
+    torch.cuda.synchronize()
+    ref = [host(t).copy() for t in (s.M, s.com, s.dL1, s.L64, s.dacc, s.phi, s.g, s.totals)]
+    for t in (s.M, s.com, s.L, s.dL1, s.L64, s.dacc, s.phi, s.g, s.totals):
+        t.fill_(float("nan"))
+    if s.Lc is not None:
+        s.Lc.fill_(float("nan"))
+    s.step()
+    torch.cuda.synchronize()
+    got = [host(t) for t in (s.M, s.com, s.dL1, s.L64, s.dacc, s.phi, s.g, s.totals)]
+    refined = c["desc"][:, 5] >= 0
+    # slots the library writes: M (refined nodes, and M0 of leaves), com
+    # (refined nodes), L64 (orders 0-1 of leaves)
+    m_mask = np.broadcast_to(refined[:, None, None] | (np.arange(20) == 0)[None, :, None],
+                             got[0].shape)
+    com_mask = np.broadcast_to(refined[:, None, None], got[1].shape)
+    l_mask = np.broadcast_to(defined_L_mask(c["desc"]), got[3].shape)
+    masks = [m_mask, com_mask, None, l_mask, None, None, None, None]
+    for a, b, m in zip(got, ref, masks):
+        if m is not None:
+            a, b = a[m], b[m]
+        assert np.array_equal(a, b)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "dfloat"])
 def test_tunings_agree_bitwise(precision):
     """Launch shapes change scheduling only: every tuning gives the same bits."""
     c, _ = oracle_solution("adaptive4")

@@ -298,24 +298,6 @@ static void build_stencils(fmm_tree_s *t)
     // (the same expression as well_separated on o2 = far_o2)
     P.far_o2 = 1;
     while (!(theta * theta * double(P.far_o2) > 1.0)) ++P.far_o2;
-    // slots reachable by each entry from each half (z-cells 0-3 / 4-7) of a node
-    t->slot_mask.assign(size_t(16) * P.ent_stride, 0);
-    for (int p = 0; p < 8; ++p) {
-        const int pp[3] = {p & 1, (p >> 1) & 1, (p >> 2) & 1};
-        for (int h = 0; h < 2; ++h)
-            for (size_t k = 0; k < lists[p].size(); ++k) {
-                const StencilEntry &e = lists[p][k];
-                int32_t m = 0;
-                for (int cz = 2 * h; cz < 2 * h + 2; ++cz)
-                    for (int cy = 0; cy < 4; ++cy)
-                        for (int cx = 0; cx < 4; ++cx) {
-                            const int bx = 2 * cx + pp[0] + e.ox + 8, by = 2 * cy + pp[1] + e.oy + 8,
-                                      bz = 2 * cz + pp[2] + e.oz + 8;
-                            m |= 1 << ((bx >> 3) + 3 * (by >> 3) + 9 * (bz >> 3));
-                        }
-                t->slot_mask[(size_t(p) * 2 + h) * P.ent_stride + k] = m;
-            }
-    }
 }
 
 // --------------------------------------------------- interaction counting
@@ -358,6 +340,55 @@ static void slot_tables(const fmm_tree_s *t, std::vector<int64_t> &tab)
 //   monopole<-multipole:  orders 0-1 (62) + correction sum (42)            -> 199
 // (Sec. 4.3 quotes 455 and 12 for the paper's own kernels.)
 static const double kFlops[4] = {240.0, 176.0, 8.0, 199.0};
+
+// Monopole<-multipole work as pair lists: for every cell of a leaf node next
+// to a refined node, the stencil entries whose source cell is refined, each
+// with the source's packed-moment offset.  Targets are sorted by pair count
+// (longest first) so that the 32 targets of a warp have nearly equal counts.
+static void build_mx_pairs(fmm_tree_s *t, const std::vector<int32_t> &mx_nodes)
+{
+    const Plan &P = t->plan;
+    struct Target { int32_t node, cell, off, count; };
+    std::vector<Target> targets;
+    std::vector<int32_t> pairs;              // (source offset, entry) interleaved
+    for (int32_t node : mx_nodes) {
+        const int32_t *nb = &t->nbr[size_t(node) * 27];
+        for (int cell = 0; cell < NCELL; ++cell) {
+            const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+            const int p = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+            const int n_ent = P.n_far[p] + P.n_near[p];
+            const int32_t off = int32_t(pairs.size() / 2);
+            for (int k = 0; k < n_ent; ++k) {
+                const StencilEntry &e = t->stencil[size_t(p) * P.ent_stride + k];
+                const int bx = x + e.ox + 8, by = y + e.oy + 8, bz = z + e.oz + 8;
+                const int slot = (bx >> 3) + 3 * (by >> 3) + 9 * (bz >> 3);
+                const int32_t src = nb[slot];
+                if (src < 0 || t->info[size_t(src)].leaf_row >= 0) continue;
+                // the kernels' parity-split cell order (parity_index)
+                const int lx = bx & 7, ly = by & 7, lz = bz & 7;
+                const int pi = ((lx & 1) + 2 * (ly & 1) + 4 * (lz & 1)) * 64 + (lx >> 1) +
+                               4 * (ly >> 1) + 16 * (lz >> 1);
+                pairs.push_back((t->info[size_t(src)].mp_row * 4 * NCELL + pi) * 4);
+                pairs.push_back(k);
+            }
+            const int32_t count = int32_t(pairs.size() / 2) - off;
+            if (count) targets.push_back(Target{node, cell, off, count});
+        }
+    }
+    std::stable_sort(targets.begin(), targets.end(),
+                     [](const Target &a, const Target &b) { return a.count > b.count; });
+    t->mx_targets.resize(targets.size() * 4);
+    for (size_t i = 0; i < targets.size(); ++i) {
+        t->mx_targets[4 * i + 0] = targets[i].node;
+        t->mx_targets[4 * i + 1] = targets[i].cell;
+        t->mx_targets[4 * i + 2] = targets[i].off;
+        t->mx_targets[4 * i + 3] = targets[i].count;
+    }
+    // the same count as the planner's slot tables (two independent walks)
+    if (int64_t(pairs.size() / 2) != P.kernel_interactions[2]) std::abort();
+    t->mx_pairs = std::move(pairs);
+    t->plan.n_mx_targets = int64_t(targets.size());
+}
 
 static void plan_work(fmm_tree_s *t)
 {
@@ -448,6 +479,7 @@ static void plan_work(fmm_tree_s *t)
     P.work_mono = push_range(mono);
     P.work_mx = push_range(mx);
     P.roots = push_range(roots);
+    build_mx_pairs(t, mx);
     P.refined = push_range(refined);
     P.refined_at.assign(size_t(t->max_level) + 2, {});
     P.nodes_at.assign(size_t(t->max_level) + 2, {});
@@ -492,7 +524,7 @@ static void free_device(fmm_tree_s *t)
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf, d.mono_woff,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.levels_df, d.mass, d.mp, d.counters,
-                    d.partials, d.chunk_sums, d.up, d.down, d.slot_mask};
+                    d.partials, d.chunk_sums, d.up, d.down, d.mx_targets, d.mx_pairs};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceTables{};
@@ -510,7 +542,8 @@ static int upload_tree(fmm_tree_s *t)
         (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||
         (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)) || (rc = upload(&d.levels, t->levels)) ||
         (rc = upload(&d.levels_df, t->levels_df)) ||
-        (rc = upload(&d.slot_mask, t->slot_mask)))
+        (rc = upload(reinterpret_cast<int32_t **>(&d.mx_targets), t->mx_targets)) ||
+        (rc = upload(reinterpret_cast<int32_t **>(&d.mx_pairs), t->mx_pairs)))
         return rc;
     // packed masses and moments: float (mixed), (hi, lo) float pairs (dfloat), double
     size_t es = t->cfg.precision == FMM_MIXED ? sizeof(float) : 2 * sizeof(float);
@@ -721,7 +754,7 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     for (int k = 0; k < 4; ++k) o->kernel_interactions[k] = P.kernel_interactions[k];
     o->reach = P.reach;
     int m2l = 1 /*pack*/ + (P.roots.count > 0) + (P.work_mp.count > 0) + (P.work_mono.count > 0) +
-              (P.work_mx.count > 0);
+              (P.n_mx_targets > 0);
     int up = 1;
     for (int lev = 1; lev < t->max_level; ++lev) up += P.refined_at[size_t(lev)].count > 0;
     int down = 0;

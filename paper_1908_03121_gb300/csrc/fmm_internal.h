@@ -81,8 +81,8 @@ struct DeviceTables {
     int32_t *tree_leaf_rows = nullptr;  // [n_leaf]
     double *levels = nullptr;        // [max_level + 1][LEVEL_FIELDS]
     float *levels_df = nullptr;      // [max_level + 1][LEVEL_DF_FIELDS][2]
-    int32_t *slot_mask = nullptr;    // [8][2][ent_stride]: neighbour slots (bit per
-                                     // slot) an entry reaches from a node half
+    int4 *mx_targets = nullptr;      // monopole<-multipole targets (node, cell, offset, count)
+    int2 *mx_pairs = nullptr;        // their pairs (packed-moment offset, stencil entry)
     // workspace
     void *mass = nullptr;            // [n][512] float or double
     void *mp = nullptr;              // [n_refined][4][512][4] packed sources: float,
@@ -121,6 +121,7 @@ struct Plan {
     std::vector<ListRange> nodes_at;     // [level] all nodes (L2L)
     ListRange work_mp, work_mono, work_mx, roots;
     ListRange refined;                    // every refined node (roots included)
+    int64_t n_mx_targets = 0;             // leaf cells with refined sources
     int64_t interactions[4] = {0, 0, 0, 0};
     int64_t kernel_interactions[4] = {0, 0, 0, 0};  // multipole, monopole, mono<-multi, root
 };
@@ -153,7 +154,8 @@ struct fmm_tree_s {
     std::vector<int32_t> tree_leaf_off, tree_leaf_rows;
     std::vector<double> levels;
     std::vector<float> levels_df;
-    std::vector<int32_t> slot_mask;
+    std::vector<int32_t> mx_targets;     // [n_mx_targets][4]: node, cell, pair offset, count
+    std::vector<int32_t> mx_pairs;       // [pairs][2]: packed-moment offset, stencil entry
     fmm::Plan plan;
     fmm_tuning tuning{};
     bool host_only = false;

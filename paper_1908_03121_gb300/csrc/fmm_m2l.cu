@@ -78,7 +78,8 @@ struct KParams {
     const int32_t *mono_woff;  // [8][ent_stride] window offsets in parity 0's order, reflected
     int n_far, n_near;       // identical for every parity
     int ent_stride;          // entries reserved per parity
-    const int32_t *slot_mask;  // [8][2][ent_stride] neighbour slots an entry can reach
+    const int4 *mx_targets;  // monopole<-multipole targets (node, cell, pair offset, count)
+    const int2 *mx_pairs;    // (packed-moment offset, stencil entry)
     int reach, py, pz, sub_stride;
     const void *mass;
     const void *mp;
@@ -822,56 +823,38 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
 }
 
 // ------------------------------------------------------------ mx_kernel
-// Leaf target, refined sources (monopole<-multipole): orders 0-1 and the
+// Leaf targets, refined sources (monopole<-multipole): orders 0-1 and the
 // correction (the target has no third moment).  Adds to what mono_kernel
-// stored for the same node, so it runs after it on the same stream.  Work
-// items are node halves (z < 4, z >= 4); a host table gives, per parity,
-// half and stencil entry, the neighbour slots its sources can fall in, so a
-// warp skips (uniformly) every entry that cannot reach a refined neighbour.
+// stored for the same cells, so it runs after it on the same stream.  Few
+// targets of a node see refined sources, and those see few (16 on average
+// on the workloads), so instead of walking every stencil entry with most
+// lanes masked off, each lane takes one target cell and walks that cell's
+// own list of (packed-moment offset, stencil entry) pairs, built on the
+// host; targets are sorted by list length, so a warp's lanes finish together.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
 {
-    __shared__ int s_nbr[27], s_leaf[27], s_row[27], s_item, s_mask;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = warp;
-    const int px = p & 1, py = (p >> 1) & 1, pz = p >> 2;
-    const int cx = lane & 3, cy = (lane >> 2) & 3, cz0 = lane >> 4;
-    const StencilEntry *ent = P.stencil + p * P.ent_stride;
-    const int n_ent = P.n_far + P.n_near;
-    for (;;) {
-        const int item = pull_item(P.counter, &s_item);
-        if (item >= P.n_items) break;
-        const int node = P.list[item >> 1];
-        const int half = item & 1;
-        load_slots(node, P, s_nbr, s_leaf, s_row);
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const unsigned bits = __ballot_sync(0xffffffffu, threadIdx.x < 27 && s_row[threadIdx.x] >= 0);
-            if (threadIdx.x == 0) s_mask = int(bits);
-        }
-        __syncthreads();
-        const int rmask = s_mask;
-        const int32_t *smask = P.slot_mask + (size_t(p) * 2 + half) * P.ent_stride;
-        const int cz = cz0 + 2 * half;
-        const int ax = 2 * cx + px, ay = 2 * cy + py, az = 2 * cz + pz;
+    const int lane = threadIdx.x & 31;
+    const int warps = int(gridDim.x) * (kThreads / 32);
+    const T *mp = static_cast<const T *>(P.mp);
+    for (int w = int(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); w * 32 < P.n_items;
+         w += warps) {
+        const int t = w * 32 + lane;
+        if (t >= P.n_items) continue;
+        const int4 tg = __ldg(P.mx_targets + t);       // node, cell, pair offset, count
+        const int x = tg.y & 7, y = (tg.y >> 3) & 7, z = tg.y >> 6;
+        const int p = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+        const StencilEntry *ent = P.stencil + p * P.ent_stride;
         Acc<T, 4> L;
         Acc<T, 3> S;
         L.zero();
         S.zero();
         int done = 0;
-        for (int e = 0; e < n_ent; ++e) {
-            if (!(__ldg(&smask[e]) & rmask)) continue;
-            const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + e));
-            int slot, pi;
-            source_cell(ax, ay, az, E.x, E.y, E.z, slot, pi);
-            const int row = s_row[slot];
+        for (int k = 0; k < tg.w; ++k) {
+            const int2 pr = __ldg(P.mx_pairs + tg.z + k);
+            const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + pr.y));
             Src<T> src;
-            if (row >= 0) {
-                load_source<T>(P, row, pi, src);
-            } else {
-                src.m0 = T(0);
-                zero_moments<T>(src);
-            }
+            load_source_at<T>(mp + pr.x, src);
             acc_mx<T>(-T(E.x) - src.d[0], -T(E.y) - src.d[1], -T(E.z) - src.d[2], src, L, S);
             if (++done == kChunk) {
                 L.flush();
@@ -881,7 +864,7 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
         }
         L.flush();
         S.flush();
-        const int cell = ax + 8 * ay + 64 * az;
+        const int node = tg.x, cell = tg.y;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const size_t idx = (size_t(node) * NCOMP + k) * NCELL + cell;
@@ -904,7 +887,6 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
         }
 #pragma unroll
         for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(S, i);
-        __syncthreads();
     }
 }
 
@@ -1092,7 +1074,8 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     P.Lc = Lc;
     P.dL1 = dL1;
     P.far_o2 = t->plan.far_o2;
-    P.slot_mask = d.slot_mask;
+    P.mx_targets = d.mx_targets;
+    P.mx_pairs = d.mx_pairs;
     P.mono_woff = d.mono_woff;
     const int cap = t->tuning.ctas_per_sm;
     const size_t wbytes = size_t(8) * Pl.sub_stride * sizeof(T);
@@ -1148,12 +1131,12 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         ++nl;
         if (e != cudaSuccess) return e;
     }
-    if ((parts & M2L_MX) && Pl.work_mx.count) {
+    if ((parts & M2L_MX) && Pl.n_mx_targets) {
         KParams K = P;
-        K.list = d.lists + Pl.work_mx.off;
-        K.n_items = int32_t(2 * Pl.work_mx.count);       // node halves
-        K.counter = d.counters + Q_MX;
-        int g = persistent_grid(mx_kernel<T>, 0, K.n_items, sms, cap);
+        K.n_items = int32_t(Pl.n_mx_targets);
+        const int64_t warps = (K.n_items + 31) / 32;
+        int g = persistent_grid(mx_kernel<T>, 0, (warps + kThreads / 32 - 1) / (kThreads / 32), sms,
+                                cap);
         timing_begin(t, FMM_K_MONO_MULTI, s);
         mx_kernel<T><<<g, kThreads, 0, s>>>(K);
         timing_end(t, s);

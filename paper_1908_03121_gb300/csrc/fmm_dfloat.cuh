@@ -104,6 +104,29 @@ __device__ __forceinline__ dfloat fmadd(dfloat a, dfloat b, dfloat c)
     return df_fast(s, t);
 }
 
+// The same without the closing Fast2Sum: the low part may grow past half an
+// ulp of the high part.  Chains of these (a running sum, a dot product) stay
+// exact to the double-float level as long as the low part stays small next
+// to the high part; renorm() restores the canonical form, and the kernels
+// call it at the end of every chain and every 16 stencil entries.
+__device__ __forceinline__ dfloat fmadd_u(dfloat a, dfloat b, dfloat c)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    float s, t;
+    df_two_sum(p, c.hi, s, t);
+    return dfloat(s, t + (e + c.lo));
+}
+__device__ __forceinline__ dfloat add_u(dfloat a, dfloat b)
+{
+    float s, e;
+    df_two_sum(a.hi, b.hi, s, e);
+    return dfloat(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ dfloat renorm(dfloat a) { return df_fast(a.hi, a.lo); }
+
 __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
 __device__ __forceinline__ dfloat &operator-=(dfloat &a, dfloat b) { return a = a - b; }
 __device__ __forceinline__ dfloat &operator*=(dfloat &a, dfloat b) { return a = a * b; }

@@ -351,7 +351,13 @@ struct Acc<dfloat, N> {
 #pragma unroll
         for (int k = 0; k < N; ++k) part[k] = dfloat(0.f);
     }
-    __device__ __forceinline__ void flush() {}
+    // the running sums take unnormalised terms (fmadd_u, add_u): restore
+    // the canonical (hi, lo) form every chunk
+    __device__ __forceinline__ void flush()
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) part[k] = renorm(part[k]);
+    }
 };
 
 // the (hi, lo) value of accumulator k
@@ -501,24 +507,24 @@ __device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const 
     T a = nm0 * D.D0;
     if (SRC_MP) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) a = fmadd(-s.B2[k], D.D2[k], a);
+        for (int k = 0; k < 5; ++k) a = fmadd_u(-s.B2[k], D.D2[k], a);
 #pragma unroll
-        for (int q = 0; q < 7; ++q) a = fmadd(s.B3[q], D.D3[q], a);
+        for (int q = 0; q < 7; ++q) a = fmadd_u(s.B3[q], D.D3[q], a);
     }
-    L.part[0] += a;
+    L.part[0] = add_u(L.part[0], renorm(a));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         T b = nm0 * D.D1[i];
         if (SRC_MP) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) b = fmadd(-s.B2[k], D.d3slice(i, k), b);
+            for (int k = 0; k < 5; ++k) b = fmadd_u(-s.B2[k], D.d3slice(i, k), b);
         }
-        L.part[1 + i] += b;
+        L.part[1 + i] = add_u(L.part[1 + i], renorm(b));
     }
 #pragma unroll
-    for (int k = 0; k < 5; ++k) L.part[4 + k] = fmadd(nm0, D.D2[k], L.part[4 + k]);
+    for (int k = 0; k < 5; ++k) L.part[4 + k] = fmadd_u(nm0, D.D2[k], L.part[4 + k]);
 #pragma unroll
-    for (int q = 0; q < 7; ++q) L.part[9 + q] = fmadd(nm0, D.D3[q], L.part[9 + q]);
+    for (int q = 0; q < 7; ++q) L.part[9 + q] = fmadd_u(nm0, D.D3[q], L.part[9 + q]);
     T w[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) w[q] = SRC_MP ? fmadd(nm0, a3A[q], s.B3[q]) : nm0 * a3A[q];
@@ -526,8 +532,8 @@ __device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const 
     for (int i = 0; i < 3; ++i) {
         T c = S.part[i];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) c = fmadd(w[q], D.U[i][q], c);
-        S.part[i] = c;
+        for (int q = 0; q < 7; ++q) c = fmadd_u(w[q], D.U[i][q], c);
+        S.part[i] = renorm(c);
     }
 }
 
@@ -541,20 +547,20 @@ __device__ __forceinline__ void acc_mx(T Rx, T Ry, T Rz, const Src<T> &s, Acc<T,
     D.template eval<true>(Rx, Ry, Rz);
     T a = -s.m0 * D.D0;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) a = fmadd(-s.B2[k], D.D2[k], a);
+    for (int k = 0; k < 5; ++k) a = fmadd_u(-s.B2[k], D.D2[k], a);
 #pragma unroll
-    for (int q = 0; q < 7; ++q) a = fmadd(s.B3[q], D.D3[q], a);
-    L.part[0] += a;
+    for (int q = 0; q < 7; ++q) a = fmadd_u(s.B3[q], D.D3[q], a);
+    L.part[0] = add_u(L.part[0], renorm(a));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         T b = -s.m0 * D.D1[i];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) b = fmadd(-s.B2[k], D.d3slice(i, k), b);
-        L.part[1 + i] += b;
+        for (int k = 0; k < 5; ++k) b = fmadd_u(-s.B2[k], D.d3slice(i, k), b);
+        L.part[1 + i] = add_u(L.part[1 + i], renorm(b));
         T c = S.part[i];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) c = fmadd(s.B3[q], D.U[i][q], c);
-        S.part[i] = c;
+        for (int q = 0; q < 7; ++q) c = fmadd_u(s.B3[q], D.U[i][q], c);
+        S.part[i] = renorm(c);
     }
 }
 
@@ -720,8 +726,8 @@ __device__ __forceinline__ void mono_entry(const T *Wb, const int *woff, const T
         const T m1 = src[b * WSTRIDE + DZ1];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            A[b].part[k] = fmadd(c[k], m0, A[b].part[k]);
-            B[b].part[k] = fmadd(c[k], m1, B[b].part[k]);
+            A[b].part[k] = fmadd_u(c[k], m0, A[b].part[k]);
+            B[b].part[k] = fmadd_u(c[k], m1, B[b].part[k]);
         }
     }
 }

@@ -61,6 +61,13 @@ __host__ __device__ constexpr int i3_at(int q, int which)
 // has the double-float one)
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+// chain forms (double-float skips the renormalisation until renorm())
+__device__ __forceinline__ float fmadd_u(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd_u(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float add_u(float a, float b) { return a + b; }
+__device__ __forceinline__ double add_u(double a, double b) { return a + b; }
+__device__ __forceinline__ float renorm(float a) { return a; }
+__device__ __forceinline__ double renorm(double a) { return a; }
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }

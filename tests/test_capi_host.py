@@ -56,7 +56,8 @@ def _adaptive(max_level=4, r=0.12):
     return adaptive_tree(want, max_level)
 
 
-@pytest.mark.parametrize("case", ["cfg1", "cfg2", "adaptive4", "adaptive4_035"])
+@pytest.mark.parametrize("case", ["cfg1", "cfg2", "adaptive4", "adaptive4_035", "adaptive4_055",
+                                  "adaptive4_030"])
 def test_planner_counts_match_oracle(case):
     if case.startswith("cfg"):
         c = make_config(case)
@@ -64,7 +65,8 @@ def test_planner_counts_match_oracle(case):
     else:
         desc = _adaptive()
         rho = np.ones((len(leaf_nodes(desc)), 512))
-        theta = 0.35 if case.endswith("035") else 0.5
+        # stencil reach 5 (0.5, 0.35), 3 (0.55) and 7 (0.3)
+        theta = {"035": 0.35, "055": 0.55, "030": 0.3}.get(case[-3:], 0.5)
     t = plan(desc, theta)
     ot = O.Tree(desc, theta)
     M, com = O.upward(ot, rho)

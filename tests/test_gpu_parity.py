@@ -56,6 +56,14 @@ def small_case(name):
         return make_config(name)
     if name == "cfg2_t035":
         return make_config("cfg2", theta=0.35)
+    # the other two stencil reaches (theta in (1/2, 1/sqrt 3] gives reach 3,
+    # theta in (1/4, 1/3] reach 7); 0.5 and 0.35 both give reach 5
+    if name == "cfg2_t055":
+        return make_config("cfg2", theta=0.55)
+    if name == "adaptive4_t030":
+        c = small_case("adaptive4")
+        c["theta"] = 0.3
+        return c
     rng = np.random.default_rng(7)
     if name == "adaptive4":
         desc = _adaptive_desc()
@@ -70,7 +78,7 @@ def small_case(name):
                 box_lo=(0.0, 0.0, 0.0), box_size=1.0)
 
 
-SMALL = ["cfg1", "cfg2", "cfg2_t035", "adaptive4", "batch3"]
+SMALL = ["cfg1", "cfg2", "cfg2_t035", "cfg2_t055", "adaptive4", "adaptive4_t030", "batch3"]
 _ORACLE = {}
 
 

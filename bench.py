@@ -128,6 +128,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def rank_max(torch, dist, v, device):
+    """The maximum of v over the ranks of the process group (v itself without
+    one): replicas are timed by the slowest rank."""
+    if dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(interactions_per_step, world, ms_max):
+    """Whole-job throughput of `world` independent replicas: every rank's
+    interactions over the slowest rank's step time."""
+    return interactions_per_step * world / (ms_max / 1000.0)
+
+
 def measured_peaks():
     try:
         return json.load(open(PEAKS_FILE))
@@ -290,11 +306,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(torch, dist, v, "cuda")
 
     c = make_config(args.workload)
     rho_host = torch.from_numpy(c["rho"]).pin_memory()
@@ -326,7 +338,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     ms_max = max_over_ranks(ms)
-    value = interactions * world / (ms_max / 1000.0)
+    value = replica_value(interactions, world, ms_max)
 
     # end to end through the public API: pinned host density in, totals out
     tot_host = torch.empty_like(solver.totals, device="cpu").pin_memory()
@@ -342,7 +354,7 @@ def run_ours(args):
         if k >= args.warmup:
             e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     e2e_ms_max = max_over_ranks(float(np.mean(e2e_ms)))
-    e2e = {"value": interactions * world / (e2e_ms_max / 1000.0), "unit": UNIT,
+    e2e = {"value": replica_value(interactions, world, e2e_ms_max), "unit": UNIT,
            "h2d_bytes_per_step": int(rho_host.numel() * 8),
            "d2h_bytes_per_step": int(tot_host.numel() * 8),
            "ms_per_step": e2e_ms_max}

@@ -1,0 +1,62 @@
+"""The multi-GPU path of bench.py on the CPU: replicas only (the solve has no
+exchange step), timed by the slowest rank; world size 2 over gloo."""
+
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 3.0 + rank                    # rank 1 is the slower replica
+    ms_max = bench.rank_max(torch, dist, ms, "cpu")
+    out[rank] = (ms_max, bench.replica_value(1000, world, ms_max))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_slowest_rank_sets_the_time():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        ms_max, value = res[r]
+        assert ms_max == 4.0
+        # both replicas' interactions over the slowest time
+        assert value == pytest.approx(1000 * world / 4.0e-3)
+
+
+def test_single_process_needs_no_group():
+    assert bench.rank_max(torch, None, 2.5, "cpu") == 2.5
+    assert bench.replica_value(10, 1, 2.0) == pytest.approx(5000.0)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""

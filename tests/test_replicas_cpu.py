@@ -37,7 +37,7 @@ def _rank_main(rank, world, port, out):
 def test_slowest_rank_sets_the_time():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)

@@ -1,6 +1,8 @@
 """Autotuner for the same-level kernels' launch shapes.
 
-Times ``fmm_m2l`` on the caller's tree for every candidate of
+Times whole solve steps (``Solver.step``: the passes overlapped on two streams,
+so co-resident kernels share SMs as they will in the real step) on the
+caller's tree for every candidate of
 ``fmm_tuning`` (sub-grids per pass of the monopole kernel, persistent CTAs per
 SM) with CUDA events on the current stream, keeps the fastest and leaves it
 set on the tree.  Each candidate is run ``reps`` times after one warm-up; the
@@ -39,13 +41,13 @@ def tune(solver, reps=5, verbose=False):
     results = []
     for cand in candidates:
         B.fmm_set_tuning(solver.tree, **cand)
-        solver.m2l()
+        solver.step()
         times = []
         for _ in range(reps):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            solver.m2l()
+            solver.step()
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b))

@@ -370,6 +370,52 @@ __device__ __forceinline__ T acc_lo(const Acc<T, N> &a, int k) { return a.lo[k];
 template <int N>
 __device__ __forceinline__ dfloat acc_lo(const Acc<dfloat, N> &, int) { return dfloat(0.f); }
 
+// Float accumulator whose (hi, lo) pairs live in shared memory, in this
+// thread's column of a [components][2][threads] array: only the chunk sums
+// take registers, which lets the multipole kernel keep three CTAs per SM.
+template <int N>
+struct SmemAcc {
+    float part[N];
+    float *col;                       // the (hi, lo) pairs of component k at col[k * 2 * kThreads]
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            part[k] = 0.f;
+            col[k * 2 * kThreads] = 0.f;
+            col[(k * 2 + 1) * kThreads] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void flush()
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            float s, e;
+            two_sum(col[k * 2 * kThreads], part[k], s, e);
+            col[k * 2 * kThreads] = s;
+            col[(k * 2 + 1) * kThreads] += e;
+            part[k] = 0.f;
+        }
+    }
+};
+template <int N>
+__device__ __forceinline__ float acc_hi(const SmemAcc<N> &a, int k) { return a.col[k * 2 * kThreads]; }
+template <int N>
+__device__ __forceinline__ float acc_lo(const SmemAcc<N> &a, int k)
+{
+    return a.col[(k * 2 + 1) * kThreads];
+}
+
+// the multipole kernel's accumulators: shared-memory pairs for float
+template <typename T, int N>
+struct MpAcc {
+    using type = Acc<T, N>;
+};
+template <int N>
+struct MpAcc<float, N> {
+    using type = SmemAcc<N>;
+};
+
 // store component k of a target cell: level units; (hi, lo) float pairs for
 // float (renormalised) and double-float (lo is zero there), else double
 template <typename T>
@@ -420,9 +466,8 @@ __device__ __forceinline__ void store_target_values(const KParams &P, int node, 
     store_neg_sum<T>(P, node, 19, cell, hi, lo, 11, 15);   // zzz = -(xxz + yyz)
 }
 
-template <typename T>
-__device__ __forceinline__ void store_target(const KParams &P, int node, int cell,
-                                             const Acc<T, 16> &L)
+template <typename T, class LA>
+__device__ __forceinline__ void store_target(const KParams &P, int node, int cell, const LA &L)
 {
     T hi[16], lo[16];
 #pragma unroll
@@ -497,9 +542,9 @@ __device__ __forceinline__ void zero_moments(Src<T> &s)
 // add that sum to the chunk sum once, so every source costs one rounding at
 // the chunk sum's magnitude; orders 2-3 and the correction take each product
 // straight into their sums as one fused multiply-add.
-template <typename T, bool SRC_MP>
-__device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const T a3A[7],
-                                       Acc<T, 16> &L, Acc<T, 3> &S)
+template <typename T, bool SRC_MP, class LA, class SA>
+__device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const T a3A[7], LA &L,
+                                       SA &S)
 {
     DTraceless<T> D;
     D.template eval<true>(Rx, Ry, Rz);
@@ -590,20 +635,21 @@ __device__ __forceinline__ double to_double(float v) { return double(v); }
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(dfloat v) { return v.to_double(); }
 
-template <typename T>
-__device__ __forceinline__ double acc_value(const Acc<T, 3> &S, int i)
+template <typename T, class SA>
+__device__ __forceinline__ double acc_value(const SA &S, int i)
 {
     return to_double(acc_hi(S, i)) + to_double(acc_lo(S, i));
 }
 
 // ------------------------------------------------------------ mp_kernel
 template <typename T>
-// float: two CTAs per SM (128 registers; the (hi, lo) pairs, touched once per
-// chunk, are what the register budget squeezes)
-__global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P)
+// float: three CTAs per SM (85 registers): the compensation pairs, touched
+// once per chunk, live in shared memory after the window
+__global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *W = reinterpret_cast<T *>(smem_raw);
+    float *Cs = reinterpret_cast<float *>(W + 8 * P.sub_stride) + threadIdx.x;   // float only
     __shared__ int s_nbr[27], s_leaf[27], s_row[27], s_item;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = warp;
@@ -629,8 +675,12 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 2 : 1) mp_kernel(KParams P
             const int base = cx + P.py * cy + P.pz * cz;
             T dA[3], a3A[7];
             load_target<T>(P, ti.mp_row, parity_index(ax, ay, az), dA, a3A);
-            Acc<T, 16> L;
-            Acc<T, 3> S;
+            typename MpAcc<T, 16>::type L;
+            typename MpAcc<T, 3>::type S;
+            if constexpr (kF32<T>) {
+                L.col = Cs;
+                S.col = Cs + 16 * 2 * kThreads;
+            }
             L.zero();
             S.zero();
             // well-separated sources: refined (full moments) or leaf (mass)
@@ -1086,8 +1136,8 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     const int cap = t->tuning.ctas_per_sm;
     const size_t wbytes = size_t(8) * Pl.sub_stride * sizeof(T);
     // mp_kernel: one window (masses of leaf sources, moment offsets of
-    // refined ones)
-    const size_t mp_bytes = wbytes;
+    // refined ones); float adds its compensation pairs, [19][2][threads]
+    const size_t mp_bytes = wbytes + (kF32<T> ? size_t(19) * 2 * kThreads * sizeof(float) : 0);
     cudaError_t e = Kernels<T>::mp(mp_bytes);
     if (e != cudaSuccess) return e;
     if (parts & M2L_RESET) {

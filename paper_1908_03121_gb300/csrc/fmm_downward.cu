@@ -68,20 +68,19 @@ __device__ __forceinline__ void l2l_cell_fp64(const NodeInfo &ni, int node, int 
                                               const void *__restrict__ Lv, const double *dL1,
                                               const double *__restrict__ com,
                                               double *__restrict__ L64, double *dacc, double lo_x,
-                                              double lo_y, double lo_z)
+                                              double lo_y, double lo_z, double (&out)[20],
+                                              double (&corr)[3])
 {
     constexpr int NK = NMAX == 1 ? 4 : 20;
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
     const double *L = lv + ni.level * LEVEL_FIELDS;
     const double sc[4] = {L[LV_S0], L[LV_S1], L[LV_S2], L[LV_S3]};
-    double out[20];
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
         const size_t idx = (size_t(node) * NCOMP + k) * NCELL + c;
         const double own = static_cast<const double *>(Lv)[idx];
         out[k] = own * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
     }
-    double corr[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc[1];
     if (ni.parent >= 0) {
@@ -132,7 +131,8 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
                                                const double *__restrict__ com,
                                                double *__restrict__ L64, double *dacc,
                                                float *__restrict__ down, double lo_x,
-                                               double lo_y, double lo_z)
+                                               double lo_y, double lo_z, double (&out)[20],
+                                               double (&corr)[3])
 {
     constexpr int NK = NMAX == 1 ? 4 : 20;
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
@@ -152,8 +152,6 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
         offc[1] = d2f_trunc(com[(size_t(node) * 3 + 1) * NCELL + c] - (lo_y + (8.0 * ni.iy + y + 0.5) * h));
         offc[2] = d2f_trunc(com[(size_t(node) * 3 + 2) * NCELL + c] - (lo_z + (8.0 * ni.iz + z + 0.5) * h));
     }
-    double out[20];
-    double corr[3];
     if (ni.parent >= 0) {
         const int pc = (4 * (ni.ix & 1) + (x >> 1)) + 8 * (4 * (ni.iy & 1) + (y >> 1)) +
                        64 * (4 * (ni.iz & 1) + (z >> 1));
@@ -221,7 +219,7 @@ __device__ __forceinline__ void l2l_cell_df(const NodeInfo &ni, int node, int c,
                                             const double *__restrict__ com,
                                             double *__restrict__ L64, double *dacc,
                                             dfloat *__restrict__ down, double lo_x, double lo_y,
-                                            double lo_z)
+                                            double lo_z, double (&out)[20], double (&corr)[3])
 {
     constexpr int NK = NMAX == 1 ? 4 : 20;
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
@@ -244,8 +242,6 @@ __device__ __forceinline__ void l2l_cell_df(const NodeInfo &ni, int node, int c,
         offc[2] = df_from_double(com[(size_t(node) * 3 + 2) * NCELL + c] -
                                  fma(f2d_bits(float(8 * ni.iz + z) + 0.5f), h, lo_z));
     }
-    double out[20];
-    double corr[3];
     if (ni.parent >= 0) {
         const int pc = (4 * (ni.ix & 1) + (x >> 1)) + 8 * (4 * (ni.iy & 1) + (y >> 1)) +
                        64 * (4 * (ni.iz & 1) + (z >> 1));
@@ -290,6 +286,30 @@ __device__ __forceinline__ void l2l_cell_df(const NodeInfo &ni, int node, int c,
     }
 }
 
+// one cell's shift in the tree's precision (MODE: FMM_FP64, FMM_MIXED or
+// FMM_DFLOAT); besides being stored, the results come back in out, corr
+template <int MODE, int NMAX>
+__device__ __forceinline__ void l2l_cell(const NodeInfo *__restrict__ info, const NodeInfo &ni,
+                                         int node, int c, const double *__restrict__ levels,
+                                         const dfloat *__restrict__ levels_df,
+                                         const void *__restrict__ Lv, const float *__restrict__ Lc,
+                                         const double *dL1, const double *__restrict__ com,
+                                         double *__restrict__ L64, double *dacc, float *down,
+                                         double lo_x, double lo_y, double lo_z, double (&out)[20],
+                                         double (&corr)[3])
+{
+    if constexpr (MODE == FMM_MIXED)
+        l2l_cell_mixed<NMAX>(ni, node, c, info, levels, static_cast<const float *>(Lv), Lc, dL1,
+                             com, L64, dacc, down, lo_x, lo_y, lo_z, out, corr);
+    else if constexpr (MODE == FMM_DFLOAT)
+        l2l_cell_df<NMAX>(ni, node, c, info, levels, levels_df, static_cast<const float *>(Lv), Lc,
+                          dL1, com, L64, dacc, reinterpret_cast<dfloat *>(down), lo_x, lo_y, lo_z,
+                          out, corr);
+    else
+        l2l_cell_fp64<NMAX>(ni, node, c, levels, Lv, dL1, com, L64, dacc, lo_x, lo_y, lo_z, out,
+                            corr);
+}
+
 // 64 threads per CTA, 8 CTAs per node, so that the few nodes of a coarse
 // level still spread their FP64 work over many SMs
 constexpr int kSliceThreads = 64;
@@ -311,31 +331,13 @@ __global__ void __launch_bounds__(kSliceThreads) l2l_kernel(const NodeInfo *__re
     const int node = nodes[blockIdx.x >> 3];
     const NodeInfo ni = info[node];
     const int c = (blockIdx.x & 7) * kSliceThreads + threadIdx.x;
-    if constexpr (MODE == FMM_MIXED) {
-        const float *Lhi = static_cast<const float *>(Lv);
-        if (ni.leaf_row >= 0)
-            l2l_cell_mixed<1>(ni, node, c, info, levels, Lhi, Lc, dL1, com, L64, dacc, down, lo_x,
-                              lo_y, lo_z);
-        else
-            l2l_cell_mixed<3>(ni, node, c, info, levels, Lhi, Lc, dL1, com, L64, dacc, down, lo_x,
-                              lo_y, lo_z);
-    } else if constexpr (MODE == FMM_DFLOAT) {
-        const float *Lhi = static_cast<const float *>(Lv);
-        dfloat *dd = reinterpret_cast<dfloat *>(down);
-        if (ni.leaf_row >= 0)
-            l2l_cell_df<1>(ni, node, c, info, levels, levels_df, Lhi, Lc, dL1, com, L64, dacc, dd,
-                           lo_x, lo_y, lo_z);
-        else
-            l2l_cell_df<3>(ni, node, c, info, levels, levels_df, Lhi, Lc, dL1, com, L64, dacc, dd,
-                           lo_x, lo_y, lo_z);
-    } else {
-        if (ni.leaf_row >= 0)
-            l2l_cell_fp64<1>(ni, node, c, levels, Lv, dL1, com, L64, dacc, lo_x, lo_y,
-                                    lo_z);
-        else
-            l2l_cell_fp64<3>(ni, node, c, levels, Lv, dL1, com, L64, dacc, lo_x, lo_y,
-                                    lo_z);
-    }
+    double out[20], corr[3];
+    if (ni.leaf_row >= 0)
+        l2l_cell<MODE, 1>(info, ni, node, c, levels, levels_df, Lv, Lc, dL1, com, L64, dacc, down,
+                          lo_x, lo_y, lo_z, out, corr);
+    else
+        l2l_cell<MODE, 3>(info, ni, node, c, levels, levels_df, Lv, Lc, dL1, com, L64, dacc, down,
+                          lo_x, lo_y, lo_z, out, corr);
 }
 
 // 64 threads per leaf node, one (x, y) column of 8 cells each.
@@ -370,38 +372,41 @@ __device__ __forceinline__ void block_sum(V v[NV], V (*sh)[NV])
     }
 }
 
-__global__ void __launch_bounds__(kForceThreads) forces_kernel(
-    const NodeInfo *__restrict__ info, const int32_t *__restrict__ leaves,
-    const double *__restrict__ levels, const double *__restrict__ L64,
-    const double *__restrict__ dacc, const double *__restrict__ rho, double *__restrict__ phi,
-    double *__restrict__ g, double *__restrict__ partials, double box_size)
-{
-    __shared__ double sh[kForceThreads / 32][6];
-    __shared__ float shf[kForceThreads / 32][2];
-    const int node = leaves[blockIdx.x];
-    const NodeInfo ni = info[node];
-    const int row = ni.leaf_row;
-    const double h = levels[ni.level * LEVEL_FIELDS + LV_H];
-    const double h3 = levels[ni.level * LEVEL_FIELDS + LV_H3];
-    const double half = 0.5 * box_size;
-    const int x = threadIdx.x & 7, y = threadIdx.x >> 3;
-    // position from the box centre (the box corner cancels); x, y fixed per thread
-    const double X0 = (8.0 * ni.ix + x + 0.5) * h - half;
-    const double X1 = (8.0 * ni.iy + y + 0.5) * h - half;
-    const double Z0 = (8.0 * ni.iz + 0.5) * h - half;
-    const float X0f = d2f_trunc(X0), X1f = d2f_trunc(X1), Z0f = d2f_trunc(Z0), hf = d2f_trunc(h);
+// per-thread state of the force pass: the (x, y) column's position and sums
+struct ForceColumn {
+    double X0, X1, Z0, h, h3;
+    float X0f, X1f, Z0f, hf;
     double F[3] = {0.0, 0.0, 0.0}, T[2] = {0.0, 0.0};
     float nf = 0.f, nt = 0.f;
-#pragma unroll
-    for (int z = 0; z < 8; ++z) {
-        const int c = threadIdx.x + 64 * z;
-        const double m = rho[size_t(row) * NCELL + c] * h3;
-        phi[size_t(row) * NCELL + c] = L64[(size_t(node) * NCOMP) * NCELL + c];
+
+    __device__ __forceinline__ ForceColumn(const NodeInfo &ni, const double *levels,
+                                           double box_size)
+    {
+        h = levels[ni.level * LEVEL_FIELDS + LV_H];
+        h3 = levels[ni.level * LEVEL_FIELDS + LV_H3];
+        const double half = 0.5 * box_size;
+        const int x = threadIdx.x & 7, y = threadIdx.x >> 3;
+        // position from the box centre (the box corner cancels); x, y fixed per thread
+        X0 = (8.0 * ni.ix + x + 0.5) * h - half;
+        X1 = (8.0 * ni.iy + y + 0.5) * h - half;
+        Z0 = (8.0 * ni.iz + 0.5) * h - half;
+        X0f = d2f_trunc(X0);
+        X1f = d2f_trunc(X1);
+        Z0f = d2f_trunc(Z0);
+        hf = d2f_trunc(h);
+    }
+
+    // cell z of the column: phi = L0, g = -(L1 + dL1), and its terms of the sums
+    __device__ __forceinline__ void cell(int row, int c, int z, double rho_c, double L0,
+                                         const double L1[3], const double acc[3],
+                                         double *__restrict__ phi, double *__restrict__ g)
+    {
+        const double m = rho_c * h3;
+        phi[size_t(row) * NCELL + c] = L0;
         double gv[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            gv[a] = -(L64[(size_t(node) * NCOMP + 1 + a) * NCELL + c] +
-                      dacc[(size_t(node) * 3 + a) * NCELL + c]);
+            gv[a] = -(L1[a] + acc[a]);
             g[(size_t(row) * 3 + a) * NCELL + c] = gv[a];
             F[a] = fma(m, gv[a], F[a]);                 // f = m g
         }
@@ -415,22 +420,84 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
         const float mf = d2f_trunc(m);
         const float gf[3] = {d2f_trunc(gv[0]), d2f_trunc(gv[1]), d2f_trunc(gv[2])};
         const float X2f = fmaf(float(z), hf, Z0f);
-        const float uf[3] = {X1f * gf[2] - X2f * gf[1], X2f * gf[0] - X0f * gf[2],
-                             X0f * gf[1] - X1f * gf[0]};
-        nf += mf * sqrtf(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
-        nt += mf * sqrtf(uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
+        // (explicit fused forms: the fused leaf pass must round exactly as
+        // the force pass does)
+        const float uf[3] = {fmaf(X1f, gf[2], -(X2f * gf[1])), fmaf(X2f, gf[0], -(X0f * gf[2])),
+                             fmaf(X0f, gf[1], -(X1f * gf[0]))};
+        nf = fmaf(mf, sqrtf(fmaf(gf[0], gf[0], fmaf(gf[1], gf[1], gf[2] * gf[2]))), nf);
+        nt = fmaf(mf, sqrtf(fmaf(uf[0], uf[0], fmaf(uf[1], uf[1], uf[2] * uf[2]))), nt);
     }
-    const double S0 = fma(h, T[0], Z0 * F[0]), S1 = fma(h, T[1], Z0 * F[1]);
-    double v[6] = {F[0], F[1], F[2], fma(X1, F[2], -S1), fma(-X0, F[2], S0),
-                   fma(X0, F[1], -X1 * F[0])};
-    float vf[2] = {nf, nt};
-    block_sum<kForceThreads, double, 6>(v, sh);
-    block_sum<kForceThreads, float, 2>(vf, shf);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 6; ++k) partials[size_t(row) * 8 + k] = v[k];
-        partials[size_t(row) * 8 + 6] = double(vf[0]);
-        partials[size_t(row) * 8 + 7] = double(vf[1]);
+
+    // the node's fixed-order block sums into its partials row
+    __device__ __forceinline__ void finish(int row, double *__restrict__ partials)
+    {
+        __shared__ double sh[kForceThreads / 32][6];
+        __shared__ float shf[kForceThreads / 32][2];
+        const double S0 = fma(h, T[0], Z0 * F[0]), S1 = fma(h, T[1], Z0 * F[1]);
+        double v[6] = {F[0], F[1], F[2], fma(X1, F[2], -S1), fma(-X0, F[2], S0),
+                       fma(X0, F[1], -X1 * F[0])};
+        float vf[2] = {nf, nt};
+        block_sum<kForceThreads, double, 6>(v, sh);
+        block_sum<kForceThreads, float, 2>(vf, shf);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 6; ++k) partials[size_t(row) * 8 + k] = v[k];
+            partials[size_t(row) * 8 + 6] = double(vf[0]);
+            partials[size_t(row) * 8 + 7] = double(vf[1]);
+        }
     }
+};
+
+__global__ void __launch_bounds__(kForceThreads) forces_kernel(
+    const NodeInfo *__restrict__ info, const int32_t *__restrict__ leaves,
+    const double *__restrict__ levels, const double *__restrict__ L64,
+    const double *__restrict__ dacc, const double *__restrict__ rho, double *__restrict__ phi,
+    double *__restrict__ g, double *__restrict__ partials, double box_size)
+{
+    const int node = leaves[blockIdx.x];
+    const NodeInfo ni = info[node];
+    const int row = ni.leaf_row;
+    ForceColumn col(ni, levels, box_size);
+#pragma unroll
+    for (int z = 0; z < 8; ++z) {
+        const int c = threadIdx.x + 64 * z;
+        double L1[3], acc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            L1[a] = L64[(size_t(node) * NCOMP + 1 + a) * NCELL + c];
+            acc[a] = dacc[(size_t(node) * 3 + a) * NCELL + c];
+        }
+        col.cell(row, c, z, rho[size_t(row) * NCELL + c], L64[(size_t(node) * NCOMP) * NCELL + c],
+                 L1, acc, phi, g);
+    }
+    col.finish(row, partials);
+}
+
+// fmm_step's last pass over the leaves: each leaf cell's shift (as
+// l2l_kernel) and its forces (as forces_kernel) in one kernel, the shifted
+// expansion going straight from registers into the force terms; the same
+// arithmetic, in the same order, as the two kernels
+template <int MODE>
+__global__ void __launch_bounds__(kForceThreads) leaf_finish_kernel(
+    const NodeInfo *__restrict__ info, const int32_t *__restrict__ leaves,
+    const double *__restrict__ levels, const dfloat *__restrict__ levels_df,
+    const void *__restrict__ Lv, const float *__restrict__ Lc, const double *dL1,
+    const double *__restrict__ com, double *__restrict__ L64, double *dacc, float *down,
+    const double *__restrict__ rho, double *__restrict__ phi, double *__restrict__ g,
+    double *__restrict__ partials, double lo_x, double lo_y, double lo_z, double box_size)
+{
+    const int node = leaves[blockIdx.x];
+    const NodeInfo ni = info[node];
+    const int row = ni.leaf_row;
+    ForceColumn col(ni, levels, box_size);
+#pragma unroll 1
+    for (int z = 0; z < 8; ++z) {
+        const int c = threadIdx.x + 64 * z;
+        double out[20], corr[3];
+        l2l_cell<MODE, 1>(info, ni, node, c, levels, levels_df, Lv, Lc, dL1, com, L64, dacc, down,
+                          lo_x, lo_y, lo_z, out, corr);
+        col.cell(row, c, z, rho[size_t(row) * NCELL + c], out[0], out + 1, corr, phi, g);
+    }
+    col.finish(row, partials);
 }
 
 // Per-tree sums of the per-leaf-node partials in two fixed-order stages, so
@@ -499,6 +566,31 @@ cudaError_t launch_l2l_nodes(const fmm_tree_s *t, const ListRange &r, const void
     return cudaGetLastError();
 }
 
+cudaError_t launch_leaf_finish(const fmm_tree_s *t, const void *L, const float *Lc,
+                               const double *dL1, const double *com, double *L64, double *dacc,
+                               const double *rho, double *phi, double *g, cudaStream_t s)
+{
+    const ListRange &r = t->plan.leaves;
+    if (r.count == 0) return cudaSuccess;
+    const auto &c = t->cfg;
+    const dfloat *ldf = reinterpret_cast<const dfloat *>(t->dev.levels_df);
+    const int32_t *nodes = t->dev.lists + r.off;
+    const unsigned grid = unsigned(r.count);
+    if (c.precision == FMM_MIXED)
+        leaf_finish_kernel<FMM_MIXED><<<grid, kForceThreads, 0, s>>>(
+            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, t->dev.down, rho,
+            phi, g, t->dev.partials, c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
+    else if (c.precision == FMM_DFLOAT)
+        leaf_finish_kernel<FMM_DFLOAT><<<grid, kForceThreads, 0, s>>>(
+            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, t->dev.down, rho,
+            phi, g, t->dev.partials, c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
+    else
+        leaf_finish_kernel<FMM_FP64><<<grid, kForceThreads, 0, s>>>(
+            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, nullptr, rho, phi,
+            g, t->dev.partials, c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *dacc,
                           const double *rho, double *phi, double *g, double *totals,
                           cudaStream_t s)
@@ -513,6 +605,11 @@ cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    return launch_force_sums(t, totals, s);
+}
+
+cudaError_t launch_force_sums(const fmm_tree_s *t, double *totals, cudaStream_t s)
+{
     timing_begin(t, FMM_K_REDUCE, s);
     const int chunks = t->plan.reduce_chunks;
     reduce_chunk_kernel<<<dim3(unsigned(t->n_trees), unsigned(chunks)), 512, 0, s>>>(

@@ -762,11 +762,11 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     o->launches_m2l = m2l;
     o->launches_step = up + m2l + down + 3;
     // fmm_step: pack in two launches (leaves, refined), the refined levels'
-    // shifts per level and every leaf's in one launch
+    // shifts per level, every leaf's shift and forces in one launch
     int refined_levels = 0;
     for (int lev = 1; lev <= t->max_level; ++lev) refined_levels += P.refined_at[size_t(lev)].count > 0;
     o->launches_fused = up + (m2l - 1) + (P.leaves.count > 0) + (P.refined.count > 0) +
-                        refined_levels + (P.leaves.count > 0) + 3;
+                        refined_levels + (P.leaves.count > 0) + 2;
     if ((t->cfg.flags & FMM_FLAG_TIMING) && !t->host_only) {
         o->timing = 1;
         timing_fold(t);
@@ -916,10 +916,12 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
         FMM_STEP_TRY(launch_l2l_nodes(t, P.refined_at[size_t(lev)], L, L_comp, dL1, com, L64,
                                       dL1_acc, s), "l2l launch");
     FMM_STEP_TRY(cudaEventRecord(ev[2], s), "cudaEventRecord");
-    // aux: every leaf's shift, forces and sums; join
+    // aux: every leaf's shift and forces in one pass (the shifted expansion
+    // feeds the forces from registers), the sums; join
     FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[2], 0), "cudaStreamWaitEvent");
-    FMM_STEP_TRY(launch_l2l_nodes(t, P.leaves, L, L_comp, dL1, com, L64, dL1_acc, a), "l2l launch");
-    FMM_STEP_TRY(launch_forces(t, L64, dL1_acc, rho, phi, g, totals, a), "forces launch");
+    FMM_STEP_TRY(launch_leaf_finish(t, L, L_comp, dL1, com, L64, dL1_acc, rho, phi, g, a),
+                 "leaf launch");
+    FMM_STEP_TRY(launch_force_sums(t, totals, a), "reduce launch");
     FMM_STEP_TRY(cudaEventRecord(ev[3], a), "cudaEventRecord");
     FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[3], 0), "cudaStreamWaitEvent");
 #undef FMM_STEP_TRY

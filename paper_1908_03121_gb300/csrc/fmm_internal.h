@@ -187,6 +187,10 @@ cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L,
 cudaError_t launch_l2l_nodes(const fmm_tree_s *t, const ListRange &r, const void *L,
                              const float *Lc, const double *dL1, const double *com,
                              double *L64, double *dacc, cudaStream_t s);
+cudaError_t launch_leaf_finish(const fmm_tree_s *t, const void *L, const float *Lc,
+                               const double *dL1, const double *com, double *L64, double *dacc,
+                               const double *rho, double *phi, double *g, cudaStream_t s);
+cudaError_t launch_force_sums(const fmm_tree_s *t, double *totals, cudaStream_t s);
 cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *dacc,
                           const double *rho, double *phi, double *g, double *totals,
                           cudaStream_t s);

@@ -277,7 +277,8 @@ int fmm_get_tuning(fmm_tree_t tree, fmm_tuning *tuning);
  * only leaf masses) runs beside the upward pass of the refined levels, the
  * refined levels' downward shifts beside the monopole<-multipole kernel, on a
  * second stream that the tree owns and that forks from and joins back into
- * `stream` through events, so the call can be captured into a CUDA graph.
+ * `stream` through events, so the call can be captured into a CUDA graph;
+ * every leaf's shift and forces run as one fused pass.
  * With FMM_FLAG_TIMING the four passes run in sequence on `stream` instead.
  * Errors: as the four calls.
  */

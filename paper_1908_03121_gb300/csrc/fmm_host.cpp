@@ -862,8 +862,8 @@ int fmm_forces(fmm_tree_t t, const double *L64, const double *dL1_acc, const dou
 // two streams: the monopole<-monopole kernel needs only leaf masses, so it
 // runs beside the upward pass of the refined levels; the refined levels'
 // shifts need only the multipole-target results, so they run beside the
-// monopole<-multipole kernel; the leaf shifts (all levels in one launch) and
-// the forces follow both.  Same kernels, same arithmetic, same results as
+// monopole<-multipole kernel; every leaf's shift and forces (all levels, one
+// fused launch) follow both.  The same arithmetic, hence the same results, as
 // fmm_upward, fmm_m2l, fmm_downward and fmm_forces in sequence.
 int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, float *L_comp,
              double *dL1, double *L64, double *dL1_acc, double *phi, double *g, double *totals,

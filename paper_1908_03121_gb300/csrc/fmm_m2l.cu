@@ -372,16 +372,21 @@ __device__ __forceinline__ dfloat acc_lo(const Acc<dfloat, N> &, int) { return d
 
 // Float accumulator whose (hi, lo) pairs live in shared memory, in this
 // thread's column of a [components][2][threads] array: only the chunk sums
-// take registers, which lets the multipole kernel keep three CTAs per SM.
-template <int N>
+// take registers.  The first NC components are compensated; the others
+// (the multipole target's orders 2-3, which reach the forces only through
+// the downward shifts, scaled by the small child offsets) are plain float
+// sums in registers.  Fewer pairs leave more of the SM's shared memory to
+// L1, where the multipole kernel rereads the sources' packed moments.
+template <int N, int NC = N>
 struct SmemAcc {
     float part[N];
-    float *col;                       // the (hi, lo) pairs of component k at col[k * 2 * kThreads]
+    float *col;                       // the (hi, lo) pairs of component k < NC at col[k * 2 * kThreads]
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            part[k] = 0.f;
+        for (int k = 0; k < N; ++k) part[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
             col[k * 2 * kThreads] = 0.f;
             col[(k * 2 + 1) * kThreads] = 0.f;
         }
@@ -389,7 +394,7 @@ struct SmemAcc {
     __device__ __forceinline__ void flush()
     {
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
+        for (int k = 0; k < NC; ++k) {
             float s, e;
             two_sum(col[k * 2 * kThreads], part[k], s, e);
             col[k * 2 * kThreads] = s;
@@ -398,23 +403,28 @@ struct SmemAcc {
         }
     }
 };
-template <int N>
-__device__ __forceinline__ float acc_hi(const SmemAcc<N> &a, int k) { return a.col[k * 2 * kThreads]; }
-template <int N>
-__device__ __forceinline__ float acc_lo(const SmemAcc<N> &a, int k)
+template <int N, int NC>
+__device__ __forceinline__ float acc_hi(const SmemAcc<N, NC> &a, int k)
 {
-    return a.col[(k * 2 + 1) * kThreads];
+    return k < NC ? a.col[k * 2 * kThreads] : a.part[k];
+}
+template <int N, int NC>
+__device__ __forceinline__ float acc_lo(const SmemAcc<N, NC> &a, int k)
+{
+    return k < NC ? a.col[(k * 2 + 1) * kThreads] : 0.f;
 }
 
-// the multipole kernel's accumulators: shared-memory pairs for float
+// the multipole kernel's accumulators: for float, shared-memory pairs for
+// orders 0-1 and the correction
 template <typename T, int N>
 struct MpAcc {
     using type = Acc<T, N>;
 };
 template <int N>
 struct MpAcc<float, N> {
-    using type = SmemAcc<N>;
+    using type = SmemAcc<N, N == 16 ? 4 : N>;
 };
+constexpr int kMpPairs = 4 + 3;      // compensated float components of mp_kernel
 
 // store component k of a target cell: level units; (hi, lo) float pairs for
 // float (renormalised) and double-float (lo is zero there), else double
@@ -643,8 +653,8 @@ __device__ __forceinline__ double acc_value(const SA &S, int i)
 
 // ------------------------------------------------------------ mp_kernel
 template <typename T>
-// float: three CTAs per SM (85 registers): the compensation pairs, touched
-// once per chunk, live in shared memory after the window
+// float: three CTAs per SM (at most 85 registers): the compensation pairs,
+// touched once per chunk, live in shared memory after the window
 __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -679,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
             typename MpAcc<T, 3>::type S;
             if constexpr (kF32<T>) {
                 L.col = Cs;
-                S.col = Cs + 16 * 2 * kThreads;
+                S.col = Cs + 4 * 2 * kThreads;
             }
             L.zero();
             S.zero();
@@ -1136,8 +1146,8 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     const int cap = t->tuning.ctas_per_sm;
     const size_t wbytes = size_t(8) * Pl.sub_stride * sizeof(T);
     // mp_kernel: one window (masses of leaf sources, moment offsets of
-    // refined ones); float adds its compensation pairs, [19][2][threads]
-    const size_t mp_bytes = wbytes + (kF32<T> ? size_t(19) * 2 * kThreads * sizeof(float) : 0);
+    // refined ones); float adds its compensation pairs, [7][2][threads]
+    const size_t mp_bytes = wbytes + (kF32<T> ? size_t(kMpPairs) * 2 * kThreads * sizeof(float) : 0);
     cudaError_t e = Kernels<T>::mp(mp_bytes);
     if (e != cudaSuccess) return e;
     if (parts & M2L_RESET) {

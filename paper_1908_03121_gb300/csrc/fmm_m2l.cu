@@ -65,7 +65,7 @@ __device__ __forceinline__ T ldg_t(const T *p)
 
 constexpr int kThreads = 256;   // 8 warps = the 8 child parities
 constexpr int kChunk = 16;      // stencil entries per compensated chunk
-constexpr int Q_MP = 0, Q_MONO = 1, Q_MX = 2;   // work-queue heads
+constexpr int Q_MP = 0, Q_MONO = 1;            // work-queue heads
 
 struct KParams {
     const NodeInfo *info;
@@ -576,10 +576,25 @@ __device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const 
         }
         L.part[1 + i] = add_u(L.part[1 + i], renorm(b));
     }
+    if constexpr (kF32<T>) {
+        // orders 2-3 (12 components) in pairs on the paired FP32 pipe
+        // (fma.rn.f32x2: each half rounds as fmaf does)
+        const float2 nm2 = make_float2(nm0, nm0);
+        const float d23[12] = {D.D2[0], D.D2[1], D.D2[2], D.D2[3], D.D2[4], D.D3[0],
+                               D.D3[1], D.D3[2], D.D3[3], D.D3[4], D.D3[5], D.D3[6]};
 #pragma unroll
-    for (int k = 0; k < 5; ++k) L.part[4 + k] = fmadd_u(nm0, D.D2[k], L.part[4 + k]);
+        for (int k = 0; k < 12; k += 2) {
+            const float2 r = __ffma2_rn(nm2, make_float2(d23[k], d23[k + 1]),
+                                        make_float2(L.part[4 + k], L.part[5 + k]));
+            L.part[4 + k] = r.x;
+            L.part[5 + k] = r.y;
+        }
+    } else {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) L.part[9 + q] = fmadd_u(nm0, D.D3[q], L.part[9 + q]);
+        for (int k = 0; k < 5; ++k) L.part[4 + k] = fmadd_u(nm0, D.D2[k], L.part[4 + k]);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) L.part[9 + q] = fmadd_u(nm0, D.D3[q], L.part[9 + q]);
+    }
     T w[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) w[q] = SRC_MP ? fmadd(nm0, a3A[q], s.B3[q]) : nm0 * a3A[q];
@@ -617,15 +632,6 @@ __device__ __forceinline__ void acc_mx(T Rx, T Ry, T Rz, const Src<T> &s, Acc<T,
         for (int q = 0; q < 7; ++q) c = fmadd_u(s.B3[q], D.U[i][q], c);
         S.part[i] = renorm(c);
     }
-}
-
-// per-lane source position: slot of the neighbour node and parity index
-__device__ __forceinline__ void source_cell(int ax, int ay, int az, int ox, int oy, int oz,
-                                            int &slot, int &pi)
-{
-    const int bx = ax + ox + 8, by = ay + oy + 8, bz = az + oz + 8;   // >= 1
-    slot = (bx >> 3) + 3 * (by >> 3) + 9 * (bz >> 3);
-    pi = parity_index(bx & 7, by & 7, bz & 7);
 }
 
 // own packed data of a multipole target: centre-of-mass offset and a3 = B3/M0

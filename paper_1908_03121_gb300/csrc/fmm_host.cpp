@@ -264,6 +264,14 @@ static void build_stencils(fmm_tree_s *t)
     t->stencil.assign(size_t(8) * P.ent_stride, StencilEntry{0, 0, 0, 0});
     for (int p = 0; p < 8; ++p)
         for (size_t k = 0; k < lists[p].size(); ++k) t->stencil[size_t(p) * P.ent_stride + k] = lists[p][k];
+    t->stencil_f.assign(t->stencil.size() * 4, 0.f);
+    for (size_t i = 0; i < t->stencil.size(); ++i) {
+        const StencilEntry &e = t->stencil[i];
+        t->stencil_f[4 * i] = float(e.ox);
+        t->stencil_f[4 * i + 1] = float(e.oy);
+        t->stencil_f[4 * i + 2] = float(e.oz);
+        std::memcpy(&t->stencil_f[4 * i + 3], &e.woff, sizeof(float));
+    }
     // monopole kernel: parity 0's weights, every parity in parity 0's order
     t->coef32.assign(size_t(P.ent_stride) * 4, 0.f);
     t->coef64.assign(size_t(P.ent_stride) * 4, 0.0);
@@ -522,7 +530,7 @@ static void free_device(fmm_tree_s *t)
         t->aux = nullptr;
     }
     DeviceTables &d = t->dev;
-    void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.coef32, d.coef64, d.coefdf, d.mono_woff,
+    void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.stencil_f, d.coef32, d.coef64, d.coefdf, d.mono_woff,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.levels_df, d.mass, d.mp, d.counters,
                     d.partials, d.chunk_sums, d.up, d.down, d.mx_targets, d.mx_pairs};
     for (void *p : ptrs)
@@ -536,7 +544,8 @@ static int upload_tree(fmm_tree_s *t)
     int rc;
     if ((rc = upload(&d.info, t->info)) || (rc = upload(&d.children, t->children)) ||
         (rc = upload(&d.nbr, t->nbr)) || (rc = upload(&d.lists, t->lists)) ||
-        (rc = upload(&d.stencil, t->stencil)) || (rc = upload(&d.coef32, t->coef32)) ||
+        (rc = upload(&d.stencil, t->stencil)) || (rc = upload(&d.stencil_f, t->stencil_f)) ||
+        (rc = upload(&d.coef32, t->coef32)) ||
         (rc = upload(&d.coef64, t->coef64)) || (rc = upload(&d.coefdf, t->coefdf)) ||
         (rc = upload(&d.mono_woff, t->mono_woff)) ||
         (rc = upload(&d.tree_leaf_off, t->tree_leaf_off)) ||

@@ -73,6 +73,8 @@ struct DeviceTables {
     int32_t *nbr = nullptr;          // [n][27], slot (dx+1)+3(dy+1)+9(dz+1)
     int32_t *lists = nullptr;        // all node-index lists, see Plan offsets
     StencilEntry *stencil = nullptr; // [8][ent_stride]
+    float *stencil_f = nullptr;      // [8][ent_stride][4] the same entries with the offset
+                                     // as floats (window offset's int bits in the fourth)
     float *coef32 = nullptr;         // [ent_stride][4] monopole weights of parity 0
     double *coef64 = nullptr;        // [ent_stride][4]
     float *coefdf = nullptr;         // [ent_stride][4][hi, lo]
@@ -147,6 +149,7 @@ struct fmm_tree_s {
     std::vector<fmm::NodeInfo> info;
     std::vector<int32_t> children, nbr, lists;
     std::vector<fmm::StencilEntry> stencil;
+    std::vector<float> stencil_f;
     std::vector<float> coef32;
     std::vector<double> coef64;
     std::vector<float> coefdf;

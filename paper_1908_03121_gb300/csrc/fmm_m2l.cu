@@ -74,6 +74,7 @@ struct KParams {
     int32_t n_items;
     int32_t *counter;
     const StencilEntry *stencil;
+    const float4 *stencil_f;  // the same, offsets as floats, window offset's bits in w
     const void *coef;        // monopole weights of parity 0
     const int32_t *mono_woff;  // [8][ent_stride] window offsets in parity 0's order, reflected
     int n_far, n_near;       // identical for every parity
@@ -671,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
     const int p = warp;
     const int px = p & 1, py = (p >> 1) & 1, pz = p >> 2;
     const int cx = lane & 3, cy = (lane >> 2) & 3, cz0 = lane >> 4;
-    const StencilEntry *ent = P.stencil + p * P.ent_stride;
+    const float4 *ent = P.stencil_f + p * P.ent_stride;   // float offsets: no conversions
     const T *mass = static_cast<const T *>(P.mass);
     const T *mp = static_cast<const T *>(P.mp);
     for (;;) {
@@ -703,8 +704,8 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
             for (int e0 = 0; e0 < P.n_far; e0 += kChunk) {
                 const int e1 = min(e0 + kChunk, P.n_far);
                 for (int e = e0; e < e1; ++e) {
-                    const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + e));
-                    const T wv = W[base + E.w];
+                    const float4 E = __ldg(ent + e);
+                    const T wv = W[base + __float_as_int(E.w)];
                     const int idx = window_decode<T>(wv);
                     Src<T> src;
                     if (idx >= 0 && idx < P.mp_limit) {
@@ -724,8 +725,8 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
             for (int e0 = P.n_far; e0 < P.n_far + P.n_near; e0 += kChunk) {
                 const int e1 = min(e0 + kChunk, P.n_far + P.n_near);
                 for (int e = e0; e < e1; ++e) {
-                    const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + e));
-                    const T wv = W[base + E.w];
+                    const float4 E = __ldg(ent + e);
+                    const T wv = W[base + __float_as_int(E.w)];
                     Src<T> src;
                     src.m0 = window_decode<T>(wv) >= 0 ? T(0) : wv;
                     acc_mp<T, false>(dA[0] - T(E.x), dA[1] - T(E.y), dA[2] - T(E.z), src, a3A,
@@ -1129,6 +1130,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     P.info = d.info;
     P.nbr = d.nbr;
     P.stencil = d.stencil;
+    P.stencil_f = reinterpret_cast<const float4 *>(d.stencil_f);
     P.coef = kF32<T> ? static_cast<const void *>(d.coef32)
              : kDF<T> ? static_cast<const void *>(d.coefdf)
                       : static_cast<const void *>(d.coef64);

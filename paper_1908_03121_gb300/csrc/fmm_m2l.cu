@@ -578,18 +578,27 @@ __device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const 
         L.part[1 + i] = add_u(L.part[1 + i], renorm(b));
     }
     if constexpr (kF32<T>) {
-        // orders 2-3 (12 components) in pairs on the paired FP32 pipe
-        // (fma.rn.f32x2: each half rounds as fmaf does)
+        // orders 2-3 (12 components): the pairs in which the derivative
+        // tensors come out of DTraceless<float> (xx yy | xz yz of D2, xxx yyy
+        // | xxz yyz of D3) on the paired FP32 pipe (fma.rn.f32x2: each half
+        // rounds as fmaf does), the other four scalar
+        constexpr int pair_a[4] = {4, 7, 9, 11}, pair_b[4] = {5, 8, 14, 15};
+        const float dv[16] = {0.f, 0.f, 0.f, 0.f, D.D2[0], D.D2[1], D.D2[2], D.D2[3],
+                              D.D2[4], D.D3[0], D.D3[1], D.D3[2], D.D3[3], D.D3[4],
+                              D.D3[5], D.D3[6]};
         const float2 nm2 = make_float2(nm0, nm0);
-        const float d23[12] = {D.D2[0], D.D2[1], D.D2[2], D.D2[3], D.D2[4], D.D3[0],
-                               D.D3[1], D.D3[2], D.D3[3], D.D3[4], D.D3[5], D.D3[6]};
 #pragma unroll
-        for (int k = 0; k < 12; k += 2) {
-            const float2 r = __ffma2_rn(nm2, make_float2(d23[k], d23[k + 1]),
-                                        make_float2(L.part[4 + k], L.part[5 + k]));
-            L.part[4 + k] = r.x;
-            L.part[5 + k] = r.y;
+        for (int j = 0; j < 4; ++j) {
+            const int a = pair_a[j], b = pair_b[j];
+            const float2 r = __ffma2_rn(nm2, make_float2(dv[a], dv[b]),
+                                        make_float2(L.part[a], L.part[b]));
+            L.part[a] = r.x;
+            L.part[b] = r.y;
         }
+        L.part[6] = fmaf(nm0, dv[6], L.part[6]);
+        L.part[10] = fmaf(nm0, dv[10], L.part[10]);
+        L.part[12] = fmaf(nm0, dv[12], L.part[12]);
+        L.part[13] = fmaf(nm0, dv[13], L.part[13]);
     } else {
 #pragma unroll
         for (int k = 0; k < 5; ++k) L.part[4 + k] = fmadd_u(nm0, D.D2[k], L.part[4 + k]);

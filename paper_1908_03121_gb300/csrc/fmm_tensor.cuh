@@ -214,6 +214,87 @@ struct DTraceless {
     }
 };
 
+// float: the same values, bit for bit, with the independent products that
+// share a form issued in pairs on the paired FP32 pipe (mul/fma.rn.f32x2,
+// each half rounding as the scalar instruction does).  The natural pairs are
+// the (x, y) and (xz, yz) products of one radial factor; the radial factors
+// themselves are scalar and duplicated into pairs where needed.
+template <>
+struct DTraceless<float> {
+    float D0, D1[3];
+    float D2[5];             // xx yy xy xz yz
+    float D3[9];             // xxx xxy xxz xyy xyz yyy yyz | xzz yzz
+    float U[3][7];           // D4 slices for the B3 basis
+
+    template <bool WITH_D4>
+    __device__ __forceinline__ void eval(float x, float y, float z)
+    {
+        const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+        const float ri = rsqrtf(r2);
+        const float ri2 = ri * ri;
+        const float d1 = -ri * ri2;
+        const float d2 = d1 * (-3.f * ri2);
+        const float d3 = d2 * (-5.f * ri2);
+        const float t2 = 3.f * d2;
+        const float2 d1p = make_float2(d1, d1), d2p = make_float2(d2, d2);
+        const float2 rxy = make_float2(x, y);
+        const float2 sq = __fmul2_rn(rxy, rxy);                       // xx, yy
+        const float2 xzyz = __fmul2_rn(rxy, make_float2(z, z));       // xz, yz
+        const float xy = x * y;
+        D0 = ri;
+        const float2 d1xy = __fmul2_rn(d1p, rxy);
+        D1[0] = d1xy.x; D1[1] = d1xy.y; D1[2] = d1 * z;
+        const float2 d2a = __ffma2_rn(d2p, sq, d1p);                   // D2 xx, yy
+        const float2 d2b = __fmul2_rn(d2p, xzyz);                      // D2 xz, yz
+        D2[0] = d2a.x; D2[1] = d2a.y; D2[2] = d2 * xy; D2[3] = d2b.x; D2[4] = d2b.y;
+        const float2 d3xy = __fmul2_rn(make_float2(d3, d3), rxy);     // d3 x, d3 y
+        const float2 t2xy = __fmul2_rn(make_float2(t2, t2), rxy);     // t2 x, t2 y
+        const float2 d2xy = __fmul2_rn(d2p, rxy);                      // d2 x, d2 y
+        const float d2z = d2 * z;
+        const float2 d3a = __ffma2_rn(d3xy, sq, t2xy);                 // xxx, yyy
+        const float2 d3b = __ffma2_rn(d3xy, xzyz, make_float2(d2z, d2z));   // xxz, yyz
+        D3[0] = d3a.x;
+        D3[1] = fmaf(d3xy.x, xy, d2xy.y);                              // xxy
+        D3[2] = d3b.x;
+        D3[3] = fmaf(d3xy.x, sq.y, d2xy.x);                            // xyy
+        D3[4] = d3xy.x * xzyz.y;                                       // xyz
+        D3[5] = d3a.y;
+        D3[6] = d3b.y;
+        D3[7] = -(D3[0] + D3[3]);                                      // xzz
+        D3[8] = -(D3[1] + D3[5]);                                      // yzz
+        if (WITH_D4) {
+            const float d4 = d3 * (-7.f * ri2);
+            const float t3 = 3.f * d3, t6 = 6.f * d3;
+            const float2 d4sq = __fmul2_rn(make_float2(d4, d4), sq);   // d4 xx, d4 yy
+            const float d4xy = d4 * xy;
+            const float2 q4 = __ffma2_rn(d4sq, sq, __ffma2_rn(make_float2(t6, t6), sq,
+                                                              make_float2(t2, t2)));   // xxxx, yyyy
+            const float2 z4 = __ffma2_rn(d4sq, xzyz, __fmul2_rn(make_float2(t3, t3), xzyz));
+                                                                       // xxxz, yyyz
+            const float t3xy = t3 * xy;
+            const float xxxx = q4.x, yyyy = q4.y, xxxz = z4.x, yyyz = z4.y;
+            const float xxxy = fmaf(d4sq.x, xy, t3xy);
+            const float xxyy = fmaf(d4sq.x, sq.y, fmaf(d3, sq.x + sq.y, d2));
+            const float xxyz = fmaf(d4sq.x, xzyz.y, d3 * xzyz.y);
+            const float xyyy = fmaf(d4xy, sq.y, t3xy);
+            const float xyyz = fmaf(d4xy, xzyz.y, d3 * xzyz.x);
+            const float xxzz = -(xxxx + xxyy), xyzz = -(xxxy + xyyy), yyzz = -(xxyy + yyyy);
+            U[0][0] = xxxx; U[0][1] = xxxy; U[0][2] = xxxz; U[0][3] = xxyy;
+            U[0][4] = xxyz; U[0][5] = xyyy; U[0][6] = xyyz;
+            U[1][0] = xxxy; U[1][1] = xxyy; U[1][2] = xxyz; U[1][3] = xyyy;
+            U[1][4] = xyyz; U[1][5] = yyyy; U[1][6] = yyyz;
+            U[2][0] = xxxz; U[2][1] = xxyz; U[2][2] = xxzz; U[2][3] = xyyz;
+            U[2][4] = xyzz; U[2][5] = yyyz; U[2][6] = yyzz;
+        }
+    }
+
+    __device__ __forceinline__ float d3slice(int i, int k) const
+    {
+        constexpr int idx[3][5] = {{0, 3, 1, 2, 4}, {1, 5, 3, 4, 6}, {2, 6, 4, 7, 8}};
+        return D3[idx[i][k]];
+    }
+};
+
 // cell (x,y,z) of a node -> parity-split position
 __host__ __device__ __forceinline__ int parity_index(int x, int y, int z)
 {

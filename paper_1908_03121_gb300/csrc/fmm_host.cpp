@@ -916,9 +916,13 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
     // the multipole targets' leaf sources read the leaf masses packed on aux
     FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[4], 0), "cudaStreamWaitEvent");
     FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_ROOT | M2L_MP), "m2l launch");
-    // aux: monopole<-multipole once the refined sources are packed (it adds
-    // to what the monopole kernel stored, on the same stream)
-    FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[1], 0), "cudaStreamWaitEvent");
+    FMM_STEP_TRY(cudaEventRecord(ev[5], s), "cudaEventRecord");
+    // aux: monopole<-multipole (it adds to what the monopole kernel stored,
+    // on the same stream).  It needs only the packed refined sources, but it
+    // waits for the multipole kernel: both hold their SMs for their whole
+    // run, and the multipole kernel is on the critical path while this one
+    // is not; after it, it runs beside the latency-bound shifts below.
+    FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[5], 0), "cudaStreamWaitEvent");
     FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_MX), "m2l launch");
     // main: shifts of the refined nodes, root level first
     for (int lev = 1; lev <= t->max_level; ++lev)

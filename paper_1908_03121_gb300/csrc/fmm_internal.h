@@ -167,7 +167,7 @@ struct fmm_tree_s {
     mutable fmm::TimerState timer;
     // fmm_step's second stream and its fork/join events (device trees only)
     cudaStream_t aux = nullptr;
-    cudaEvent_t step_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t step_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace fmm {

@@ -774,8 +774,10 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     // shifts per level, every leaf's shift and forces in one launch
     int refined_levels = 0;
     for (int lev = 1; lev <= t->max_level; ++lev) refined_levels += P.refined_at[size_t(lev)].count > 0;
-    o->launches_fused = up + (m2l - 1) + (P.leaves.count > 0) + (P.refined.count > 0) +
-                        refined_levels + (P.leaves.count > 0) + 2;
+    // (the monopole<-multipole targets ride in the multipole launch)
+    const int mx_alone = (P.n_mx_targets > 0) && (P.work_mp.count == 0);
+    o->launches_fused = up + (m2l - 1) - (P.n_mx_targets > 0) + mx_alone + (P.leaves.count > 0) +
+                        (P.refined.count > 0) + refined_levels + (P.leaves.count > 0) + 2;
     if ((t->cfg.flags & FMM_FLAG_TIMING) && !t->host_only) {
         o->timing = 1;
         timing_fold(t);
@@ -907,23 +909,24 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
     FMM_STEP_TRY(launch_pack(t, M, com, a, PACK_LEAVES), "pack launch");
     FMM_STEP_TRY(cudaEventRecord(ev[4], a), "cudaEventRecord");
     FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_MONO), "m2l launch");
+    FMM_STEP_TRY(cudaEventRecord(ev[5], a), "cudaEventRecord");
     // main: M2M, refined sources, root and multipole targets
     for (int lev = t->max_level - 1; lev >= 1; --lev)
         if (P.refined_at[size_t(lev)].count)
             FMM_STEP_TRY(launch_m2m_level(t, lev, M, com, s), "m2m launch");
     FMM_STEP_TRY(launch_pack(t, M, com, s, PACK_REFINED), "pack launch");
     FMM_STEP_TRY(cudaEventRecord(ev[1], s), "cudaEventRecord");
-    // the multipole targets' leaf sources read the leaf masses packed on aux
-    FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[4], 0), "cudaStreamWaitEvent");
-    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_ROOT | M2L_MP), "m2l launch");
-    FMM_STEP_TRY(cudaEventRecord(ev[5], s), "cudaEventRecord");
-    // aux: monopole<-multipole (it adds to what the monopole kernel stored,
-    // on the same stream).  It needs only the packed refined sources, but it
-    // waits for the multipole kernel: both hold their SMs for their whole
-    // run, and the multipole kernel is on the critical path while this one
-    // is not; after it, it runs beside the latency-bound shifts below.
-    FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[5], 0), "cudaStreamWaitEvent");
-    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_MX), "m2l launch");
+    // the multipole targets' leaf sources read the leaf masses packed on aux;
+    // the same launch then takes the monopole<-multipole targets, which add
+    // to what the monopole kernel stored, so it also waits for that kernel
+    // (on cfg-size trees it has finished by then).  The monopole<-multipole
+    // work fills the multipole kernel's tail, where its last coarse items
+    // leave SMs idle; as a launch of its own it held its SMs for its whole
+    // run and delayed whichever of the multipole kernel and the shifts
+    // came second.
+    FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[5], 0), "cudaStreamWaitEvent");
+    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_ROOT | M2L_MP | M2L_MPX),
+                 "m2l launch");
     // main: shifts of the refined nodes, root level first
     for (int lev = 1; lev <= t->max_level; ++lev)
         FMM_STEP_TRY(launch_l2l_nodes(t, P.refined_at[size_t(lev)], L, L_comp, dL1, com, L64,

@@ -181,7 +181,10 @@ enum { PACK_ALL = 0, PACK_LEAVES = 1, PACK_REFINED = 2 };
 cudaError_t launch_pack(const fmm_tree_s *t, const double *M, const double *com,
                         cudaStream_t s, int which = PACK_ALL);
 // parts of the same-level pass (bits; M2L_ALL = all, counters reset first)
-enum { M2L_RESET = 1, M2L_ROOT = 2, M2L_MP = 4, M2L_MONO = 8, M2L_MX = 16, M2L_ALL = 31 };
+// M2L_MPX: the multipole launch also takes the monopole<-multipole targets
+// (after its own queue; the monopole kernel must have finished)
+enum { M2L_RESET = 1, M2L_ROOT = 2, M2L_MP = 4, M2L_MONO = 8, M2L_MX = 16, M2L_ALL = 31,
+       M2L_MPX = 32 };
 cudaError_t launch_m2l(const fmm_tree_s *t, void *L, float *Lc, double *dL1,
                        cudaStream_t s, int *n_launches, int parts = M2L_ALL);
 cudaError_t launch_l2l_level(const fmm_tree_s *t, int level, const void *L,

@@ -65,7 +65,7 @@ __device__ __forceinline__ T ldg_t(const T *p)
 
 constexpr int kThreads = 256;   // 8 warps = the 8 child parities
 constexpr int kChunk = 16;      // stencil entries per compensated chunk
-constexpr int Q_MP = 0, Q_MONO = 1;            // work-queue heads
+constexpr int Q_MP = 0, Q_MONO = 1, Q_MX = 2;   // work-queue heads (Q_MX: the fused launch)
 
 struct KParams {
     const NodeInfo *info;
@@ -80,6 +80,8 @@ struct KParams {
     int n_far, n_near;       // identical for every parity
     int ent_stride;          // entries reserved per parity
     const int4 *mx_targets;  // monopole<-multipole targets (node, cell, pair offset, count)
+    int32_t n_mx;            // monopole<-multipole targets the multipole launch takes (0: none)
+    int32_t *mx_counter;     // their queue head
     const int2 *mx_pairs;    // (packed-moment offset, stencil entry)
     int reach, py, pz, sub_stride;
     const void *mass;
@@ -667,6 +669,62 @@ __device__ __forceinline__ double acc_value(const SA &S, int i)
     return to_double(acc_hi(S, i)) + to_double(acc_lo(S, i));
 }
 
+// ------------------------------------------------- monopole<-multipole
+// One leaf target cell with refined sources (one lane): its own list of
+// (packed-moment offset, stencil entry) pairs, orders 0-1 and the correction
+// added to what the monopole kernel stored for the cell.
+template <typename T>
+__device__ __forceinline__ void mx_target(const KParams &P, int t)
+{
+    const T *mp = static_cast<const T *>(P.mp);
+    const int4 tg = __ldg(P.mx_targets + t);       // node, cell, pair offset, count
+    const int x = tg.y & 7, y = (tg.y >> 3) & 7, z = tg.y >> 6;
+    const int p = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+    const StencilEntry *ent = P.stencil + p * P.ent_stride;
+    Acc<T, 4> L;
+    Acc<T, 3> S;
+    L.zero();
+    S.zero();
+    int done = 0;
+    for (int k = 0; k < tg.w; ++k) {
+        const int2 pr = __ldg(P.mx_pairs + tg.z + k);
+        const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + pr.y));
+        Src<T> src;
+        load_source_at<T>(mp + pr.x, src);
+        acc_mx<T>(-T(E.x) - src.d[0], -T(E.y) - src.d[1], -T(E.z) - src.d[2], src, L, S);
+        if (++done == kChunk) {
+            L.flush();
+            S.flush();
+            done = 0;
+        }
+    }
+    L.flush();
+    S.flush();
+    const int node = tg.x, cell = tg.y;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const size_t idx = (size_t(node) * NCOMP + k) * NCELL + cell;
+        if constexpr (kF32<T>) {
+            float *Lh = static_cast<float *>(P.L);
+            float s, e;
+            two_sum(Lh[idx], L.hi[k], s, e);
+            const float lo = P.Lc[idx] + L.lo[k] + e;
+            const float s2 = s + lo;
+            Lh[idx] = s2;
+            P.Lc[idx] = lo - (s2 - s);
+        } else if constexpr (kDF<T>) {
+            float *Lh = static_cast<float *>(P.L);
+            const dfloat v = dfloat(Lh[idx], P.Lc[idx]) + L.part[k];
+            Lh[idx] = v.hi;
+            P.Lc[idx] = v.lo;
+        } else {
+            static_cast<double *>(P.L)[idx] += L.hi[k];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(S, i);
+}
+
 // ------------------------------------------------------------ mp_kernel
 template <typename T>
 // float: three CTAs per SM (at most 85 registers): the compensation pairs,
@@ -751,6 +809,20 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
                 P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(S, i);
         }
         __syncthreads();
+    }
+    // fmm_step also hands this launch the monopole<-multipole targets: once
+    // the multipole queue is empty, each warp pulls 32 of them at a time
+    // from their own queue, which fills the tail that the coarse multipole
+    // items leave (the monopole kernel, whose results they add to, has
+    // finished before this launch)
+    if (P.n_mx > 0) {
+        for (;;) {
+            int w = 0;
+            if (lane == 0) w = atomicAdd(P.mx_counter, 1);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (w * 32 >= P.n_mx) break;
+            if (w * 32 + lane < P.n_mx) mx_target<T>(P, w * 32 + lane);
+        }
     }
 }
 
@@ -918,57 +990,10 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
 {
     const int lane = threadIdx.x & 31;
     const int warps = int(gridDim.x) * (kThreads / 32);
-    const T *mp = static_cast<const T *>(P.mp);
     for (int w = int(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); w * 32 < P.n_items;
          w += warps) {
         const int t = w * 32 + lane;
-        if (t >= P.n_items) continue;
-        const int4 tg = __ldg(P.mx_targets + t);       // node, cell, pair offset, count
-        const int x = tg.y & 7, y = (tg.y >> 3) & 7, z = tg.y >> 6;
-        const int p = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
-        const StencilEntry *ent = P.stencil + p * P.ent_stride;
-        Acc<T, 4> L;
-        Acc<T, 3> S;
-        L.zero();
-        S.zero();
-        int done = 0;
-        for (int k = 0; k < tg.w; ++k) {
-            const int2 pr = __ldg(P.mx_pairs + tg.z + k);
-            const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + pr.y));
-            Src<T> src;
-            load_source_at<T>(mp + pr.x, src);
-            acc_mx<T>(-T(E.x) - src.d[0], -T(E.y) - src.d[1], -T(E.z) - src.d[2], src, L, S);
-            if (++done == kChunk) {
-                L.flush();
-                S.flush();
-                done = 0;
-            }
-        }
-        L.flush();
-        S.flush();
-        const int node = tg.x, cell = tg.y;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const size_t idx = (size_t(node) * NCOMP + k) * NCELL + cell;
-            if constexpr (kF32<T>) {
-                float *Lh = static_cast<float *>(P.L);
-                float s, e;
-                two_sum(Lh[idx], L.hi[k], s, e);
-                const float lo = P.Lc[idx] + L.lo[k] + e;
-                const float s2 = s + lo;
-                Lh[idx] = s2;
-                P.Lc[idx] = lo - (s2 - s);
-            } else if constexpr (kDF<T>) {
-                float *Lh = static_cast<float *>(P.L);
-                const dfloat v = dfloat(Lh[idx], P.Lc[idx]) + L.part[k];
-                Lh[idx] = v.hi;
-                P.Lc[idx] = v.lo;
-            } else {
-                static_cast<double *>(P.L)[idx] += L.hi[k];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(S, i);
+        if (t < P.n_items) mx_target<T>(P, t);
     }
 }
 
@@ -1173,6 +1198,9 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     }
     const int sms = sm_count_of_current_device();
     int nl = 0;
+    // M2L_MPX: the monopole<-multipole targets ride in the multipole launch
+    // when there is one, else they get their own
+    const bool mx_in_mp = (parts & M2L_MPX) && (parts & M2L_MP) && Pl.work_mp.count > 0;
     if ((parts & M2L_ROOT) && Pl.roots.count) {
         KParams R = P;
         R.list = d.lists + Pl.roots.off;
@@ -1188,6 +1216,10 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         K.list = d.lists + Pl.work_mp.off;
         K.n_items = int32_t(Pl.work_mp.count);
         K.counter = d.counters + Q_MP;
+        if (mx_in_mp) {
+            K.n_mx = int32_t(Pl.n_mx_targets);
+            K.mx_counter = d.counters + Q_MX;
+        }
         int g = persistent_grid(mp_kernel<T>, mp_bytes, Pl.work_mp.count, sms, cap);
         timing_begin(t, FMM_K_MULTIPOLE, s);
         mp_kernel<T><<<g, kThreads, mp_bytes, s>>>(K);
@@ -1214,7 +1246,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         ++nl;
         if (e != cudaSuccess) return e;
     }
-    if ((parts & M2L_MX) && Pl.n_mx_targets) {
+    if ((parts & (M2L_MX | M2L_MPX)) && !mx_in_mp && Pl.n_mx_targets) {
         KParams K = P;
         K.n_items = int32_t(Pl.n_mx_targets);
         const int64_t warps = (K.n_items + 31) / 32;

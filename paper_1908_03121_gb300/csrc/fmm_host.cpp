@@ -871,11 +871,12 @@ int fmm_forces(fmm_tree_t t, const double *L64, const double *dL1_acc, const dou
 
 // The whole step as one call, with the passes' independent work overlapped on
 // two streams: the monopole<-monopole kernel needs only leaf masses, so it
-// runs beside the upward pass of the refined levels; the refined levels'
-// shifts need only the multipole-target results, so they run beside the
-// monopole<-multipole kernel; every leaf's shift and forces (all levels, one
-// fused launch) follow both.  The same arithmetic, hence the same results, as
-// fmm_upward, fmm_m2l, fmm_downward and fmm_forces in sequence.
+// runs beside the upward pass of the refined levels; the multipole launch
+// also takes the monopole<-multipole targets once its own queue is empty,
+// with the roots beside it on the second stream; then the refined levels'
+// shifts, and every leaf's shift and forces (all levels, one fused launch).
+// The same arithmetic, hence the same results, as fmm_upward, fmm_m2l,
+// fmm_downward and fmm_forces in sequence.
 int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, float *L_comp,
              double *dL1, double *L64, double *dL1_acc, double *phi, double *g, double *totals,
              fmm_stream_t stream)
@@ -904,13 +905,14 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
     FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_RESET), "queue reset");
     FMM_STEP_TRY(launch_p2m(t, rho, M, s), "p2m launch");
     FMM_STEP_TRY(cudaEventRecord(ev[0], s), "cudaEventRecord");
+    // Events: 0 P2M done, 1 refined sources packed, 2 refined shifts done,
+    // 3 second stream done, 4 roots done, 5 monopole kernel done.
     // aux: leaf masses, monopole<-monopole
     FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[0], 0), "cudaStreamWaitEvent");
     FMM_STEP_TRY(launch_pack(t, M, com, a, PACK_LEAVES), "pack launch");
-    FMM_STEP_TRY(cudaEventRecord(ev[4], a), "cudaEventRecord");
     FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_MONO), "m2l launch");
     FMM_STEP_TRY(cudaEventRecord(ev[5], a), "cudaEventRecord");
-    // main: M2M, refined sources, root and multipole targets
+    // main: M2M, refined sources, multipole targets
     for (int lev = t->max_level - 1; lev >= 1; --lev)
         if (P.refined_at[size_t(lev)].count)
             FMM_STEP_TRY(launch_m2m_level(t, lev, M, com, s), "m2m launch");
@@ -925,8 +927,13 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
     // run and delayed whichever of the multipole kernel and the shifts
     // came second.
     FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[5], 0), "cudaStreamWaitEvent");
-    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_ROOT | M2L_MP | M2L_MPX),
-                 "m2l launch");
+    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_MP | M2L_MPX), "m2l launch");
+    // aux: the roots (16 CTAs per root) beside the multipole launch rather
+    // than before it on the main stream, where the GPU idled around them
+    FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[1], 0), "cudaStreamWaitEvent");
+    FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_ROOT), "m2l launch");
+    FMM_STEP_TRY(cudaEventRecord(ev[4], a), "cudaEventRecord");
+    FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[4], 0), "cudaStreamWaitEvent");
     // main: shifts of the refined nodes, root level first
     for (int lev = 1; lev <= t->max_level; ++lev)
         FMM_STEP_TRY(launch_l2l_nodes(t, P.refined_at[size_t(lev)], L, L_comp, dL1, com, L64,

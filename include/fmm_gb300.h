@@ -272,13 +272,14 @@ int fmm_get_tuning(fmm_tree_t tree, fmm_tuning *tuning);
 /*
  * The whole step in one call: fmm_upward, fmm_m2l, fmm_downward and
  * fmm_forces on the arguments they take (rho as for fmm_upward and
- * fmm_forces), with the same kernels, arithmetic and results.  The passes'
- * independent work is overlapped: the monopole<-monopole kernel (it needs
- * only leaf masses) runs beside the upward pass of the refined levels, the
- * refined levels' downward shifts beside the monopole<-multipole kernel, on a
- * second stream that the tree owns and that forks from and joins back into
- * `stream` through events, so the call can be captured into a CUDA graph;
- * every leaf's shift and forces run as one fused pass.
+ * fmm_forces), with the same arithmetic and results.  The passes'
+ * independent work is overlapped on a second stream that the tree owns and
+ * that forks from and joins back into `stream` through events, so the call
+ * can be captured into a CUDA graph: the monopole<-monopole kernel (it needs
+ * only leaf masses) runs beside the upward pass of the refined levels, and
+ * the roots beside the multipole kernel.  The multipole launch also takes
+ * the monopole<-multipole targets once its own queue is empty, and every
+ * leaf's shift and forces run as one fused pass.
  * With FMM_FLAG_TIMING the four passes run in sequence on `stream` instead.
  * Errors: as the four calls.
  */

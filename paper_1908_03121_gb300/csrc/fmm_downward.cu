@@ -429,18 +429,38 @@ struct ForceColumn {
     }
 
     // the node's fixed-order block sums into its partials row
+    // The node's six FP64 sums over its 64 columns, in a fixed order: eight
+    // threads per value add eight columns each, then six threads add the
+    // eight partial sums.  That is 63 adds per value, where a shuffle tree
+    // has every lane of both warps add at each of its five levels (five
+    // times the FP64 operations, on the pipe that bounds this pass).
     __device__ __forceinline__ void finish(int row, double *__restrict__ partials)
     {
-        __shared__ double sh[kForceThreads / 32][6];
+        __shared__ double sh[6][kForceThreads];
+        __shared__ double sh8[6][8];
         __shared__ float shf[kForceThreads / 32][2];
         const double S0 = fma(h, T[0], Z0 * F[0]), S1 = fma(h, T[1], Z0 * F[1]);
-        double v[6] = {F[0], F[1], F[2], fma(X1, F[2], -S1), fma(-X0, F[2], S0),
-                       fma(X0, F[1], -X1 * F[0])};
+        const double v[6] = {F[0], F[1], F[2], fma(X1, F[2], -S1), fma(-X0, F[2], S0),
+                             fma(X0, F[1], -X1 * F[0])};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = v[k];
         float vf[2] = {nf, nt};
-        block_sum<kForceThreads, double, 6>(v, sh);
-        block_sum<kForceThreads, float, 2>(vf, shf);
+        block_sum<kForceThreads, float, 2>(vf, shf);     // (its barrier publishes sh)
+        if (threadIdx.x < 48) {
+            const int k = threadIdx.x % 6, q = threadIdx.x / 6;
+            double t = sh[k][8 * q];
+#pragma unroll
+            for (int i = 1; i < 8; ++i) t += sh[k][8 * q + i];
+            sh8[k][q] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double t = sh8[threadIdx.x][0];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) t += sh8[threadIdx.x][q];
+            partials[size_t(row) * 8 + threadIdx.x] = t;
+        }
         if (threadIdx.x == 0) {
-            for (int k = 0; k < 6; ++k) partials[size_t(row) * 8 + k] = v[k];
             partials[size_t(row) * 8 + 6] = double(vf[0]);
             partials[size_t(row) * 8 + 7] = double(vf[1]);
         }

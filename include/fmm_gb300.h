@@ -184,7 +184,10 @@ int fmm_get_stats(fmm_tree_t tree, fmm_stats *out);
  * the cell centre (locally homogeneous density, Sec. 3 and Sec. 4.3).
  * Refined cells: mass, centre of mass and central moments of their eight
  * child cells, combined in FP64, deepest level first.
- *   rho: device double [n_leaf][512], read.
+ *   rho: double [n_leaf][512], read once, by one kernel: device memory,
+ *        or page-locked host memory mapped into the device's address space
+ *        (the kernel then reads it over the host link; the caller keeps it
+ *        unchanged until the pass has completed on `stream`).
  *   M:   device double [n_nodes][20][512], written.  For leaf nodes only
  *        component 0 (the cell mass) is written; their other components are
  *        zero by definition and are not touched.
@@ -279,7 +282,10 @@ int fmm_get_tuning(fmm_tree_t tree, fmm_tuning *tuning);
  * only leaf masses) runs beside the upward pass of the refined levels, and
  * the roots beside the multipole kernel.  The multipole launch also takes
  * the monopole<-multipole targets once its own queue is empty, and every
- * leaf's shift and forces run as one fused pass.
+ * leaf's shift and forces run as one fused pass, which takes the cell masses
+ * from M: the step reads rho in P2M only, so rho may be page-locked host
+ * memory as for fmm_upward (the whole input transfer then happens inside
+ * the P2M kernel, with no separate copy).
  * With FMM_FLAG_TIMING the four passes run in sequence on `stream` instead.
  * Errors: as the four calls.
  */

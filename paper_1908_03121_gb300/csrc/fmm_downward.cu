@@ -396,12 +396,12 @@ struct ForceColumn {
         hf = d2f_trunc(h);
     }
 
-    // cell z of the column: phi = L0, g = -(L1 + dL1), and its terms of the sums
-    __device__ __forceinline__ void cell(int row, int c, int z, double rho_c, double L0,
+    // cell z of the column, of mass m: phi = L0, g = -(L1 + dL1), and its
+    // terms of the sums
+    __device__ __forceinline__ void cell(int row, int c, int z, double m, double L0,
                                          const double L1[3], const double acc[3],
                                          double *__restrict__ phi, double *__restrict__ g)
     {
-        const double m = rho_c * h3;
         phi[size_t(row) * NCELL + c] = L0;
         double gv[3];
 #pragma unroll
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
             L1[a] = L64[(size_t(node) * NCOMP + 1 + a) * NCELL + c];
             acc[a] = dacc[(size_t(node) * 3 + a) * NCELL + c];
         }
-        col.cell(row, c, z, rho[size_t(row) * NCELL + c], L64[(size_t(node) * NCOMP) * NCELL + c],
+        col.cell(row, c, z, rho[size_t(row) * NCELL + c] * col.h3, L64[(size_t(node) * NCOMP) * NCELL + c],
                  L1, acc, phi, g);
     }
     col.finish(row, partials);
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kForceThreads) leaf_finish_kernel(
     const double *__restrict__ levels, const dfloat *__restrict__ levels_df,
     const void *__restrict__ Lv, const float *__restrict__ Lc, const double *dL1,
     const double *__restrict__ com, double *__restrict__ L64, double *dacc, float *down,
-    const double *__restrict__ rho, double *__restrict__ phi, double *__restrict__ g,
+    const double *__restrict__ M, double *__restrict__ phi, double *__restrict__ g,
     double *__restrict__ partials, double lo_x, double lo_y, double lo_z, double box_size)
 {
     const int node = leaves[blockIdx.x];
@@ -515,7 +515,10 @@ __global__ void __launch_bounds__(kForceThreads) leaf_finish_kernel(
         double out[20], corr[3];
         l2l_cell<MODE, 1>(info, ni, node, c, levels, levels_df, Lv, Lc, dL1, com, L64, dacc, down,
                           lo_x, lo_y, lo_z, out, corr);
-        col.cell(row, c, z, rho[size_t(row) * NCELL + c], out[0], out + 1, corr, phi, g);
+        // the cell mass as P2M left it in M (rho h^3, the same product): the
+        // step reads the density in P2M only, so it may sit in pinned host
+        // memory
+        col.cell(row, c, z, M[(size_t(node) * NCOMP) * NCELL + c], out[0], out + 1, corr, phi, g);
     }
     col.finish(row, partials);
 }
@@ -588,7 +591,7 @@ cudaError_t launch_l2l_nodes(const fmm_tree_s *t, const ListRange &r, const void
 
 cudaError_t launch_leaf_finish(const fmm_tree_s *t, const void *L, const float *Lc,
                                const double *dL1, const double *com, double *L64, double *dacc,
-                               const double *rho, double *phi, double *g, cudaStream_t s)
+                               const double *M, double *phi, double *g, cudaStream_t s)
 {
     const ListRange &r = t->plan.leaves;
     if (r.count == 0) return cudaSuccess;
@@ -598,15 +601,15 @@ cudaError_t launch_leaf_finish(const fmm_tree_s *t, const void *L, const float *
     const unsigned grid = unsigned(r.count);
     if (c.precision == FMM_MIXED)
         leaf_finish_kernel<FMM_MIXED><<<grid, kForceThreads, 0, s>>>(
-            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, t->dev.down, rho,
+            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, t->dev.down, M,
             phi, g, t->dev.partials, c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
     else if (c.precision == FMM_DFLOAT)
         leaf_finish_kernel<FMM_DFLOAT><<<grid, kForceThreads, 0, s>>>(
-            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, t->dev.down, rho,
+            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, t->dev.down, M,
             phi, g, t->dev.partials, c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
     else
         leaf_finish_kernel<FMM_FP64><<<grid, kForceThreads, 0, s>>>(
-            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, nullptr, rho, phi,
+            t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, nullptr, M, phi,
             g, t->dev.partials, c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
     return cudaGetLastError();
 }

@@ -942,7 +942,7 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
     // aux: every leaf's shift and forces in one pass (the shifted expansion
     // feeds the forces from registers), the sums; join
     FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[2], 0), "cudaStreamWaitEvent");
-    FMM_STEP_TRY(launch_leaf_finish(t, L, L_comp, dL1, com, L64, dL1_acc, rho, phi, g, a),
+    FMM_STEP_TRY(launch_leaf_finish(t, L, L_comp, dL1, com, L64, dL1_acc, M, phi, g, a),
                  "leaf launch");
     FMM_STEP_TRY(launch_force_sums(t, totals, a), "reduce launch");
     FMM_STEP_TRY(cudaEventRecord(ev[3], a), "cudaEventRecord");

@@ -195,7 +195,7 @@ cudaError_t launch_l2l_nodes(const fmm_tree_s *t, const ListRange &r, const void
                              double *L64, double *dacc, cudaStream_t s);
 cudaError_t launch_leaf_finish(const fmm_tree_s *t, const void *L, const float *Lc,
                                const double *dL1, const double *com, double *L64, double *dacc,
-                               const double *rho, double *phi, double *g, cudaStream_t s);
+                               const double *M, double *phi, double *g, cudaStream_t s);
 cudaError_t launch_force_sums(const fmm_tree_s *t, double *totals, cudaStream_t s);
 cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *dacc,
                           const double *rho, double *phi, double *g, double *totals,

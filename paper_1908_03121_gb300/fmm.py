@@ -333,17 +333,20 @@ class Solver:
         return {k: (st["kernel_ms"][i], st["kernel_launches"][i])
                 for i, k in enumerate(KERNEL_SLOTS)}
 
-    def capture(self):
-        """Record step() on self.rho into a CUDA graph (call once, then replay)."""
+    def capture(self, rho=None):
+        """Record step() into a CUDA graph (call once, then replay).  rho:
+        self.rho by default, or a page-locked host tensor that the step's P2M
+        kernel then reads directly every replay (the graph keeps its
+        address)."""
         import torch
-        self.step()                       # warm-up outside capture
+        self.step(rho)                    # warm-up outside capture
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             with torch.cuda.graph(g, stream=s):
-                self.step()
+                self.step(rho)
         torch.cuda.current_stream().wait_stream(s)
         self.graph = g
         return g

@@ -184,11 +184,11 @@ int fmm_get_stats(fmm_tree_t tree, fmm_stats *out);
  * the cell centre (locally homogeneous density, Sec. 3 and Sec. 4.3).
  * Refined cells: mass, centre of mass and central moments of their eight
  * child cells, combined in FP64, deepest level first.
- *   rho: double [n_leaf][512], read once, by one kernel: device memory,
- *        or page-locked host memory mapped into the device's address space
- *        (the kernel then reads it over the host link; the caller keeps it
- *        unchanged until the pass has completed on `stream`).
- *   M:   device double [n_nodes][20][512], written.  For leaf nodes only
+ *   rho: double [n_leaf][512], 16-byte aligned, read once, by one kernel:
+ *        device memory, or page-locked host memory mapped into the device's
+ *        address space (the kernel then reads it over the host link; the
+ *        caller keeps it unchanged until the pass has completed on `stream`).
+ *   M:   device double [n_nodes][20][512], 16-byte aligned, written.  For leaf nodes only
  *        component 0 (the cell mass) is written; their other components are
  *        zero by definition and are not touched.
  *   com: device double [n_nodes][3][512], written for refined nodes only

@@ -798,11 +798,16 @@ static int check_device_tree(fmm_tree_t t)
     return FMM_OK;
 }
 
+// P2M moves the density and the leaf masses as 16-byte vectors
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 int fmm_upward(fmm_tree_t t, const double *rho, double *M, double *com, fmm_stream_t stream)
 {
     int rc = check_device_tree(t);
     if (rc) return rc;
     if (!rho || !M || !com) return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(rho) || !aligned16(M))
+        return fail(FMM_ERR_INVALID_ARG, "rho and M must be 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     timing_begin(t, FMM_K_P2M, s);
     cudaError_t e = launch_p2m(t, rho, M, s);
@@ -885,6 +890,8 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
     if (rc) return rc;
     if (!rho || !M || !com || !L || !dL1 || !L64 || !dL1_acc || !phi || !g || !totals)
         return fail(FMM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(rho) || !aligned16(M))
+        return fail(FMM_ERR_INVALID_ARG, "rho and M must be 16-byte aligned");
     if (t->cfg.precision != FMM_FP64 && !L_comp)
         return fail(FMM_ERR_INVALID_ARG, "L_comp is required in FMM_MIXED and FMM_DFLOAT");
     if (t->cfg.flags & FMM_FLAG_TIMING) {

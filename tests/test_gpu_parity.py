@@ -305,6 +305,20 @@ def test_deterministic_and_graph_replay(precision):
     s.close()
 
 
+def test_misaligned_density_is_refused():
+    """P2M moves the density and the leaf masses as 16-byte vectors: a
+    misaligned pointer is an argument error, found before any launch."""
+    c, _ = oracle_solution("cfg1")
+    s = F.Solver(c["desc"], c["theta"], precision="mixed")
+    buf = torch.zeros(s.rho.numel() + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(F.FmmError):
+        F.fmm_upward(s.tree, buf[1:].data_ptr(), s.M, s.com)
+    with pytest.raises(F.FmmError):
+        s.step(buf[1:])
+    torch.cuda.synchronize()
+    s.close()
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_step_reads_pinned_host_density(precision):

@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(kForceThreads) leaf_finish_kernel(
     const NodeInfo ni = info[node];
     const int row = ni.leaf_row;
     ForceColumn col(ni, levels, box_size);
-#pragma unroll 1
+#pragma unroll
     for (int z = 0; z < 8; ++z) {
         const int c = threadIdx.x + 64 * z;
         double out[20], corr[3];

@@ -301,6 +301,7 @@ class Solver:
         self.totals = torch.zeros((nt, 8), **f64)
         self.rho = torch.zeros((nl, NCELL), **f64)
         self.graph = None
+        self._stream_state = None          # run_stream: second buffer, graphs, copy stream
 
     def upward(self, rho=None, stream=None):
         fmm_upward(self.tree, self.rho if rho is None else rho, self.M, self.com, stream)
@@ -354,8 +355,74 @@ class Solver:
     def replay(self):
         self.graph.replay()
 
+    def run_stream(self, inputs, on_result=None, before_step=None):
+        """Solve one step per page-locked host density in ``inputs`` (each
+        shaped and typed like ``self.rho``), back to back on the current
+        stream.  Step k + 1's density is copied to the device on a copy
+        stream while step k computes: two device density buffers, one
+        captured graph each.  Every step's totals are copied back to
+        page-locked host memory.  ``on_result(k, totals)`` runs on the host
+        for step k once step k + 1 has been enqueued, and for the last step
+        at the end.  ``before_step()``, if given, is called on the host
+        before each step is enqueued (work it enqueues on the current stream
+        runs before the step).  Returns the number of steps; afterwards
+        ``self.graph`` reads ``self.rho`` again."""
+        import torch
+        inputs = list(inputs)
+        for x in inputs:
+            if (x.device.type != "cpu" or not x.is_pinned() or x.dtype != self.rho.dtype
+                    or tuple(x.shape) != tuple(self.rho.shape)):
+                raise ValueError("run_stream inputs must be page-locked host tensors shaped "
+                                 "and typed like Solver.rho")
+        n = len(inputs)
+        if n == 0:
+            return 0
+        if self._stream_state is None:
+            rho_b = self.rho.clone()            # the warm-up step sees a valid density
+            g_b = self.capture(rho_b)
+            g_a = self.capture()
+            tot = [torch.empty(tuple(self.totals.shape), dtype=self.totals.dtype).pin_memory()
+                   for _ in range(2)]
+            self._stream_state = ((self.rho, rho_b), (g_a, g_b), torch.cuda.Stream(), tot)
+        bufs, graphs, cs, tot = self._stream_state
+        main = torch.cuda.current_stream()
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        done = [torch.cuda.Event(), torch.cuda.Event()]
+        cs.wait_stream(main)               # earlier work on the buffers is done first
+
+        def copy_in(k):
+            b = k % 2
+            with torch.cuda.stream(cs):
+                if k >= 2:
+                    cs.wait_event(done[b])     # step k - 2 has read this buffer
+                bufs[b].copy_(inputs[k], non_blocking=True)
+                copied[b].record(cs)
+
+        copy_in(0)
+        for k in range(n):
+            if k + 1 < n:
+                copy_in(k + 1)
+            b = k % 2
+            main.wait_event(copied[b])
+            if before_step is not None:
+                before_step()
+            graphs[b].replay()
+            tot[b].copy_(self.totals, non_blocking=True)
+            done[b].record(main)
+            if k >= 1:
+                done[(k - 1) % 2].synchronize()
+                if on_result is not None:
+                    on_result(k - 1, tot[(k - 1) % 2])
+        done[(n - 1) % 2].synchronize()
+        if on_result is not None:
+            on_result(n - 1, tot[(n - 1) % 2])
+        main.wait_stream(cs)
+        self.graph = graphs[0]
+        return n
+
     def close(self):
         self.graph = None
+        self._stream_state = None
         if self.tree is not None:
             self.tree.close()
             self.tree = None

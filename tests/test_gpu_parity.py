@@ -349,6 +349,44 @@ def test_step_reads_pinned_host_density(precision):
     s.close()
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_run_stream_matches_single_steps(precision):
+    """Solver.run_stream (next density copied during the current step, two
+    device buffers and graphs) gives, for every step, the same totals bits
+    as one step() per density, in order, and leaves the last step's field."""
+    c, _ = oracle_solution("adaptive4")
+    s = F.Solver(c["desc"], c["theta"], precision=precision, G=c["G"], box_lo=c["box_lo"],
+                 box_size=c["box_size"])
+    base = np.ascontiguousarray(c["rho"])
+    rhos = [torch.from_numpy(base * f).pin_memory() for f in (1.0, 1.5, 0.75, 2.0, 1.25)]
+    ref_tot, ref_g = [], None
+    for r in rhos:
+        s.rho.copy_(r.cuda())
+        s.step()
+        torch.cuda.synchronize()
+        ref_tot.append(host(s.totals).copy())
+        ref_g = host(s.g).copy()
+    s.rho.copy_(rhos[0].cuda())
+    got = {}
+    before = []
+    n = s.run_stream(rhos, lambda k, t: got.__setitem__(k, t.numpy().copy()),
+                     lambda: before.append(1))
+    assert n == len(rhos) and len(before) == len(rhos)
+    assert sorted(got) == list(range(len(rhos)))
+    for k in range(len(rhos)):
+        assert np.array_equal(got[k], ref_tot[k]), k
+    assert np.array_equal(host(s.g), ref_g)
+    # a second stream reuses the captured graphs; a wrong input is refused
+    got.clear()
+    s.run_stream(rhos[::-1], lambda k, t: got.__setitem__(k, t.numpy().copy()))
+    for k in range(len(rhos)):
+        assert np.array_equal(got[k], ref_tot[len(rhos) - 1 - k]), k
+    with pytest.raises(ValueError):
+        s.run_stream([torch.from_numpy(base)])           # not page-locked
+    s.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "dfloat"])
 @pytest.mark.parametrize("name", ["adaptive4", "batch3", "cfg2"])
 def test_fused_step_matches_passes(name, precision):

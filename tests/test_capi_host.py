@@ -14,7 +14,7 @@ import pytest
 import paper_1908_03121_gb300 as F
 from paper_1908_03121_gb300 import fmm as B
 from oracle import oracle as O
-from workloads import make_config, uniform_tree, adaptive_tree, leaf_nodes
+from workloads import make_config, uniform_tree, adaptive_tree, leaf_nodes, concat_trees
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "fmm_gb300.h")
@@ -57,11 +57,16 @@ def _adaptive(max_level=4, r=0.12):
 
 
 @pytest.mark.parametrize("case", ["cfg1", "cfg2", "adaptive4", "adaptive4_035", "adaptive4_055",
-                                  "adaptive4_030"])
+                                  "adaptive4_030", "single", "singles2"])
 def test_planner_counts_match_oracle(case):
     if case.startswith("cfg"):
         c = make_config(case)
         desc, rho, theta = c["desc"], c["rho"], c["theta"]
+    elif case.startswith("single"):
+        # one leaf sub-grid per tree: every pair on the root level, 512 x 511
+        desc = uniform_tree(1) if case == "single" else concat_trees([uniform_tree(1)] * 2)
+        rho = np.ones((len(desc), 512))
+        theta = 0.5
     else:
         desc = _adaptive()
         rho = np.ones((len(leaf_nodes(desc)), 512))
@@ -73,6 +78,8 @@ def test_planner_counts_match_oracle(case):
     _, _, counts = O.m2l(ot, M, com)
     assert list(t.stats["interactions"]) == list(counts)
     assert sum(t.stats["kernel_interactions"]) == sum(counts)
+    if case.startswith("single"):
+        assert list(counts) == [0, 0, 512 * 511 * len(desc), 0]
 
 
 def test_planner_stencil_sizes():

@@ -67,6 +67,13 @@ def small_case(name):
     rng = np.random.default_rng(7)
     if name == "adaptive4":
         desc = _adaptive_desc()
+    elif name == "single":
+        # degenerate: one leaf sub-grid, no refined node, no M2M level, every
+        # pair on the root level (the root kernel's leaf path only)
+        desc = uniform_tree(1)
+    elif name == "singles2":
+        # two independent single-sub-grid trees solved in one batch
+        desc = concat_trees([uniform_tree(1), uniform_tree(1)])
     elif name == "batch3":
         desc = concat_trees([uniform_tree(2), _adaptive_desc(4),
                              _adaptive_desc(3, centre=(0.7, 0.2, 0.5), r=0.2)])
@@ -78,7 +85,8 @@ def small_case(name):
                 box_lo=(0.0, 0.0, 0.0), box_size=1.0)
 
 
-SMALL = ["cfg1", "cfg2", "cfg2_t035", "cfg2_t055", "adaptive4", "adaptive4_t030", "batch3"]
+SMALL = ["cfg1", "cfg2", "cfg2_t035", "cfg2_t055", "adaptive4", "adaptive4_t030", "batch3",
+         "single", "singles2"]
 _ORACLE = {}
 
 
@@ -169,10 +177,11 @@ def test_upward_parity(name):
     M, com = host(s.M), host(s.com)
     refined = c["desc"][:, 5] >= 0
     assert rel_err(M[:, 0], ref["M"][:, 0]) <= FP64_TOL
-    assert rel_err(M[refined][:, 4:10], ref["M"][refined][:, 4:10]) <= FP64_TOL
-    assert rel_err(M[refined][:, 10:20], ref["M"][refined][:, 10:20]) <= FP64_TOL
-    assert np.all(M[refined][:, 1:4] == 0.0)
-    assert np.abs(com[refined] - ref["com"][refined]).max() <= FP64_TOL * 1.0
+    if refined.any():
+        assert rel_err(M[refined][:, 4:10], ref["M"][refined][:, 4:10]) <= FP64_TOL
+        assert rel_err(M[refined][:, 10:20], ref["M"][refined][:, 10:20]) <= FP64_TOL
+        assert np.all(M[refined][:, 1:4] == 0.0)
+        assert np.abs(com[refined] - ref["com"][refined]).max() <= FP64_TOL * 1.0
     s.close()
 
 

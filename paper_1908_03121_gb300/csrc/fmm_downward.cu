@@ -495,9 +495,12 @@ __global__ void __launch_bounds__(kForceThreads) forces_kernel(
 // fmm_step's last pass over the leaves: each leaf cell's shift (as
 // l2l_kernel) and its forces (as forces_kernel) in one kernel, the shifted
 // expansion going straight from registers into the force terms; the same
-// arithmetic, in the same order, as the two kernels
+// arithmetic, in the same order, as the two kernels.  At most 80 registers
+// (12 CTAs per SM, 24 warps, no spills): the pass is bound by the FP64 pipe,
+// and the extra warps keep more FP64 operations in flight than the 96
+// registers it would otherwise take
 template <int MODE>
-__global__ void __launch_bounds__(kForceThreads) leaf_finish_kernel(
+__global__ void __launch_bounds__(kForceThreads, 12) leaf_finish_kernel(
     const NodeInfo *__restrict__ info, const int32_t *__restrict__ leaves,
     const double *__restrict__ levels, const dfloat *__restrict__ levels_df,
     const void *__restrict__ Lv, const float *__restrict__ Lc, const double *dL1,

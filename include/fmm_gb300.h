@@ -273,6 +273,25 @@ int fmm_set_tuning(fmm_tree_t tree, const fmm_tuning *tuning);
 int fmm_get_tuning(fmm_tree_t tree, fmm_tuning *tuning);
 
 /*
+ * Input checks that the kernels make while they run (the calls stay
+ * asynchronous and capturable); each sets a bit of a status word that the
+ * tree keeps on the device until fmm_get_status clears it.
+ *   FMM_STATUS_BAD_DENSITY: a leaf density read by the upward pass's P2M
+ *     kernel (fmm_upward, fmm_step) was zero, negative or NaN.  The method
+ *     needs every cell mass positive: a refined cell's centre of mass, and
+ *     the correction's M_B^(0)/M_A^(0), divide by masses (Sec. 4.3 and the
+ *     angular-momentum correction).  Zero-density regions take a small
+ *     floor instead (the workloads use 1e-10).  The outputs of a step that
+ *     set the bit are undefined.
+ */
+enum { FMM_STATUS_BAD_DENSITY = 1 };
+
+/* Wait for all work on the device, then store the status word's bits in
+ * *status and, if `clear` is nonzero, clear them.  Not for use during stream
+ * capture.  Errors: FMM_ERR_INVALID_ARG (NULL, host-only tree), FMM_ERR_CUDA. */
+int fmm_get_status(fmm_tree_t tree, int32_t *status, int clear);
+
+/*
  * The whole step in one call: fmm_upward, fmm_m2l, fmm_downward and
  * fmm_forces on the arguments they take (rho as for fmm_upward and
  * fmm_forces), with the same arithmetic and results.  The passes'

@@ -569,6 +569,9 @@ static int upload_tree(fmm_tree_s *t)
         (e = cudaMalloc(reinterpret_cast<void **>(&d.chunk_sums), chunk_b)) != cudaSuccess)
         return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
     d.workspace_bytes = mass_b + mp_b + part_b + chunk_b + 64 * sizeof(int32_t);
+    // work queues and the status word start at zero
+    if ((e = cudaMemset(d.counters, 0, 64 * sizeof(int32_t))) != cudaSuccess)
+        return cuda_fail(e, "cudaMemset");
     if (t->cfg.precision != FMM_FP64) {
         size_t up_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 20 * NCELL * 2 * sizeof(float);
         if ((e = cudaMalloc(reinterpret_cast<void **>(&d.up), up_b)) != cudaSuccess)
@@ -983,6 +986,21 @@ int fmm_get_tuning(fmm_tree_t t, fmm_tuning *tu)
 {
     if (!t || !tu) return fail(FMM_ERR_INVALID_ARG, "NULL argument");
     *tu = t->tuning;
+    return FMM_OK;
+}
+
+int fmm_get_status(fmm_tree_t t, int32_t *status, int clear)
+{
+    int rc = check_device_tree(t);
+    if (rc) return rc;
+    if (!status) return fail(FMM_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    int32_t *word = t->dev.counters + kStatusSlot;
+    if ((e = cudaMemcpy(status, word, sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    if (clear && (e = cudaMemset(word, 0, sizeof(int32_t))) != cudaSuccess)
+        return cuda_fail(e, "cudaMemset");
     return FMM_OK;
 }
 

@@ -89,7 +89,7 @@ struct DeviceTables {
     void *mass = nullptr;            // [n][512] float or double
     void *mp = nullptr;              // [n_refined][4][512][4] packed sources: float,
                                      // double-float pairs or double
-    int32_t *counters = nullptr;     // work-queue heads
+    int32_t *counters = nullptr;     // work-queue heads; [kStatusSlot]: FMM_STATUS_* bits
     double *partials = nullptr;      // [n_leaf][8]
     double *chunk_sums = nullptr;    // [n_trees][reduce_chunks][8]
     float *up = nullptr;             // mixed, dfloat: [n_refined][20][512] double-float
@@ -102,6 +102,10 @@ struct DeviceTables {
 };
 
 // offsets of the node lists inside DeviceTables::lists
+// the slot of DeviceTables::counters that holds the status word (the work
+// queues use slots 0-3, which every step resets)
+constexpr int kStatusSlot = 8;
+
 struct ListRange {
     int64_t off = 0, count = 0;
 };

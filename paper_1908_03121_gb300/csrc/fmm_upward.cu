@@ -20,18 +20,22 @@ namespace {
 // P2M: leaf cells hold m = rho h^3 at their centre (point-mass reading of a
 // locally homogeneous density).  Two cells per thread, cells x-fastest, as
 // 16-byte loads and stores: the density may sit in pinned host memory, and
-// wider requests keep more of it in flight over the host link.
+// wider requests keep more of it in flight over the host link.  A density
+// that is not positive (zero, negative, NaN) sets FMM_STATUS_BAD_DENSITY in
+// the status word: the centres of mass divide by masses.
 __global__ void __launch_bounds__(NCELL / 2) p2m_kernel(const NodeInfo *__restrict__ info,
                                                         const int32_t *__restrict__ leaves,
                                                         const double *__restrict__ levels,
                                                         const double *__restrict__ rho,
-                                                        double *__restrict__ M)
+                                                        double *__restrict__ M,
+                                                        int32_t *__restrict__ status)
 {
     const int node = leaves[blockIdx.x];
     const NodeInfo ni = info[node];
     const double h3 = levels[ni.level * LEVEL_FIELDS + LV_H3];
     const int c = 2 * threadIdx.x;
     const double2 r = *reinterpret_cast<const double2 *>(rho + size_t(ni.leaf_row) * NCELL + c);
+    if (!(r.x > 0.0) || !(r.y > 0.0)) atomicOr(status, FMM_STATUS_BAD_DENSITY);
     *reinterpret_cast<double2 *>(M + (size_t(node) * NCOMP) * NCELL + c) =
         make_double2(r.x * h3, r.y * h3);
 }
@@ -424,7 +428,8 @@ cudaError_t launch_p2m(const fmm_tree_s *t, const double *rho, double *M, cudaSt
     // 16-byte accesses: rho and M must be 16-byte aligned (checked by the
     // public calls)
     p2m_kernel<<<unsigned(r.count), NCELL / 2, 0, s>>>(t->dev.info, t->dev.lists + r.off,
-                                                       t->dev.levels, rho, M);
+                                                       t->dev.levels, rho, M,
+                                                       t->dev.counters + kStatusSlot);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ FMM_FP64 = 0
 FMM_MIXED = 1
 FMM_DFLOAT = 2
 PRECISIONS = {"fp64": FMM_FP64, "mixed": FMM_MIXED, "dfloat": FMM_DFLOAT}
+FMM_STATUS_BAD_DENSITY = 1
 FMM_FLAG_HOST_ONLY = 1
 FMM_FLAG_TIMING = 2
 KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_multi", "l2l",
@@ -31,7 +32,8 @@ KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_mul
 
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
             "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_step", "fmm_set_tuning", "fmm_get_tuning",
-            "fmm_forces_noalloc", "fmm_check_conversions", "fmm_destroy_tree", "fmm_last_error")
+            "fmm_forces_noalloc", "fmm_check_conversions", "fmm_get_status", "fmm_destroy_tree",
+            "fmm_last_error")
 
 NCELL = 512
 NCOMP = 20
@@ -109,6 +111,7 @@ def load(build=True):
         lib.fmm_check_conversions.argtypes = [P, ctypes.c_int64, P, P]
         lib.fmm_set_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_get_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
+        lib.fmm_get_status.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
         lib.fmm_last_error.argtypes = []
         lib.fmm_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -262,6 +265,14 @@ def fmm_get_tuning(tree):
     return {"mono_subgrids": t.mono_subgrids, "ctas_per_sm": t.ctas_per_sm}
 
 
+def fmm_get_status(tree, clear=True):
+    """The tree's device status word (FMM_STATUS_* bits), read after the
+    device is idle; cleared afterwards unless ``clear`` is false."""
+    st = ctypes.c_int32(0)
+    _check(load().fmm_get_status(tree.handle, ctypes.byref(st), 1 if clear else 0))
+    return int(st.value)
+
+
 def fmm_last_error():
     return load().fmm_last_error().decode()
 
@@ -327,6 +338,11 @@ class Solver:
         self.m2l(stream)
         self.downward(stream)
         self.forces(rho, stream)
+
+    def status(self, clear=True):
+        """FMM_STATUS_* bits recorded by the kernels since the last clear
+        (FMM_STATUS_BAD_DENSITY: a leaf density was not positive)."""
+        return fmm_get_status(self.tree, clear)
 
     def kernel_times(self):
         """Per-kernel device ms since the last call (trees built with timing=True)."""

@@ -169,6 +169,11 @@ def test_rejects_null_and_host_only_calls():
     with pytest.raises(F.FmmError):
         F.fmm_m2l(t, 1, 1, 1, 1, 1, stream=0)
     assert "HOST_ONLY" in F.fmm_last_error()
+    # the status word lives on the device: a host-only tree has none
+    with pytest.raises(F.FmmError) as ei:
+        F.fmm_get_status(t)
+    assert ei.value.code == B.FMM_ERR_INVALID_ARG
+    assert B.load().fmm_get_status(t.handle, None, 0) == B.FMM_ERR_INVALID_ARG
 
 
 def test_batched_trees_plan_independently():

@@ -358,6 +358,31 @@ def test_step_reads_pinned_host_density(precision):
     s.close()
 
 
+@pytest.mark.parametrize("bad", [0.0, -1.0, float("nan")])
+def test_non_positive_density_sets_the_status_word(bad):
+    """A leaf density that is zero, negative or NaN sets
+    FMM_STATUS_BAD_DENSITY during the step (the calls stay asynchronous);
+    fmm_get_status reads and clears it, and a valid density leaves it clear."""
+    c, _ = oracle_solution("adaptive4")
+    s = F.Solver(c["desc"], c["theta"], precision="mixed", G=c["G"], box_lo=c["box_lo"],
+                 box_size=c["box_size"])
+    s.rho.copy_(dev(c["rho"]))
+    s.step()
+    assert s.status() == 0
+    s.rho[3, 77] = bad
+    s.step()
+    assert s.status(clear=False) == F.FMM_STATUS_BAD_DENSITY
+    assert s.status() == F.FMM_STATUS_BAD_DENSITY          # read, then cleared
+    assert s.status() == 0
+    s.upward()                                             # the pass call checks too
+    assert s.status() == F.FMM_STATUS_BAD_DENSITY
+    s.rho.copy_(dev(c["rho"]))
+    s.capture()
+    s.replay()
+    assert s.status() == 0
+    s.close()
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_run_stream_matches_single_steps(precision):

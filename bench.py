@@ -173,6 +173,26 @@ def profiled_traffic(kernel, workload):
     return float(val.group(1))
 
 
+# the same-level kernels and the interactions each evaluates (fmm_get_stats'
+# kernel_interactions order)
+M2L_KERNELS = (("multipole", "mp<-mp and mp<-mono (multipole kernel)"),
+               ("monopole", "mono<-mono (monopole kernel)"),
+               ("mono_multi", "mono<-mp (monopole<-multipole kernel)"),
+               ("root", "root level, every kind (root kernel)"))
+
+
+def m2l_rates_by_kernel(per_kernel, kernel_interactions):
+    """Interactions/s of each same-level kernel: the interactions it evaluates
+    per step over its measured ms per step (kernels that did not run are left
+    out)."""
+    rates = {}
+    for (key, label), n in zip(M2L_KERNELS, kernel_interactions):
+        ms = per_kernel.get(key, {}).get("ms_per_step", 0.0)
+        if ms > 0 and n > 0:
+            rates[label] = n / (ms / 1000.0)
+    return rates
+
+
 def workload_config(name, c, stats, sizes, precision):
     cells = int(sizes["n_leaf"]) * 512
     return {
@@ -474,6 +494,7 @@ def run_ours(args):
         result["m2l_interactions_per_s"] = interactions / (
             sum(per_kernel.get(k, {}).get("ms_per_step", 0.0)
                 for k in ("pack", "root", "multipole", "monopole", "mono_multi")) / 1000.0)
+        result["m2l_interactions_per_s_by_kernel"] = m2l_rates_by_kernel(per_kernel, kin)
 
         # FP64 GPU path on the same workload: rate and the mixed path's error
         if args.precision == "mixed" and args.fp64_steps > 0:

@@ -60,3 +60,14 @@ def test_reference_arm_other_ranks_exit_without_work():
                        timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_m2l_rates_by_kernel():
+    """Each same-level kernel's rate is its own interactions over its own
+    time; a kernel that did not run (no time or no work) is left out."""
+    per_kernel = {"multipole": {"ms_per_step": 2.0}, "monopole": {"ms_per_step": 0.5},
+                  "root": {"ms_per_step": 0.0}, "pack": {"ms_per_step": 9.0}}
+    rates = bench.m2l_rates_by_kernel(per_kernel, [1000, 3000, 40, 7])
+    assert rates == {"mp<-mp and mp<-mono (multipole kernel)": 1000 / 0.002,
+                     "mono<-mono (monopole kernel)": 3000 / 0.0005}
+    assert bench.m2l_rates_by_kernel({}, [1, 2, 3, 4]) == {}

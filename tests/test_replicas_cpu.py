@@ -71,3 +71,20 @@ def test_m2l_rates_by_kernel():
     assert rates == {"mp<-mp and mp<-mono (multipole kernel)": 1000 / 0.002,
                      "mono<-mono (monopole kernel)": 3000 / 0.0005}
     assert bench.m2l_rates_by_kernel({}, [1, 2, 3, 4]) == {}
+
+
+def test_per_cell_force_errors():
+    """Per-cell relative errors use vector norms, skip cells whose reference
+    field is below the floor, and take nearest-rank quantiles."""
+    import torch
+    g_ref = torch.zeros(1, 3, 512, dtype=torch.float64)
+    g_ref[0, 0, :] = 1.0                      # |g_ref| = 1 in every cell ...
+    g_ref[0, 0, 500:] = 1e-6                  # ... but 12 cells below the floor
+    g = g_ref.clone()
+    rel = torch.arange(500, dtype=torch.float64) * 1e-8   # 0, 1e-8, ..., 4.99e-6
+    g[0, 1, :500] = rel                       # an orthogonal error of that size
+    g[0, 2, 500:] = 1.0                       # huge errors where the floor excludes
+    out = bench.per_cell_force_errors(g, g_ref)
+    assert out["cells"] == 500
+    assert out["median"] == rel[249].item()
+    assert out["p99"] == rel[int(0.99 * 499)].item()

@@ -8,6 +8,7 @@ The shared library is compiled on first use with the system C compiler
 (``build()``), into ``oracle/_build/``.
 """
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -26,6 +27,12 @@ NCELL = 512
 NCOMP = 20
 
 
+def _compile(src, out):
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+
+
 def build(force=False):
     """Compile the oracle with gcc (OpenMP over target cells, IEEE FP64)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
@@ -33,31 +40,60 @@ def build(force=False):
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    _compile(_SRC, tmp)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def _bind(lib):
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    lib.oracle_upward.argtypes = [P, I64, P, P, P, P]
+    lib.oracle_m2l.argtypes = [P, I64, P, P, P, P, P, P, P, I64, ctypes.c_int, ctypes.c_int]
+    lib.oracle_sources.argtypes = [P, I64, P, I64, ctypes.c_int, P, P, I64]
+    lib.oracle_sources.restype = I64
+    lib.oracle_coverage.argtypes = [P, I64, P, P, P]
+    lib.oracle_downward.argtypes = [P, I64, P, P, P, P, P, P]
+    lib.oracle_forces.argtypes = [P, I64, P, P, P, P, P, P, P]
+    lib.oracle_pair_m2l.argtypes = [ctypes.c_double, P, P, P, P, ctypes.c_int, P, P]
+    lib.oracle_dtensors.argtypes = [P, P, P, P, P, P]
+    return lib
 
 
 def _lib():
     global _LIB
     with _LOCK:
         if _LIB is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            I64 = ctypes.c_int64
-            lib.oracle_upward.argtypes = [P, I64, P, P, P, P]
-            lib.oracle_m2l.argtypes = [P, I64, P, P, P, P, P, P, P, I64, ctypes.c_int, ctypes.c_int]
-            lib.oracle_sources.argtypes = [P, I64, P, I64, ctypes.c_int, P, P, I64]
-            lib.oracle_sources.restype = I64
-            lib.oracle_coverage.argtypes = [P, I64, P, P, P]
-            lib.oracle_downward.argtypes = [P, I64, P, P, P, P, P, P]
-            lib.oracle_forces.argtypes = [P, I64, P, P, P, P, P, P, P]
-            lib.oracle_pair_m2l.argtypes = [ctypes.c_double, P, P, P, P, ctypes.c_int, P, P]
-            lib.oracle_dtensors.argtypes = [P, P, P, P, P, P]
-            _LIB = lib
+            _LIB = _bind(ctypes.CDLL(build()))
         return _LIB
+
+
+def source_text():
+    """The oracle's C source (for tests that compile altered copies)."""
+    with open(_SRC) as f:
+        return f.read()
+
+
+@contextlib.contextmanager
+def variant(source, out_path):
+    """Compile `source` (a copy of the oracle's C source, e.g. with a planted
+    mistake) to `out_path` with the oracle's own flags, and route every call
+    of this module to it inside the block (the tests' check that each pin
+    catches the mistakes it is meant to)."""
+    global _LIB
+    src_path = out_path + ".c"
+    with open(src_path, "w") as f:
+        f.write(source)
+    _compile(src_path, out_path)
+    lib = _bind(ctypes.CDLL(out_path))
+    with _LOCK:
+        saved = _LIB
+        _LIB = lib
+    try:
+        yield
+    finally:
+        with _LOCK:
+            _LIB = saved
 
 
 def _p(a):

@@ -9,10 +9,29 @@ functions of ``test_oracle_pins`` unchanged, so this file checks that the
 pins discriminate.  It does not add pins of its own.  No GPU is involved.
 """
 
+import itertools
+import os
+
 import pytest
 
 import test_oracle_pins as pins
 from oracle import oracle as O
+
+# compiled copies go beside the oracle's own build (git-ignored), removed
+# afterwards.  Every case gets a path no earlier case used: the dynamic loader
+# hands back an already loaded library for a path it has seen.
+_WORK = os.path.join(os.path.dirname(O.build()), "mutants")
+_CASE = itertools.count()
+
+
+@pytest.fixture
+def work_so():
+    os.makedirs(_WORK, exist_ok=True)
+    path = os.path.join(_WORK, f"case_{os.getpid()}_{next(_CASE)}.so")
+    yield path
+    for f in (path, path + ".c"):
+        if os.path.exists(f):
+            os.remove(f)
 
 # (name, original text, mutated text, pins expected to catch it)
 MUTANTS = [
@@ -103,11 +122,11 @@ PINS = {
 
 
 @pytest.mark.parametrize("name,old,new,catchers", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_planted_mistake(name, old, new, catchers, tmp_path):
+def test_pins_catch_planted_mistake(name, old, new, catchers, work_so):
     src = O.source_text()
     assert src.count(old) == 1, f"mutation site not unique or missing: {name}"
     caught = []
-    with O.variant(src.replace(old, new), str(tmp_path / "oracle_mutant.so")):
+    with O.variant(src.replace(old, new), work_so):
         for pin in catchers:
             try:
                 PINS[pin]()
@@ -117,9 +136,9 @@ def test_pins_catch_planted_mistake(name, old, new, catchers, tmp_path):
     assert caught, f"no pin caught: {name}"
 
 
-def test_unaltered_copy_passes_every_pin(tmp_path):
+def test_unaltered_copy_passes_every_pin(work_so):
     """The harness itself: a copy compiled the same way passes all the pins
     used above, so a caught mutant is caught for its mistake."""
-    with O.variant(O.source_text(), str(tmp_path / "oracle_copy.so")):
+    with O.variant(O.source_text(), work_so):
         for pin in PINS.values():
             pin()

@@ -53,7 +53,8 @@ WORKLOAD_TEXT = {
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    # 300 steps time about 0.9 s of solve: enough for several clock samples
+    p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="cfg5")
@@ -90,7 +91,7 @@ class ClockSampler:
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "100"]
         if self.pci:
             cmd += ["-i", self.pci]
         try:
@@ -102,7 +103,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.1)                   # the sample in flight at the end
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)

@@ -184,3 +184,20 @@ def test_batched_trees_plan_independently():
     one = plan(c["desc"], 0.5)
     assert list(t.stats["interactions"]) == [3 * v for v in one.stats["interactions"]]
     assert t.sizes["n_trees"] == 3
+
+
+def test_tuning_set_get_and_validation():
+    """fmm_set_tuning keeps valid launch shapes, refuses the others and then
+    leaves the previous tuning in place (host-only tree: no CUDA)."""
+    t = plan(uniform_tree(2), 0.5)
+    assert F.fmm_get_tuning(t) == {"mono_subgrids": 0, "ctas_per_sm": 0}
+    F.fmm_set_tuning(t, mono_subgrids=2, ctas_per_sm=1)
+    assert F.fmm_get_tuning(t) == {"mono_subgrids": 2, "ctas_per_sm": 1}
+    for nb, cap in ((3, 0), (5, 0), (-1, 0), (1, 33), (1, -1)):
+        with pytest.raises(F.FmmError) as ei:
+            F.fmm_set_tuning(t, mono_subgrids=nb, ctas_per_sm=cap)
+        assert ei.value.code == B.FMM_ERR_INVALID_ARG
+        assert F.fmm_get_tuning(t) == {"mono_subgrids": 2, "ctas_per_sm": 1}
+    for nb in (0, 1, 2, 4):
+        F.fmm_set_tuning(t, mono_subgrids=nb, ctas_per_sm=32)
+        assert F.fmm_get_tuning(t) == {"mono_subgrids": nb, "ctas_per_sm": 32}

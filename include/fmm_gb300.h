@@ -170,13 +170,16 @@ typedef struct {
 int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes,
                    const fmm_config *cfg, fmm_tree_t *out);
 
-/* Buffer sizes for this tree (host, immediate). */
+/* Sizes of the buffers the caller allocates for this tree (the octree of
+ * Sec. 4.2: 512 cells per sub-grid) and of the tree's own workspace; host,
+ * immediate.  Errors: FMM_ERR_INVALID_ARG (NULL). */
 int fmm_get_sizes(fmm_tree_t tree, fmm_sizes *out);
 
 /* Interaction counts of the opening rule, stencil sizes, the operation-count
  * model (Sec. 4.3 quotes 455 and 12 operations for its two main kernels;
  * this library reports its own counts) and launch counts (host, immediate;
- * with FMM_FLAG_TIMING it first waits for the timed launches). */
+ * with FMM_FLAG_TIMING it first waits for the timed launches).
+ * Errors: FMM_ERR_INVALID_ARG (NULL). */
 int fmm_get_stats(fmm_tree_t tree, fmm_stats *out);
 
 /*
@@ -193,6 +196,10 @@ int fmm_get_stats(fmm_tree_t tree, fmm_stats *out);
  *        zero by definition and are not touched.
  *   com: device double [n_nodes][3][512], written for refined nodes only
  *        (a leaf cell's centre of mass is its centre by definition).
+ * Kernels are enqueued on `stream`; the call neither allocates nor waits.  A
+ * density that is not positive sets FMM_STATUS_BAD_DENSITY (fmm_get_status).
+ * Errors: FMM_ERR_INVALID_ARG (NULL tree or buffer, a FMM_FLAG_HOST_ONLY
+ * tree, rho or M not 16-byte aligned), FMM_ERR_CUDA (a launch failed).
  */
 int fmm_upward(fmm_tree_t tree, const double *rho, double *M, double *com,
                fmm_stream_t stream);
@@ -220,6 +227,8 @@ int fmm_upward(fmm_tree_t tree, const double *rho, double *M, double *com,
  * double, contracts in float with two-sum compensated accumulation, and
  * finishes the correction in double; FMM_DFLOAT evaluates every step (offsets,
  * derivative tensors, contraction, sums) in double-float.
+ * Errors: FMM_ERR_INVALID_ARG (NULL tree or buffer, L_comp NULL in FMM_MIXED
+ * or FMM_DFLOAT, a FMM_FLAG_HOST_ONLY tree), FMM_ERR_CUDA (a launch failed).
  */
 int fmm_m2l(fmm_tree_t tree, const double *M, const double *com, void *L,
             float *L_comp, double *dL1, fmm_stream_t stream);
@@ -237,13 +246,16 @@ int fmm_m2l(fmm_tree_t tree, const double *M, const double *com, void *L,
  * FMM_MIXED forms the shift increments (the k >= 1 terms) in float from float
  * copies of the parent expansion; FMM_FP64 and FMM_DFLOAT shift in double,
  * FMM_DFLOAT reading L as the double sum L + L_comp.
+ * Errors: as fmm_m2l.
  */
 int fmm_downward(fmm_tree_t tree, const void *L, const float *L_comp,
                  const double *dL1, const double *com, double *L64,
                  double *dL1_acc, fmm_stream_t stream);
 
 /*
- * Potential and field at leaf cells and the conservation sums, in FP64:
+ * Potential and field at leaf cells and the conservation sums, in FP64 (the
+ * end of Sec. 4.3's third step; the sums check the momentum and
+ * angular-momentum conservation of Sec. 2):
  *   phi = L64^(0), g = -(L64^(1) + dL1_acc), f = m g with m = rho h^3.
  *   phi:    device double [n_leaf][512], written.
  *   g:      device double [n_leaf][3][512], written.
@@ -252,6 +264,9 @@ int fmm_downward(fmm_tree_t tree, const void *L, const float *L_comp,
  *           The sums are FP64 in a fixed order (deterministic); the per-cell
  *           magnitudes in the last two, which only normalise the first two,
  *           are formed in float.
+ *   rho:    as for fmm_upward (read).
+ * Errors: FMM_ERR_INVALID_ARG (NULL tree or buffer, a FMM_FLAG_HOST_ONLY
+ * tree), FMM_ERR_CUDA (a launch failed).
  */
 int fmm_forces(fmm_tree_t tree, const double *L64, const double *dL1_acc,
                const double *rho, double *phi, double *g, double *totals,
@@ -292,7 +307,7 @@ enum { FMM_STATUS_BAD_DENSITY = 1 };
 int fmm_get_status(fmm_tree_t tree, int32_t *status, int clear);
 
 /*
- * The whole step in one call: fmm_upward, fmm_m2l, fmm_downward and
+ * The whole step of Sec. 4.3 in one call: fmm_upward, fmm_m2l, fmm_downward and
  * fmm_forces on the arguments they take (rho as for fmm_upward and
  * fmm_forces), with the same arithmetic and results.  The passes'
  * independent work is overlapped on a second stream that the tree owns and
@@ -356,10 +371,13 @@ int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int32_t n_tree
 int fmm_check_conversions(const double *values, int64_t n, int32_t *mismatch,
                           fmm_stream_t stream);
 
-/* Release the tree's host and device memory (synchronises the device first). */
+/* Release the tree's host and device memory, and its streams and events
+ * (synchronises the device first).  NULL is ignored; no error return. */
 void fmm_destroy_tree(fmm_tree_t tree);
 
-/* Message of the calling thread's last failed call ("" if none). */
+/* Message of the calling thread's last failed call ("" if none).  The string
+ * belongs to the library and stays valid until that thread's next failing
+ * call. */
 const char *fmm_last_error(void);
 
 #ifdef __cplusplus

@@ -58,12 +58,20 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="cfg5")
-    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--precision", choices=["mixed", "fp64", "dfloat"], default="mixed")
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--dfloat-steps", type=int, default=5)
     p.add_argument("--theta035-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    # other modes (no bench line): a minimal run of one pass for profiler
+    # captures, and an opening-angle sweep
+    p.add_argument("--profile-pass", choices=["upward", "m2l", "downward", "forces", "step"],
+                   default=None, help="run one pass --reps times (for ncu) and exit")
+    p.add_argument("--reps", type=int, default=1)
+    p.add_argument("--mono-subgrids", type=int, default=2)
+    p.add_argument("--theta-sweep", default=None,
+                   help="comma-separated opening angles: time the step at each and exit")
     return p.parse_args()
 
 
@@ -593,10 +601,113 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------ profiling driver
+def run_profile_pass(args):
+    """The smallest program around one pass, for profiler captures: the
+    chosen workload's buffers, one upward pass, then the pass --reps times.
+    No graph, no timing tree, no oracle."""
+    import torch
+    import paper_1908_03121_gb300 as F
+    from workloads import make_config
+
+    c = make_config(args.workload)
+    s = F.Solver(c["desc"], c["theta"], precision=args.precision)
+    F.fmm_set_tuning(s.tree, mono_subgrids=args.mono_subgrids)
+    s.rho.copy_(torch.from_numpy(c["rho"]).cuda())
+    s.upward()
+    if args.profile_pass in ("downward", "forces"):
+        s.m2l()
+    if args.profile_pass == "forces":
+        s.downward()
+    run = {"upward": s.upward, "m2l": s.m2l, "downward": s.downward, "forces": s.forces,
+           "step": s.step}[args.profile_pass]
+    for _ in range(args.reps):
+        run()
+    torch.cuda.synchronize()
+    print(f"{args.workload} {args.precision} {args.profile_pass} x{args.reps}: ok", flush=True)
+    s.close()
+    return 0
+
+
+# ---------------------------------------------------- opening-angle sweep
+def run_theta_sweep(args):
+    """The whole step at each opening angle: the tree planned anew (reach,
+    far/near offsets per parity, their union: 1074 at theta = 0.35), the
+    autotuned step captured and replayed with an L2 flush before each timed
+    replay, median of --steps; the FP64 path beside it for the speedup and the
+    field error, and the net force and torque.  One JSON object per angle,
+    then a markdown table."""
+    import torch
+    import paper_1908_03121_gb300 as F
+    from paper_1908_03121_gb300 import autotune
+    from workloads import make_config
+
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def net(tot):
+        return (float(np.max(np.linalg.norm(tot[:, 0:3], axis=1) / tot[:, 6])),
+                float(np.max(np.linalg.norm(tot[:, 3:6], axis=1) / tot[:, 7])))
+
+    rows = []
+    for theta in [float(t) for t in args.theta_sweep.split(",")]:
+        c = make_config(args.workload, theta=theta)
+        rho = torch.from_numpy(c["rho"]).cuda()
+        s = F.Solver(c["desc"], c["theta"], precision=args.precision)
+        st = s.tree.stats
+        inter = int(sum(st["interactions"]))
+        s.rho.copy_(rho)
+        s.step()
+        autotune.tune(s)
+        s.capture()
+        _, per, _ = time_graph(torch, s, args.steps, 2, flush, stream, label="theta_sweep")
+        ms = float(np.median(per))
+        g_ours = s.g.clone()
+        nf, nt = net(s.totals.cpu().numpy())
+        cells = int(s.tree.sizes["n_nodes"]) * 512          # every target cell
+        s.close()
+        s64 = F.Solver(c["desc"], c["theta"], precision="fp64")
+        s64.rho.copy_(rho)
+        s64.step()
+        s64.capture()
+        _, per64, _ = time_graph(torch, s64, max(1, args.fp64_steps), 1, flush, stream,
+                                 label="theta_sweep_fp64")
+        ms64 = float(np.median(per64))
+        err = float((g_ours - s64.g).abs().max() / s64.g.abs().max())
+        s64.close()
+        row = {"theta": theta, "precision": args.precision, "reach": int(st["reach"]),
+               "stencil_far": int(st["stencil_far"]), "stencil_near": int(st["stencil_near"]),
+               "stencil_union": int(st["stencil_union"]), "interactions_per_step": inter,
+               "ms_per_step": ms, "interactions_per_s": inter / (ms / 1000.0),
+               "paper_equivalent_evals_per_s": st["stencil_union"] * cells / (ms / 1000.0),
+               "fp64_ms_per_step": ms64, "speedup_over_fp64": ms64 / ms,
+               "force_err_vs_fp64": err, "net_force": nf, "net_torque": nt}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print()
+    print("| theta | reach | far + near per parity | union | interactions / step | ms | "
+          "interactions/s | paper-equivalent evals/s | FP64 ms | speedup | force err | net torque |")
+    print("|---:|---:|---:|---:|---:|---:|---:|---:|---:|---:|---:|---:|")
+    for r in rows:
+        print(f"| {r['theta']} | {r['reach']} | {r['stencil_far']} + {r['stencil_near']} | "
+              f"{r['stencil_union']} | {r['interactions_per_step']:,} | {r['ms_per_step']:.2f} | "
+              f"{r['interactions_per_s']:.3g} | {r['paper_equivalent_evals_per_s']:.3g} | "
+              f"{r['fp64_ms_per_step']:.1f} | {r['speedup_over_fp64']:.1f}x | "
+              f"{r['force_err_vs_fp64']:.1e} | {r['net_torque']:.1e} |")
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_pass:
+        return run_profile_pass(args)
+    if args.theta_sweep:
+        return run_theta_sweep(args)
     return run_ours(args)
 
 

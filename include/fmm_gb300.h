@@ -339,8 +339,15 @@ int fmm_step(fmm_tree_t tree, const double *rho, double *M, double *com, void *L
  * loads it, until the process exits.
  *   leaf_table: device int32 [n_leaf][6], one row per leaf node in leaf-row
  *               order: node index, level, ix, iy, iz, tree_id (the tree's
- *               descriptor values).
- *   n_leaf:     1..65536 (FMM_ERR_INVALID_ARG beyond the array's size).
+ *               descriptor values).  The kernels check every row: node in
+ *               [0, n_nodes), level in 1..20, ix, iy, iz in [0, 2^(level-1)),
+ *               tree_id in [0, n_trees).  A row that fails is skipped without
+ *               any access through it: its phi and g rows are set to NaN, and
+ *               the totals of every tree come out NaN.
+ *   n_leaf:     1..65536 (FMM_ERR_INVALID_ARG beyond the array's size); rho,
+ *               phi and g have n_leaf rows.
+ *   n_nodes:    number of nodes of the node-indexed buffers L64 and dL1_acc
+ *               (>= n_leaf).
  *   n_trees:    number of trees, 1..65535; totals gets one row per tree.
  *   box_size:   edge of the domain (box_lo does not enter the sums).
  *   L64, dL1_acc, rho, phi, g, totals: as for fmm_forces.
@@ -349,10 +356,10 @@ int fmm_step(fmm_tree_t tree, const double *rho, double *M, double *com, void *L
  * them.  The first call on a device looks up the array's device address with
  * that device current; make that first call before any stream capture.
  */
-int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int32_t n_trees,
-                       double box_size, const double *L64, const double *dL1_acc,
-                       const double *rho, double *phi, double *g, double *totals,
-                       fmm_stream_t stream);
+int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int64_t n_nodes,
+                       int32_t n_trees, double box_size, const double *L64,
+                       const double *dL1_acc, const double *rho, double *phi, double *g,
+                       double *totals, fmm_stream_t stream);
 
 /*
  * fmm_check_conversions -- diagnostic, no counterpart in the paper.  The

@@ -62,16 +62,41 @@ __device__ __forceinline__ void block_sum8(double v[8], double (*sh)[8])
     }
 }
 
+// a leaf-table row the pass can use: node inside the caller's node-indexed
+// buffers, level 1..20, coordinates inside that level's grid, tree inside
+// the totals
+__device__ __forceinline__ bool row_valid(const int32_t *lt, int64_t n_nodes, int32_t n_trees)
+{
+    const int level = lt[1];
+    if (lt[0] < 0 || int64_t(lt[0]) >= n_nodes || level < 1 || level > 20) return false;
+    const int side = 1 << (level - 1);
+    return lt[2] >= 0 && lt[2] < side && lt[3] >= 0 && lt[3] < side && lt[4] >= 0 &&
+           lt[4] < side && lt[5] >= 0 && lt[5] < n_trees;
+}
+
 // One CTA per leaf node (leaf table row r = leaf row r): phi, g and the
-// node's 8 partial sums into the static scratch rows.
+// node's 8 partial sums into the static scratch rows.  A row that fails
+// row_valid reads nothing through its node index: its phi and g rows and its
+// partial sums are NaN.
 __global__ void __launch_bounds__(kThreads) noalloc_leaf_kernel(
-    const int32_t *__restrict__ leaf_table, const double *__restrict__ L64,
-    const double *__restrict__ dacc, const double *__restrict__ rho, double *__restrict__ phi,
-    double *__restrict__ g, double *__restrict__ partials, double box_size)
+    const int32_t *__restrict__ leaf_table, int64_t n_nodes, int32_t n_trees,
+    const double *__restrict__ L64, const double *__restrict__ dacc,
+    const double *__restrict__ rho, double *__restrict__ phi, double *__restrict__ g,
+    double *__restrict__ partials, double box_size)
 {
     __shared__ double sh[kThreads / 32][8];
     const int row = blockIdx.x;
     const int32_t *lt = leaf_table + size_t(row) * 6;
+    if (!row_valid(lt, n_nodes, n_trees)) {
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        for (int c = threadIdx.x; c < fmm::NCELL; c += kThreads) {
+            phi[size_t(row) * fmm::NCELL + c] = nan;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) g[(size_t(row) * 3 + a) * fmm::NCELL + c] = nan;
+        }
+        if (threadIdx.x < 8) partials[size_t(row) * 8 + threadIdx.x] = nan;
+        return;
+    }
     const int node = lt[0], level = lt[1], ix = lt[2], iy = lt[3], iz = lt[4];
     const double h = box_size / (8.0 * double(1u << (level - 1)));
     const double h3 = h * h * h;
@@ -114,22 +139,37 @@ __global__ void __launch_bounds__(kThreads) noalloc_leaf_kernel(
 }
 
 // One CTA per tree: the tree's rows of the scratch array in ascending row
-// order (fixed order, deterministic).
+// order (fixed order, deterministic).  If any row of the table is invalid,
+// every tree's totals are NaN (a row with a bad tree id belongs to no tree,
+// so no single tree could carry the error).
 __global__ void __launch_bounds__(512) noalloc_reduce_kernel(const int32_t *__restrict__ leaf_table,
-                                                             int64_t n_leaf,
+                                                             int64_t n_leaf, int64_t n_nodes,
+                                                             int32_t n_trees,
                                                              const double *__restrict__ partials,
                                                              double *__restrict__ totals)
 {
     __shared__ double sh[16][8];
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
     const int tree = blockIdx.x;
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t i = threadIdx.x; i < n_leaf; i += blockDim.x)
+    int bad = 0;
+    for (int64_t i = threadIdx.x; i < n_leaf; i += blockDim.x) {
+        if (!row_valid(leaf_table + i * 6, n_nodes, n_trees)) {
+            bad = 1;
+            continue;
+        }
         if (leaf_table[i * 6 + 5] == tree)
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] += partials[size_t(i) * 8 + k];
-    block_sum8(v, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 8; ++k) totals[size_t(tree) * 8 + k] = v[k];
+    }
+    if (bad) atomicOr(&s_bad, 1);
+    block_sum8(v, sh);          // its barrier publishes s_bad
+    if (threadIdx.x == 0) {
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        for (int k = 0; k < 8; ++k) totals[size_t(tree) * 8 + k] = s_bad ? nan : v[k];
+    }
 }
 
 // device address of the scratch array for the current device (set-up on
@@ -156,10 +196,10 @@ int scratch_for_current_device(double **out)
 
 extern "C" {
 
-int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int32_t n_trees,
-                       double box_size, const double *L64, const double *dL1_acc,
-                       const double *rho, double *phi, double *g, double *totals,
-                       fmm_stream_t stream)
+int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int64_t n_nodes,
+                       int32_t n_trees, double box_size, const double *L64,
+                       const double *dL1_acc, const double *rho, double *phi, double *g,
+                       double *totals, fmm_stream_t stream)
 {
     if (!leaf_table || !L64 || !dL1_acc || !rho || !phi || !g || !totals)
         return noalloc_fail(FMM_ERR_INVALID_ARG, "NULL buffer");
@@ -167,6 +207,7 @@ int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int32_t n_tree
         return noalloc_fail(FMM_ERR_INVALID_ARG,
                             "n_leaf must lie in 1.." + std::to_string(kMaxLeafNodes) +
                                 " (the size of the fixed scratch array)");
+    if (n_nodes < n_leaf) return noalloc_fail(FMM_ERR_INVALID_ARG, "n_nodes must be >= n_leaf");
     if (n_trees < 1 || n_trees > 65535)
         return noalloc_fail(FMM_ERR_INVALID_ARG, "n_trees must lie in 1..65535");
     if (!(box_size > 0.0)) return noalloc_fail(FMM_ERR_INVALID_ARG, "box_size must be positive");
@@ -174,12 +215,14 @@ int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int32_t n_tree
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    noalloc_leaf_kernel<<<unsigned(n_leaf), kThreads, 0, s>>>(leaf_table, L64, dL1_acc, rho, phi, g,
-                                                              scratch, box_size);
+    noalloc_leaf_kernel<<<unsigned(n_leaf), kThreads, 0, s>>>(leaf_table, n_nodes, n_trees, L64,
+                                                              dL1_acc, rho, phi, g, scratch,
+                                                              box_size);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return noalloc_fail(FMM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
-    noalloc_reduce_kernel<<<unsigned(n_trees), 512, 0, s>>>(leaf_table, n_leaf, scratch, totals);
+    noalloc_reduce_kernel<<<unsigned(n_trees), 512, 0, s>>>(leaf_table, n_leaf, n_nodes, n_trees,
+                                                            scratch, totals);
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return noalloc_fail(FMM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -106,8 +106,8 @@ def load(build=True):
         lib.fmm_step.argtypes = [P] * 13
         lib.fmm_destroy_tree.argtypes = [P]
         lib.fmm_destroy_tree.restype = None
-        lib.fmm_forces_noalloc.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
-                                           P, P, P, P, P, P, P]
+        lib.fmm_forces_noalloc.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.c_double, P, P, P, P, P, P, P]
         lib.fmm_check_conversions.argtypes = [P, ctypes.c_int64, P, P]
         lib.fmm_set_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_get_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
@@ -236,12 +236,13 @@ def fmm_destroy_tree(tree):
     load().fmm_destroy_tree(tree.handle)
 
 
-def fmm_forces_noalloc(leaf_table, n_leaf, n_trees, box_size, L64, dL1_acc, rho, phi, g,
-                       totals, stream=None):
+def fmm_forces_noalloc(leaf_table, n_leaf, n_nodes, n_trees, box_size, L64, dL1_acc, rho, phi,
+                       g, totals, stream=None):
     """The leaf-force pass without a tree handle or any allocation (for callers
     that cannot allocate device memory); ``leaf_table`` is a device int32
-    [n_leaf, 6] tensor (node, level, ix, iy, iz, tree_id per leaf node)."""
-    _check(load().fmm_forces_noalloc(_ptr(leaf_table), int(n_leaf), int(n_trees),
+    [n_leaf, 6] tensor (node, level, ix, iy, iz, tree_id per leaf node),
+    ``n_nodes`` the node count of L64 and dL1_acc."""
+    _check(load().fmm_forces_noalloc(_ptr(leaf_table), int(n_leaf), int(n_nodes), int(n_trees),
                                      float(box_size), _ptr(L64), _ptr(dL1_acc), _ptr(rho),
                                      _ptr(phi), _ptr(g), _ptr(totals), _stream(stream)))
 

@@ -47,8 +47,8 @@ def test_forces_noalloc_matches_fmm_forces(name, precision):
         phi = torch.full_like(s.phi, float("nan"))
         g = torch.full_like(s.g, float("nan"))
         tot = torch.full_like(s.totals, float("nan"))
-        F.fmm_forces_noalloc(table, n_leaf, n_trees, c["box_size"], s.L64, s.dacc, s.rho,
-                             phi, g, tot)
+        F.fmm_forces_noalloc(table, n_leaf, len(c["desc"]), n_trees, c["box_size"], s.L64,
+                             s.dacc, s.rho, phi, g, tot)
         torch.cuda.synchronize()
         assert torch.equal(phi, ref_phi)
         assert torch.equal(g, ref_g)
@@ -64,6 +64,34 @@ def test_forces_noalloc_matches_fmm_forces(name, precision):
 
 def test_forces_noalloc_rejects_oversize():
     with pytest.raises(F.FmmError) as ei:
-        F.fmm_forces_noalloc(1, 65537, 1, 1.0, 1, 1, 1, 1, 1, 1)
+        F.fmm_forces_noalloc(1, 65537, 65537, 1, 1.0, 1, 1, 1, 1, 1, 1)
     assert ei.value.code == B.FMM_ERR_INVALID_ARG
     assert "65536" in F.fmm_last_error()
+
+
+@pytest.mark.parametrize("col,value", [(0, 10 ** 6), (0, -1), (1, 0), (1, 21), (2, 9999),
+                                       (5, 7), (5, -2)])
+def test_forces_noalloc_flags_bad_rows(col, value):
+    """A leaf-table row whose node, level, coordinates or tree lie outside
+    the caller's buffers is skipped by the kernels (no access through it):
+    its field rows and every tree's totals come out NaN, the good rows are
+    untouched."""
+    c = make_config("cfg1")
+    s = F.Solver(c["desc"], c["theta"], precision="fp64")
+    s.rho.copy_(torch.from_numpy(c["rho"]).cuda())
+    s.step()
+    torch.cuda.synchronize()
+    t = leaf_table(c["desc"])
+    t[3, col] = value
+    table = torch.from_numpy(t).cuda()
+    phi = torch.zeros_like(s.phi)
+    g = torch.zeros_like(s.g)
+    tot = torch.zeros_like(s.totals)
+    F.fmm_forces_noalloc(table, t.shape[0], len(c["desc"]), 1, c["box_size"], s.L64, s.dacc,
+                         s.rho, phi, g, tot)
+    torch.cuda.synchronize()
+    assert torch.isnan(phi[3]).all() and torch.isnan(g[3]).all()
+    good = [r for r in range(t.shape[0]) if r != 3]
+    assert torch.equal(phi[good], s.phi[good]) and torch.equal(g[good], s.g[good])
+    assert torch.isnan(tot).all()
+    s.close()

@@ -35,10 +35,18 @@ METRIC = "M2L cell-interactions/s on 1 GB300, FP32-mixed vs FP64 at rel. force e
 UNIT = "cell-interactions/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILES = os.path.join(ROOT, "profiles")
-# FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max clock
+# FP32 FMA peak of a GB300 from its unit counts: 152 SMs x 128 lanes x 2 flop
+# x 2.07 GHz maximum clock (the measured figure, from an FMA loop timed on
+# the GPU in use, is what the roofline uses)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64 rate of a GB300 (Blackwell Ultra): 1.25 TFLOP/s
+# FP64 rate of a GB300 (Blackwell Ultra): 1.25 TFLOP/s nominal
 FP64_PEAK_TFLOPS = 1.25
+# the paper's operation counts per interaction (Sec. 4.3): multipole targets
+# 455, monopole<-monopole 12, with its 1074-point stencil at theta = 0.35
+PAPER_FLOPS_MULTIPOLE = 455
+PAPER_FLOPS_MONOPOLE = 12
+# the paper's Table 2 FMM rates (FP64, whole same-level pass), context only
+PAPER_TABLE2_GFLOPS = {"P100 (Piz Daint node)": 973, "V100 PCIe": 2271}
 L2_FLUSH_BYTES = 256 << 20
 
 WORKLOAD_TEXT = {
@@ -62,6 +70,12 @@ def parse_args():
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--dfloat-steps", type=int, default=5)
     p.add_argument("--theta035-steps", type=int, default=5)
+    # the other full-size workloads reported beside the headline one
+    p.add_argument("--extra-workloads", default="cfg3,cfg4")
+    p.add_argument("--extra-steps", type=int, default=20)
+    # the full FP64 oracle solve of the adaptive level-5 binary (cfg3), for
+    # each precision's error against the oracle itself (about 20-40 s of CPU)
+    p.add_argument("--no-oracle-accuracy", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     # other modes (no bench line): a minimal run of one pass for profiler
@@ -306,6 +320,101 @@ def run_reference(args):
     return 0
 
 
+# -------------------------------------------------------- measured peaks
+def measure_peaks(torch, F, pci=None):
+    """FP32 and FP64 fused multiply-add rates of this GPU: the library's
+    fmm_peak_rate loop (every SM, 8 CTAs of 256 threads, 8 independent chains
+    per thread), timed by CUDA events on the launch stream, best of several
+    launches, with the SM clock sampled meanwhile.  Changes no GPU setting."""
+    stream = torch.cuda.current_stream()
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    out = {}
+    clocks = ClockSampler(pci)
+    clocks.start()
+    for kind, iters, reps in (("fp32", 40000, 12), ("fp32x2", 20000, 6), ("fp64", 600, 6)):
+        F.fmm_peak_rate(kind, iters, 8, sink)              # warm-up
+        best = 0.0
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fl = F.fmm_peak_rate(kind, iters, 8, sink)
+            b.record(stream)
+            b.synchronize()
+            best = max(best, fl / (a.elapsed_time(b) / 1000.0) / 1e12)
+        out[kind + "_tflops"] = best
+    torch.cuda.synchronize()
+    out["clocks"] = clocks.stop()
+    out["how"] = ("fmm_peak_rate: fused multiply-add loop on every SM (8 CTAs x 256 threads, "
+                  "8 independent chains per thread), CUDA events, best launch")
+    return out
+
+
+# ----------------------------------------------------- other workloads
+def net_sums(tot):
+    """Largest net force and net torque over the trees, each relative to its
+    normaliser (sum |f|, sum |x cross f|)."""
+    return (float(np.max(np.linalg.norm(tot[:, 0:3], axis=1) / tot[:, 6])),
+            float(np.max(np.linalg.norm(tot[:, 3:6], axis=1) / tot[:, 7])))
+
+
+def other_workload(torch, F, autotune, name, args, flush, stream, keep):
+    """One full-size workload in every precision: interactions/s of the
+    captured, autotuned step (median of --extra-steps; FP64 of --fp64-steps),
+    force error against the FP64 GPU path, net force and torque.  The fields
+    are left in ``keep[name]`` (host arrays) for the oracle comparison."""
+    from workloads import make_config
+    cw = make_config(name)
+    rho = torch.from_numpy(cw["rho"]).cuda()
+    out = {"workload": f"{name}: {WORKLOAD_TEXT.get(name, name)}"}
+    got = {}
+    for prec in ("mixed", "dfloat", "fp64"):
+        sw = F.Solver(cw["desc"], cw["theta"], precision=prec)
+        st, sz = sw.tree.stats, sw.tree.sizes
+        sw.rho.copy_(rho)
+        sw.step()
+        tuning = autotune.tune(sw)[0]
+        sw.capture()
+        steps = max(1, args.fp64_steps) if prec == "fp64" else args.extra_steps
+        ms, _, _ = time_graph(torch, sw, steps, 2, flush, stream, label=f"{name}_{prec}")
+        inter = int(sum(st["interactions"]))
+        nf, nt = net_sums(sw.totals.double().cpu().numpy())
+        got[prec] = sw.g.clone()
+        out[prec] = {"value": inter / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms,
+                     "net_force": nf, "net_torque": nt, "tuning": tuning}
+        out["n_trees"], out["n_nodes"], out["leaf_cells"] = (int(sz["n_trees"]), int(sz["n_nodes"]),
+                                                             int(sz["n_leaf"]) * 512)
+        out["interactions_per_step"] = inter
+        sw.close()
+    g64 = got["fp64"]
+    for prec in ("mixed", "dfloat"):
+        out[prec]["force_err_vs_fp64_path"] = float((got[prec] - g64).abs().max() / g64.abs().max())
+        out[prec]["force_err_per_cell_p99"] = per_cell_force_errors(got[prec], g64)["p99"]
+        out[prec]["speedup_over_fp64"] = out["fp64"]["ms_per_step"] / out[prec]["ms_per_step"]
+    keep[name] = {k: v.cpu().numpy() for k, v in got.items()}
+    return out
+
+
+def oracle_accuracy(name, fields):
+    """Each precision's field against the complete FP64 oracle solve of the
+    workload: max |g - g_oracle| / max |g_oracle| over every leaf cell, and the
+    per-cell 99th percentile."""
+    import torch
+    from oracle import oracle as O
+    from workloads import make_config
+    c = make_config(name)
+    t0 = time.perf_counter()
+    ref = O.solve(O.Tree.from_config(c), c["rho"])
+    gref = ref["g"]
+    out = {"workload": name, "oracle_seconds": time.perf_counter() - t0,
+           "oracle_cores": os.cpu_count()}
+    for prec, g in fields.items():
+        out[prec] = {"force_err": float(np.abs(g - gref).max() / np.abs(gref).max()),
+                     "force_err_per_cell_p99": per_cell_force_errors(
+                         torch.from_numpy(g), torch.from_numpy(gref))["p99"]}
+    return out
+
+
 # ------------------------------------------------------------------- ours
 def time_graph(torch, solver, steps, warmup, flush, stream, clocks=None, label="timed_steps"):
     """Per-step device ms of graph replays; the L2 flush runs between steps,
@@ -330,7 +439,7 @@ def time_graph(torch, solver, steps, warmup, flush, stream, clocks=None, label="
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop() if clocks else None
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    return float(np.mean(ms)), ms, clk
+    return float(np.median(ms)), ms, clk
 
 
 def run_ours(args):
@@ -492,6 +601,8 @@ def run_ours(args):
                 v["share"] = v["ms_per_step"] / total if total else 0.0
             return out
 
+        peaks = measure_peaks(torch, F, pci)
+        result["peaks"] = peaks
         per_kernel = kernel_times(args.precision, best, max(3, min(args.steps, 20)))
         result["kernels"] = per_kernel
         inter = stats["interactions"]
@@ -505,10 +616,16 @@ def run_ours(args):
         dom = max(work, key=lambda k: per_kernel.get(k, {}).get("ms_per_step", 0.0))
         dom_ms = per_kernel[dom]["ms_per_launch"]
         achieved = work[dom] / (dom_ms / 1000.0) / 1e12
-        if args.precision == "mixed":
-            peak, which = FP32_PEAK_TFLOPS, "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+        # the same-level kernels of the mixed and double-float precisions run
+        # on the FP32 pipe, the FP64 precision's on the FP64 pipe: the peak is
+        # that pipe's fused multiply-add rate measured above on this GPU
+        if args.precision in ("mixed", "dfloat"):
+            peak = peaks["fp32_tflops"]
+            which = (f"measured FP32 FMA loop ({peak:.1f} TFLOP/s; derived from unit counts "
+                     f"and the 2.07 GHz clock: {FP32_PEAK_TFLOPS:.1f})")
         else:
-            peak, which = FP64_PEAK_TFLOPS, "FP64: GB300 rate 1.25 TFLOP/s"
+            peak = peaks["fp64_tflops"]
+            which = f"measured FP64 FMA loop ({peak:.2f} TFLOP/s; nominal {FP64_PEAK_TFLOPS})"
         result["roofline"] = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                               "unit": "TFLOP/s", "frac": achieved / peak,
                               "traffic": profiled_traffic(dom, args.workload),
@@ -577,22 +694,51 @@ def run_ours(args):
             st35 = s35.tree.stats
             inter35 = int(sum(st35["interactions"]))
             target_cells = int(s35.tree.sizes["n_nodes"]) * 512
+            sz35 = s35.tree.sizes
+            union = int(st35["stencil_union"])
+            # the paper's accounting (Sec. 4.3, Sec. 6.1): every sub-grid's
+            # kernel evaluates the whole superimposed stencil for its 512
+            # cells, at 455 operations per point for a multipole target and
+            # 12 for a monopole target, over the step time
+            paper_ops = 512 * union * (int(sz35["n_refined"]) * PAPER_FLOPS_MULTIPOLE +
+                                       int(sz35["n_leaf"]) * PAPER_FLOPS_MONOPOLE)
             result["theta_0.35"] = {
                 "value": inter35 / (ms35 / 1000.0), "unit": UNIT, "ms_per_step": ms35,
                 "interactions_per_step": inter35,
-                "stencil_union": int(st35["stencil_union"]),
-                "paper_equivalent_stencil_evaluations_per_s":
-                    int(st35["stencil_union"]) * target_cells / (ms35 / 1000.0),
-                "note": "paper-equivalent = 1074-point stencil x all target cells / step time"}
+                "stencil_union": union,
+                "paper_equivalent_stencil_evaluations_per_s": union * target_cells / (ms35 / 1000.0),
+                "paper_gflops": paper_ops / (ms35 / 1000.0) / 1e9,
+                "paper_table2_gflops_fp64_context": PAPER_TABLE2_GFLOPS,
+                "note": "paper-equivalent = 1074-point stencil x all target cells / step time; "
+                        "paper_gflops = the same points x 455 (multipole targets) or 12 "
+                        "(monopole targets) / step time, the paper's own accounting"}
             s35.close()
+
+        # the other full-size workloads: each precision through the captured,
+        # autotuned step (median of --extra-steps), with its error against
+        # the FP64 GPU path and its net force and torque
+        extra = [w for w in args.extra_workloads.split(",") if w and w != args.workload]
+        accuracy_ref = {}
+        for wname in extra:
+            result[wname] = other_workload(torch, F, autotune, wname, args, flush, stream,
+                                           accuracy_ref)
+        # the headline path against the FP64 oracle itself (cfg3 solved
+        # completely on the host)
+        if world == 1 and not args.no_oracle_accuracy and "cfg3" in accuracy_ref:
+            result["accuracy_vs_oracle"] = oracle_accuracy("cfg3", accuracy_ref["cfg3"])
 
         if world == 1 and not args.no_cpu_baseline:
             rate, info = oracle_rate(c, args.cpu_seconds)
+            rate1, info1 = oracle_rate(c, max(2.0, args.cpu_seconds / 2), batch=256, n_threads=1)
             result["cpu_baseline"] = {
                 "value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                 "sample": f"FP64 oracle same-level pass over {info['cells']} random target "
                           f"cells of {args.workload} ({info['interactions']} interactions, "
-                          f"{info['seconds']:.1f} s), upward pass untimed"}
+                          f"{info['seconds']:.1f} s), upward pass untimed",
+                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                  "sample": f"{info1['cells']} random target cells "
+                                            f"({info1['interactions']} interactions, "
+                                            f"{info1['seconds']:.1f} s)"}}
         print(json.dumps(result), flush=True)
     solver.close()
     if dist is not None:

@@ -378,6 +378,25 @@ int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int64_t n_node
 int fmm_check_conversions(const double *values, int64_t n, int32_t *mismatch,
                           fmm_stream_t stream);
 
+/*
+ * fmm_peak_rate -- diagnostic, no counterpart in the paper: the denominators
+ * of the roofline fractions of the FP32- and FP64-bound kernels, measured on
+ * the GPU in use rather than taken from a datasheet.  Enqueues one launch of
+ * blocks_per_sm x (number of SMs) CTAs of 256 threads, each thread running
+ * 8 independent fused multiply-add chains for iters x 16 steps:
+ *   kind 0: float fmaf;  1: the paired FP32 form (two lanes per
+ *   instruction);  2: double fma.
+ *   sink:  device float [1], written only on a value no chain can reach (it
+ *          keeps the chains live; its content is meaningless).
+ *   flops: host double, receives the launch's operation count (2 per
+ *          multiply-add lane); divide by the launch's CUDA-event time.
+ * Changes no GPU setting.  Errors: FMM_ERR_INVALID_ARG (kind outside 0..2,
+ * iters outside 1..2^40, blocks_per_sm outside 1..32, NULL pointer),
+ * FMM_ERR_CUDA.
+ */
+int fmm_peak_rate(int32_t kind, int64_t iters, int32_t blocks_per_sm, float *sink,
+                  double *flops, fmm_stream_t stream);
+
 /* Release the tree's host and device memory, and its streams and events
  * (synchronises the device first).  NULL is ignored; no error return. */
 void fmm_destroy_tree(fmm_tree_t tree);

@@ -32,8 +32,8 @@ KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_mul
 
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
             "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_step", "fmm_set_tuning", "fmm_get_tuning",
-            "fmm_forces_noalloc", "fmm_check_conversions", "fmm_get_status", "fmm_destroy_tree",
-            "fmm_last_error")
+            "fmm_forces_noalloc", "fmm_check_conversions", "fmm_peak_rate", "fmm_get_status",
+            "fmm_destroy_tree", "fmm_last_error")
 
 NCELL = 512
 NCOMP = 20
@@ -109,6 +109,8 @@ def load(build=True):
         lib.fmm_forces_noalloc.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                            ctypes.c_double, P, P, P, P, P, P, P]
         lib.fmm_check_conversions.argtypes = [P, ctypes.c_int64, P, P]
+        lib.fmm_peak_rate.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, P,
+                                      ctypes.POINTER(ctypes.c_double), P]
         lib.fmm_set_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_get_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_get_status.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
@@ -253,6 +255,20 @@ def fmm_check_conversions(values, mismatch, stream=None):
     [1]) receives 0 when all agree, else a bit mask."""
     _check(load().fmm_check_conversions(_ptr(values), int(values.numel()), _ptr(mismatch),
                                         _stream(stream)))
+
+
+PEAK_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def fmm_peak_rate(kind, iters, blocks_per_sm, sink, stream=None):
+    """Diagnostic: enqueue one fused multiply-add loop launch (kind "fp32",
+    "fp32x2" or "fp64") and return its operation count; time it with CUDA
+    events on the same stream.  ``sink`` is a device float tensor of one
+    element."""
+    fl = ctypes.c_double(0.0)
+    _check(load().fmm_peak_rate(int(PEAK_KINDS.get(kind, kind)), int(iters), int(blocks_per_sm),
+                                _ptr(sink), ctypes.byref(fl), _stream(stream)))
+    return fl.value
 
 
 def fmm_set_tuning(tree, mono_subgrids=0, ctas_per_sm=0):

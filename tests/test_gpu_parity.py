@@ -24,10 +24,14 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 FORCE_TOL = 1e-6
-# Float contraction rounds the two directions of a pair independently, so the
-# mixed path conserves momentum only to about float epsilon times the pair
-# terms; this bound is that arithmetic's, not the 1e-12 target.
-MIXED_CONSERVATION = 1e-7
+# The conservation target (net force and net torque relative to sum |f| and
+# sum |x cross f|).  The double-float and FP64 precisions meet it; the mixed
+# precision's float contraction does not (1e-10 to 2e-9 measured at every
+# level of multipole targets), which the expected-failure tests below record.
+CONSERVATION_TARGET = 1e-12
+MIXED_XFAIL = ("float contraction rounds the two directions of each pair independently: "
+               "net torque 1e-10 to 2e-9 at every level of multipole targets (measured), "
+               "against the 1e-12 target; the double-float precision meets it")
 # Double-float carries about 48 bits (unit roundoff 2^-48 ~ 3.6e-15 per
 # operation); a few hundred terms of a hundred operations each put the
 # same-level result near 1e-13 relative (measured up to 1.4e-13 on the small
@@ -277,10 +281,19 @@ def test_end_to_end_mixed(name):
     g, gref = host(s.g), ref["g"]
     assert rel_err(g, gref) <= FORCE_TOL
     assert rel_err(host(s.phi), ref["phi"]) <= FORCE_TOL
-    tot = host(s.totals)
-    assert np.all(tree_force(tot) <= MIXED_CONSERVATION), tree_force(tot)
-    assert np.all(tree_torque(tot) <= MIXED_CONSERVATION), tree_torque(tot)
     s.close()
+
+
+@pytest.mark.xfail(reason=MIXED_XFAIL)
+@pytest.mark.parametrize("name", ["cfg1", "cfg2", "adaptive4", "batch3"])
+def test_mixed_conservation_target(name):
+    """The 1e-12 conservation target, on the mixed precision."""
+    c, _ = oracle_solution(name)
+    s = solve_gpu(c, "mixed")
+    tot = host(s.totals)
+    s.close()
+    assert np.all(tree_force(tot) <= CONSERVATION_TARGET), tree_force(tot)
+    assert np.all(tree_torque(tot) <= CONSERVATION_TARGET), tree_torque(tot)
 
 
 @pytest.mark.parametrize("name", SMALL)
@@ -548,12 +561,10 @@ def test_full_size_sampled(name):
     for sl in ORDER_SLICES[:2]:
         assert rel_err(Lgpu[:, sl], Lref[:, sl]) <= FP64_TOL
     s.close()
-    # mixed path, the benchmark's configuration
+    # mixed path, the benchmark's configuration (its conservation against
+    # the target: test_gpu_full_oracle)
     s = solve_gpu(c, "mixed")
     assert rel_err(host(s.g)[rows, :, cells], ref["g"]) <= FORCE_TOL
-    tot = host(s.totals)
-    assert np.all(tree_force(tot) <= MIXED_CONSERVATION), tree_force(tot)
-    assert np.all(tree_torque(tot) <= MIXED_CONSERVATION), tree_torque(tot)
     s.close()
     # double-float (conserving) path
     s = solve_gpu(c, "dfloat")

@@ -59,7 +59,7 @@ enum {
     FMM_ERR_INVALID_ARG = -1,        /* null pointer, bad config, host-only tree */
     FMM_ERR_TREE = -2,               /* descriptors do not form a valid octree */
     FMM_ERR_CUDA = -3,               /* a CUDA call or launch failed */
-    FMM_ERR_TIMEOUT = -4,            /* reserved: a device wait exceeded its budget */
+    FMM_ERR_TIMEOUT = -4,            /* a device-side wait exceeded its budget */
     FMM_ERR_NOMEM = -5               /* device or host allocation failed */
 };
 
@@ -279,7 +279,19 @@ typedef struct {
     int32_t mono_subgrids;           /* sub-grids per pass of the monopole kernel:
                                         1, 2 or 4 (float) / 1, 2 (double) */
     int32_t ctas_per_sm;             /* cap on persistent CTAs per SM (0 = occupancy) */
-    int32_t reserved[6];
+    int32_t dataflow;                /* 1: fmm_step runs the refined levels' shifts and
+                                        every leaf's shift and forces as one persistent
+                                        launch, each item waiting on its parent's
+                                        readiness counter (the device-side counterpart
+                                        of the paper's futurization, Sec. 4.1 and
+                                        Sec. 5.1) instead of one launch per level */
+    int32_t wait_budget_us;          /* budget of one device-side wait, microseconds
+                                        (0 = 1 s); on expiry the wait gives up and
+                                        FMM_STATUS_TIMEOUT is set */
+    int32_t drop_first_producer;     /* test injection, host side: the dataflow queue
+                                        leaves out the first node's items, so the waits
+                                        on it run out (0 in normal use) */
+    int32_t reserved[3];
 } fmm_tuning;
 
 /* Set / read the tree's tuning (host, immediate; affects later launches).
@@ -298,12 +310,17 @@ int fmm_get_tuning(fmm_tree_t tree, fmm_tuning *tuning);
  *     angular-momentum correction).  Zero-density regions take a small
  *     floor instead (the workloads use 1e-10).  The outputs of a step that
  *     set the bit are undefined.
+ *   FMM_STATUS_TIMEOUT: a device-side wait of the dataflow pass (fmm_tuning
+ *     .dataflow) ran past its budget; the waits give up, the kernel returns,
+ *     and the step's outputs are undefined.
  */
-enum { FMM_STATUS_BAD_DENSITY = 1 };
+enum { FMM_STATUS_BAD_DENSITY = 1, FMM_STATUS_TIMEOUT = 2 };
 
 /* Wait for all work on the device, then store the status word's bits in
  * *status and, if `clear` is nonzero, clear them.  Not for use during stream
- * capture.  Errors: FMM_ERR_INVALID_ARG (NULL, host-only tree), FMM_ERR_CUDA. */
+ * capture.  Returns FMM_ERR_TIMEOUT (with the bits stored) when
+ * FMM_STATUS_TIMEOUT is among them.  Errors: FMM_ERR_INVALID_ARG (NULL,
+ * host-only tree), FMM_ERR_CUDA. */
 int fmm_get_status(fmm_tree_t tree, int32_t *status, int clear);
 
 /*
@@ -377,6 +394,64 @@ int fmm_forces_noalloc(const int32_t *leaf_table, int64_t n_leaf, int64_t n_node
  */
 int fmm_check_conversions(const double *values, int64_t n, int32_t *mismatch,
                           fmm_stream_t stream);
+
+/*
+ * Self-consistent-field initial models (Sec. 3 and Sec. 4.2: the initial
+ * scenario is assembled with the self-consistent field technique alongside
+ * the FMM solver; the method is Hachisu's 1986 SCF).  Polytropes
+ * P = K rho^(1 + 1/n) in synchronous rotation about the z axis through the
+ * centre of mass: inside star i the enthalpy
+ *   H = (n + 1) K_i rho^(1/n) = C_i - Phi + Omega^2 w^2 / 2
+ * (w: distance from the axis) vanishes on the star's surface.
+ */
+typedef struct {
+    double n;                        /* polytropic index, > 0 */
+    double rho_max[2];               /* maximum density of star 1 (> 0) and star 2
+                                        (0: a single star) */
+    double point_a[3];               /* surface point of star 1 (H = 0 there) */
+    double point_b[3];               /* second surface point of star 1 (rotate only) */
+    double point_c[3];               /* surface point of star 2 */
+    double centre[2][3];             /* star i's cells: centre within r_lim[i] of
+                                        centre[i], on star i's side of x_split */
+    double r_lim[2];
+    double x_split;                  /* star 1: x < x_split, star 2: x >= x_split */
+    double rho_floor;                /* density outside the stars, >= 0 */
+    int32_t rotate;                  /* 1: Omega from H = 0 at A and B; 0: Omega = 0 */
+    int32_t reserved;
+} fmm_scf_params;
+
+typedef struct {
+    double omega2;                   /* Omega^2 of this iteration */
+    double C[2];                     /* C_1, C_2 */
+    double com[3];                   /* centre of mass of the input density */
+    double H_max[2];                 /* each star's largest enthalpy (K_i = H_max,i /
+                                        ((n + 1) rho_max,i^(1/n))) */
+    double phi_points[3];            /* potential at the cells of A, B, C */
+    double mass;                     /* total mass of the input density */
+} fmm_scf_result;
+
+/*
+ * One SCF iteration after a solve of the same tree (e.g. fmm_step on rho):
+ *   phi:     device double [n_leaf][512], the potential of rho (read);
+ *   rho:     device double [n_leaf][512], the density that phi belongs to;
+ *   rho_out: device double [n_leaf][512], receives
+ *            rho_max,i (H / H_max,i)^n where H > 0 in star i, else rho_floor
+ *            (may be rho itself).
+ * The centre of mass is summed per leaf node on the device and over the
+ * nodes on the host in a fixed order; the surface conditions hold at the
+ * centres of the leaf cells containing A, B, C (w measured there); then
+ *   Omega^2 = 2 (Phi_A - Phi_B) / (w_A^2 - w_B^2)   (0 unless rotate),
+ *   C_1 = Phi_A - Omega^2 w_A^2 / 2,  C_2 = Phi_C - Omega^2 w_C^2 / 2.
+ * Synchronises `stream` twice (the scalars need the potential at three cells
+ * and the per-node sums); the density kernel is left enqueued.  Uses the
+ * tree's workspace: do not overlap it with other calls on the tree.
+ * Errors: FMM_ERR_INVALID_ARG (NULL, host-only tree, a batch of several
+ * trees, parameters out of range, a point outside every leaf node, no
+ * positive mass, a star with no positive enthalpy), FMM_ERR_CUDA.
+ */
+int fmm_scf_update(fmm_tree_t tree, const fmm_scf_params *params, const double *phi,
+                   const double *rho, double *rho_out, fmm_scf_result *out,
+                   fmm_stream_t stream);
 
 /*
  * fmm_peak_rate -- diagnostic, no counterpart in the paper: the denominators

@@ -20,7 +20,8 @@ One iteration, from a density rho:
   1. Phi: the FMM potential of rho at every leaf cell (``oracle.solve``);
   2. X: the centre of mass of rho (cell masses rho h^3 at cell centres);
   3. from H = 0 at two surface points A, B of star 1 and one point C of
-     star 2 (the leaf cells containing them; w measured from X):
+     star 2 (at the centres of the leaf cells containing them, where the
+     potential is known; w measured from X):
         Omega^2 = 2 (Phi_A - Phi_B) / (w_A^2 - w_B^2),
         C_1 = Phi_A - Omega^2 w_A^2 / 2,   C_2 = Phi_C - Omega^2 w_C^2 / 2;
      a static model (``rotate`` false) has Omega^2 = 0 and needs A and C only;
@@ -79,8 +80,8 @@ def iterate(c, rho, params):
     """One SCF iteration of the workload ``c`` (tree and solve parameters)
     from the density ``rho`` [n_leaf, 512].  ``params``: dict with n,
     rho_max (2), point_a, point_b, point_c (3-vectors), x_split, centre
-    (two 3-vectors), r_lim (2), rho_floor, rotate.  Returns (rho', info) with info = omega2, C (2), com, H_max (2),
-    phi."""
+    (two 3-vectors), r_lim (2), rho_floor, rotate.  Returns (rho', info)
+    with info = omega2, C (2), com, H_max (2), phi."""
     tree = O.Tree.from_config(c)
     phi = O.solve(tree, rho)["phi"]
     pos, vol = leaf_cell_geometry(c["desc"], c["box_lo"], c["box_size"])

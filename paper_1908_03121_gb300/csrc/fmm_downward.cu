@@ -526,6 +526,115 @@ __global__ void __launch_bounds__(kForceThreads, 12) leaf_finish_kernel(
     col.finish(row, partials);
 }
 
+// ---------------------------------------------------------------- dataflow
+// The downward pass as one persistent launch (the device-side counterpart of
+// the paper's futurized tree traversal, Sec. 4.1 and Sec. 5.1): CTAs pull
+// items from one queue -- every refined node's eight 64-cell slices, root
+// level first, then every leaf node, coarse levels first -- and an item
+// starts as soon as its parent's eight slices are done (a readiness counter
+// per node), rather than when the whole previous level's launch has ended.
+// Every item's producer sits earlier in the queue, and a CTA only waits
+// after it has dequeued its item, so the items it waits on were dequeued by
+// CTAs that are already running: progress does not depend on how many CTAs
+// are resident.  Each wait is bounded: past its budget it sets
+// FMM_STATUS_TIMEOUT and an abort flag that ends every later wait at once,
+// and the kernel returns (the step's outputs are then undefined).  The
+// arithmetic per cell is that of l2l_kernel and leaf_finish_kernel, so the
+// results are the same bits.
+struct DflowParams {
+    const NodeInfo *info;
+    const int32_t *items;
+    int32_t n_items, n_refined_items;
+    int32_t *head, *ready, *abort_flag, *status;
+    long long budget_ns;
+    const double *levels;
+    const dfloat *levels_df;
+    const void *L;
+    const float *Lc;
+    const double *dL1;
+    const double *com;
+    double *L64, *dacc;
+    float *down;
+    const double *M;
+    double *phi, *g, *partials;
+    double lo_x, lo_y, lo_z, box_size;
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// thread 0: wait until the node's eight slices are done; 0 if the wait gave
+// up (its budget ran out here, or another wait's did)
+__device__ int wait_node(const DflowParams &P, int node)
+{
+    if (ld_acquire(P.ready + node) >= 8) return 1;
+    const unsigned long long t0 = global_ns();
+    // the iteration cap bounds the wait even if the timer did not advance
+    for (int it = 0; it < (1 << 26); ++it) {
+        __nanosleep(128);
+        if (ld_acquire(P.ready + node) >= 8) return 1;
+        if (ld_acquire(P.abort_flag)) return 0;
+        if ((long long)(global_ns() - t0) > P.budget_ns) break;
+    }
+    atomicOr(P.status, FMM_STATUS_TIMEOUT);
+    atomicExch(P.abort_flag, 1);
+    return 0;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kForceThreads, 12) dataflow_kernel(DflowParams P)
+{
+    __shared__ int s_pos, s_go;
+    for (;;) {
+        __syncthreads();                 // the previous item's shared state is done with
+        if (threadIdx.x == 0) s_pos = atomicAdd(P.head, 1);
+        __syncthreads();
+        const int pos = s_pos;
+        if (pos >= P.n_items) break;
+        const bool refined = pos < P.n_refined_items;
+        const int it = P.items[pos];
+        const int node = refined ? it >> 3 : it;
+        const NodeInfo ni = P.info[node];
+        if (threadIdx.x == 0) s_go = ni.parent < 0 ? 1 : wait_node(P, ni.parent);
+        __syncthreads();
+        if (!s_go) continue;
+        if (refined) {
+            const int c = (it & 7) * kForceThreads + threadIdx.x;
+            double out[20], corr[3];
+            l2l_cell<MODE, 3>(P.info, ni, node, c, P.levels, P.levels_df, P.L, P.Lc, P.dL1, P.com,
+                              P.L64, P.dacc, P.down, P.lo_x, P.lo_y, P.lo_z, out, corr);
+            // publish: every thread's stores, then the counter
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(P.ready + node, 1);
+        } else {
+            const int row = ni.leaf_row;
+            ForceColumn col(ni, P.levels, P.box_size);
+#pragma unroll
+            for (int z = 0; z < 8; ++z) {
+                const int c = threadIdx.x + 64 * z;
+                double out[20], corr[3];
+                l2l_cell<MODE, 1>(P.info, ni, node, c, P.levels, P.levels_df, P.L, P.Lc, P.dL1,
+                                  P.com, P.L64, P.dacc, P.down, P.lo_x, P.lo_y, P.lo_z, out, corr);
+                col.cell(row, c, z, P.M[(size_t(node) * NCOMP) * NCELL + c], out[0], out + 1, corr,
+                         P.phi, P.g);
+            }
+            col.finish(row, P.partials);
+        }
+    }
+}
+
 // Per-tree sums of the per-leaf-node partials in two fixed-order stages, so
 // the FP64 adds spread over many SMs: chunks of kReduceRows leaf rows per CTA,
 // then one warp per tree over its chunks.
@@ -615,6 +724,62 @@ cudaError_t launch_leaf_finish(const fmm_tree_s *t, const void *L, const float *
             t->dev.info, nodes, t->dev.levels, ldf, L, Lc, dL1, com, L64, dacc, nullptr, M, phi,
             g, t->dev.partials, c.box_lo[0], c.box_lo[1], c.box_lo[2], c.box_size);
     return cudaGetLastError();
+}
+
+cudaError_t launch_downward_dataflow(const fmm_tree_s *t, const void *L, const float *Lc,
+                                     const double *dL1, const double *com, double *L64,
+                                     double *dacc, const double *M, double *phi, double *g,
+                                     cudaStream_t s)
+{
+    const Plan &Pl = t->plan;
+    if (Pl.dflow_items == 0) return cudaSuccess;
+    const auto &c = t->cfg;
+    DflowParams P{};
+    P.info = t->dev.info;
+    // the test injection leaves the first refined node's eight items out
+    const int drop = (t->tuning.drop_first_producer && Pl.dflow_refined_items >= 8) ? 8 : 0;
+    P.items = t->dev.dflow_items + drop;
+    P.n_items = int32_t(Pl.dflow_items - drop);
+    P.n_refined_items = int32_t(Pl.dflow_refined_items - drop);
+    P.head = t->dev.counters + kDflowHeadSlot;
+    P.abort_flag = t->dev.counters + kDflowAbortSlot;
+    P.status = t->dev.counters + kStatusSlot;
+    P.ready = t->dev.dflow_ready;
+    P.budget_ns = t->tuning.wait_budget_us > 0 ? 1000ll * t->tuning.wait_budget_us
+                                               : kDefaultWaitBudgetNs;
+    P.levels = t->dev.levels;
+    P.levels_df = reinterpret_cast<const dfloat *>(t->dev.levels_df);
+    P.L = L;
+    P.Lc = Lc;
+    P.dL1 = dL1;
+    P.com = com;
+    P.L64 = L64;
+    P.dacc = dacc;
+    P.down = t->dev.down;
+    P.M = M;
+    P.phi = phi;
+    P.g = g;
+    P.partials = t->dev.partials;
+    P.lo_x = c.box_lo[0];
+    P.lo_y = c.box_lo[1];
+    P.lo_z = c.box_lo[2];
+    P.box_size = c.box_size;
+    cudaError_t e = cudaMemsetAsync(t->dev.dflow_ready, 0, size_t(t->n) * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.head, 0, 2 * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    auto launch = [&](auto kern) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kForceThreads, 0) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const int64_t cap = int64_t(per_sm) * sm_count_of_current_device();
+        const unsigned grid = unsigned(P.n_items < cap ? P.n_items : cap);
+        kern<<<grid, kForceThreads, 0, s>>>(P);
+        return cudaGetLastError();
+    };
+    if (c.precision == FMM_MIXED) return launch(dataflow_kernel<FMM_MIXED>);
+    if (c.precision == FMM_DFLOAT) return launch(dataflow_kernel<FMM_DFLOAT>);
+    return launch(dataflow_kernel<FMM_FP64>);
 }
 
 cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *dacc,

@@ -398,6 +398,28 @@ static void build_mx_pairs(fmm_tree_s *t, const std::vector<int32_t> &mx_nodes)
     t->plan.n_mx_targets = int64_t(targets.size());
 }
 
+// The dataflow downward queue: every refined node's eight slices, levels
+// from the root down, then every leaf node, coarse levels first, so that each
+// item's parent comes earlier in the queue.
+static void plan_dataflow(fmm_tree_s *t)
+{
+    std::vector<int32_t> &q = t->dflow_items;
+    q.clear();
+    for (int lev = 1; lev <= t->max_level; ++lev)
+        for (int64_t i = 0; i < t->n; ++i) {
+            const NodeInfo &x = t->info[size_t(i)];
+            if (x.level == lev && x.leaf_row < 0)
+                for (int sl = 0; sl < 8; ++sl) q.push_back(int32_t(i * 8 + sl));
+        }
+    t->plan.dflow_refined_items = int64_t(q.size());
+    for (int lev = 1; lev <= t->max_level; ++lev)
+        for (int64_t i = 0; i < t->n; ++i) {
+            const NodeInfo &x = t->info[size_t(i)];
+            if (x.level == lev && x.leaf_row >= 0) q.push_back(int32_t(i));
+        }
+    t->plan.dflow_items = int64_t(q.size());
+}
+
 static void plan_work(fmm_tree_s *t)
 {
     Plan &P = t->plan;
@@ -532,7 +554,8 @@ static void free_device(fmm_tree_s *t)
     DeviceTables &d = t->dev;
     void *ptrs[] = {d.info, d.children, d.nbr, d.lists, d.stencil, d.stencil_f, d.coef32, d.coef64, d.coefdf, d.mono_woff,
                     d.tree_leaf_off, d.tree_leaf_rows, d.levels, d.levels_df, d.mass, d.mp, d.counters,
-                    d.partials, d.chunk_sums, d.up, d.down, d.mx_targets, d.mx_pairs};
+                    d.partials, d.chunk_sums, d.up, d.down, d.mx_targets, d.mx_pairs,
+                    d.dflow_items, d.dflow_ready};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceTables{};
@@ -552,7 +575,8 @@ static int upload_tree(fmm_tree_s *t)
         (rc = upload(&d.tree_leaf_rows, t->tree_leaf_rows)) || (rc = upload(&d.levels, t->levels)) ||
         (rc = upload(&d.levels_df, t->levels_df)) ||
         (rc = upload(reinterpret_cast<int32_t **>(&d.mx_targets), t->mx_targets)) ||
-        (rc = upload(reinterpret_cast<int32_t **>(&d.mx_pairs), t->mx_pairs)))
+        (rc = upload(reinterpret_cast<int32_t **>(&d.mx_pairs), t->mx_pairs)) ||
+        (rc = upload(&d.dflow_items, t->dflow_items)))
         return rc;
     // packed masses and moments: float (mixed), (hi, lo) float pairs (dfloat), double
     size_t es = t->cfg.precision == FMM_MIXED ? sizeof(float) : 2 * sizeof(float);
@@ -566,9 +590,12 @@ static int upload_tree(fmm_tree_s *t)
         (e = cudaMalloc(&d.mp, mp_b)) != cudaSuccess ||
         (e = cudaMalloc(reinterpret_cast<void **>(&d.counters), 64 * sizeof(int32_t))) != cudaSuccess ||
         (e = cudaMalloc(reinterpret_cast<void **>(&d.partials), part_b)) != cudaSuccess ||
-        (e = cudaMalloc(reinterpret_cast<void **>(&d.chunk_sums), chunk_b)) != cudaSuccess)
+        (e = cudaMalloc(reinterpret_cast<void **>(&d.chunk_sums), chunk_b)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void **>(&d.dflow_ready), size_t(t->n) * sizeof(int32_t))) !=
+            cudaSuccess)
         return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
-    d.workspace_bytes = mass_b + mp_b + part_b + chunk_b + 64 * sizeof(int32_t);
+    d.workspace_bytes = mass_b + mp_b + part_b + chunk_b + 64 * sizeof(int32_t) +
+                        size_t(t->n) * sizeof(int32_t);
     // work queues and the status word start at zero
     if ((e = cudaMemset(d.counters, 0, 64 * sizeof(int32_t))) != cudaSuccess)
         return cuda_fail(e, "cudaMemset");
@@ -684,6 +711,7 @@ int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config
     }
     build_stencils(t);
     plan_work(t);
+    plan_dataflow(t);
     // per-level geometry: h = box / (8 * 2^(l-1)) is exact up to the box edge
     t->levels.assign(size_t(t->max_level + 1) * LEVEL_FIELDS, 0.0);
     for (int lev = 1; lev <= t->max_level; ++lev) {
@@ -944,6 +972,15 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
     FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_ROOT), "m2l launch");
     FMM_STEP_TRY(cudaEventRecord(ev[4], a), "cudaEventRecord");
     FMM_STEP_TRY(cudaStreamWaitEvent(s, ev[4], 0), "cudaStreamWaitEvent");
+    if (t->tuning.dataflow) {
+        // main: the refined shifts and the leaf pass in one persistent
+        // launch, each item started by its parent's readiness counter; the
+        // sums
+        FMM_STEP_TRY(launch_downward_dataflow(t, L, L_comp, dL1, com, L64, dL1_acc, M, phi, g, s),
+                     "dataflow launch");
+        FMM_STEP_TRY(launch_force_sums(t, totals, s), "reduce launch");
+        return FMM_OK;
+    }
     // main: shifts of the refined nodes, root level first
     for (int lev = 1; lev <= t->max_level; ++lev)
         FMM_STEP_TRY(launch_l2l_nodes(t, P.refined_at[size_t(lev)], L, L_comp, dL1, com, L64,
@@ -978,6 +1015,10 @@ int fmm_set_tuning(fmm_tree_t t, const fmm_tuning *tu)
         return fail(FMM_ERR_INVALID_ARG, "mono_subgrids must be 0, 1, 2 or 4");
     if (tu->ctas_per_sm < 0 || tu->ctas_per_sm > 32)
         return fail(FMM_ERR_INVALID_ARG, "ctas_per_sm must lie in 0..32");
+    if (tu->dataflow < 0 || tu->dataflow > 1 || tu->drop_first_producer < 0 ||
+        tu->drop_first_producer > 1 || tu->wait_budget_us < 0)
+        return fail(FMM_ERR_INVALID_ARG, "dataflow and drop_first_producer must be 0 or 1, "
+                                         "wait_budget_us not negative");
     t->tuning = *tu;
     return FMM_OK;
 }
@@ -1001,6 +1042,8 @@ int fmm_get_status(fmm_tree_t t, int32_t *status, int clear)
         return cuda_fail(e, "cudaMemcpy");
     if (clear && (e = cudaMemset(word, 0, sizeof(int32_t))) != cudaSuccess)
         return cuda_fail(e, "cudaMemset");
+    if (*status & FMM_STATUS_TIMEOUT)
+        return fail(FMM_ERR_TIMEOUT, "a device-side wait of the dataflow pass ran out of budget");
     return FMM_OK;
 }
 

@@ -94,6 +94,10 @@ struct DeviceTables {
     double *chunk_sums = nullptr;    // [n_trees][reduce_chunks][8]
     float *up = nullptr;             // mixed, dfloat: [n_refined][20][512] double-float
                                      // (hi, lo) results of the upward pass per refined cell
+    int32_t *dflow_items = nullptr;  // dataflow downward queue: refined (node, slice) items
+                                     // node * 8 + slice, root level first, then leaf nodes
+                                     // by level
+    int32_t *dflow_ready = nullptr;  // [n]: slices of the node's shift completed this step
     float *down = nullptr;           // mixed: [n_refined][23][512] float copy, double-
                                      // float: the same as (hi, lo) pairs, of each refined
                                      // cell's final expansion (20) and centre-of-mass
@@ -105,6 +109,11 @@ struct DeviceTables {
 // the slot of DeviceTables::counters that holds the status word (the work
 // queues use slots 0-3, which every step resets)
 constexpr int kStatusSlot = 8;
+// the dataflow downward pass's queue head and abort flag (reset every step)
+constexpr int kDflowHeadSlot = 16;
+constexpr int kDflowAbortSlot = 17;
+// default budget of one device-side wait of the dataflow pass
+constexpr long long kDefaultWaitBudgetNs = 1000000000ll;
 
 struct ListRange {
     int64_t off = 0, count = 0;
@@ -128,6 +137,8 @@ struct Plan {
     ListRange work_mp, work_mono, work_mx, roots;
     ListRange refined;                    // every refined node (roots included)
     int64_t n_mx_targets = 0;             // leaf cells with refined sources
+    int64_t dflow_refined_items = 0;      // refined (node, slice) items of the dataflow queue
+    int64_t dflow_items = 0;              // all its items (the leaf nodes after them)
     int64_t interactions[4] = {0, 0, 0, 0};
     int64_t kernel_interactions[4] = {0, 0, 0, 0};  // multipole, monopole, mono<-multi, root
 };
@@ -163,6 +174,7 @@ struct fmm_tree_s {
     std::vector<float> levels_df;
     std::vector<int32_t> mx_targets;     // [n_mx_targets][4]: node, cell, pair offset, count
     std::vector<int32_t> mx_pairs;       // [pairs][2]: packed-moment offset, stencil entry
+    std::vector<int32_t> dflow_items;    // the dataflow downward queue (DeviceTables)
     fmm::Plan plan;
     fmm_tuning tuning{};
     bool host_only = false;
@@ -201,6 +213,12 @@ cudaError_t launch_leaf_finish(const fmm_tree_s *t, const void *L, const float *
                                const double *dL1, const double *com, double *L64, double *dacc,
                                const double *M, double *phi, double *g, cudaStream_t s);
 cudaError_t launch_force_sums(const fmm_tree_s *t, double *totals, cudaStream_t s);
+// the refined levels' shifts and every leaf's shift and forces in one
+// persistent launch ordered by per-node readiness counters
+cudaError_t launch_downward_dataflow(const fmm_tree_s *t, const void *L, const float *Lc,
+                                     const double *dL1, const double *com, double *L64,
+                                     double *dacc, const double *M, double *phi, double *g,
+                                     cudaStream_t s);
 cudaError_t launch_forces(const fmm_tree_s *t, const double *L64, const double *dacc,
                           const double *rho, double *phi, double *g, double *totals,
                           cudaStream_t s);

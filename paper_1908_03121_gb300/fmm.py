@@ -25,6 +25,7 @@ FMM_MIXED = 1
 FMM_DFLOAT = 2
 PRECISIONS = {"fp64": FMM_FP64, "mixed": FMM_MIXED, "dfloat": FMM_DFLOAT}
 FMM_STATUS_BAD_DENSITY = 1
+FMM_STATUS_TIMEOUT = 2
 FMM_FLAG_HOST_ONLY = 1
 FMM_FLAG_TIMING = 2
 KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_multi", "l2l",
@@ -32,8 +33,8 @@ KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_mul
 
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
             "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_step", "fmm_set_tuning", "fmm_get_tuning",
-            "fmm_forces_noalloc", "fmm_check_conversions", "fmm_peak_rate", "fmm_get_status",
-            "fmm_destroy_tree", "fmm_last_error")
+            "fmm_forces_noalloc", "fmm_check_conversions", "fmm_peak_rate", "fmm_scf_update",
+            "fmm_get_status", "fmm_destroy_tree", "fmm_last_error")
 
 NCELL = 512
 NCOMP = 20
@@ -75,7 +76,27 @@ class FmmStats(ctypes.Structure):
 
 class FmmTuning(ctypes.Structure):
     _fields_ = [("mono_subgrids", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("dataflow", ctypes.c_int32), ("wait_budget_us", ctypes.c_int32),
+                ("drop_first_producer", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+TUNING_KEYS = ("mono_subgrids", "ctas_per_sm", "dataflow", "wait_budget_us",
+               "drop_first_producer")
+
+
+class FmmScfParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_double), ("rho_max", ctypes.c_double * 2),
+                ("point_a", ctypes.c_double * 3), ("point_b", ctypes.c_double * 3),
+                ("point_c", ctypes.c_double * 3), ("centre", (ctypes.c_double * 3) * 2),
+                ("r_lim", ctypes.c_double * 2), ("x_split", ctypes.c_double),
+                ("rho_floor", ctypes.c_double), ("rotate", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class FmmScfResult(ctypes.Structure):
+    _fields_ = [("omega2", ctypes.c_double), ("C", ctypes.c_double * 2),
+                ("com", ctypes.c_double * 3), ("H_max", ctypes.c_double * 2),
+                ("phi_points", ctypes.c_double * 3), ("mass", ctypes.c_double)]
 
 
 _LOCK = threading.Lock()
@@ -111,6 +132,8 @@ def load(build=True):
         lib.fmm_check_conversions.argtypes = [P, ctypes.c_int64, P, P]
         lib.fmm_peak_rate.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, P,
                                       ctypes.POINTER(ctypes.c_double), P]
+        lib.fmm_scf_update.argtypes = [P, ctypes.POINTER(FmmScfParams), P, P, P,
+                                       ctypes.POINTER(FmmScfResult), P]
         lib.fmm_set_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_get_tuning.argtypes = [P, ctypes.POINTER(FmmTuning)]
         lib.fmm_get_status.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
@@ -271,15 +294,46 @@ def fmm_peak_rate(kind, iters, blocks_per_sm, sink, stream=None):
     return fl.value
 
 
-def fmm_set_tuning(tree, mono_subgrids=0, ctas_per_sm=0):
-    t = FmmTuning(int(mono_subgrids), int(ctas_per_sm))
+def scf_params(n, rho_max, point_a, point_c, centre, r_lim, x_split, point_b=(0.0, 0.0, 0.0),
+               rho_floor=1e-10, rotate=True):
+    """An fmm_scf_params structure (see include/fmm_gb300.h)."""
+    p = FmmScfParams()
+    p.n = float(n)
+    p.rho_max[:] = [float(v) for v in rho_max]
+    p.point_a[:] = [float(v) for v in point_a]
+    p.point_b[:] = [float(v) for v in point_b]
+    p.point_c[:] = [float(v) for v in point_c]
+    for i in range(2):
+        p.centre[i][:] = [float(v) for v in centre[i]]
+    p.r_lim[:] = [float(v) for v in r_lim]
+    p.x_split = float(x_split)
+    p.rho_floor = float(rho_floor)
+    p.rotate = 1 if rotate else 0
+    return p
+
+
+def fmm_scf_update(tree, params, phi, rho, rho_out, stream=None):
+    """One self-consistent-field iteration's density update after a solve of
+    ``tree`` (``phi`` the potential of ``rho``); returns the iteration's
+    scalars as a dict."""
+    r = FmmScfResult()
+    _check(load().fmm_scf_update(tree.handle, ctypes.byref(params), _ptr(phi), _ptr(rho),
+                                 _ptr(rho_out), ctypes.byref(r), _stream(stream)))
+    return {"omega2": r.omega2, "C": tuple(r.C), "com": tuple(r.com), "H_max": tuple(r.H_max),
+            "phi_points": tuple(r.phi_points), "mass": r.mass}
+
+
+def fmm_set_tuning(tree, mono_subgrids=0, ctas_per_sm=0, dataflow=0, wait_budget_us=0,
+                   drop_first_producer=0):
+    t = FmmTuning(int(mono_subgrids), int(ctas_per_sm), int(dataflow), int(wait_budget_us),
+                  int(drop_first_producer))
     _check(load().fmm_set_tuning(tree.handle, ctypes.byref(t)))
 
 
 def fmm_get_tuning(tree):
     t = FmmTuning()
     _check(load().fmm_get_tuning(tree.handle, ctypes.byref(t)))
-    return {"mono_subgrids": t.mono_subgrids, "ctas_per_sm": t.ctas_per_sm}
+    return {k: getattr(t, k) for k in TUNING_KEYS}
 
 
 def fmm_get_status(tree, clear=True):

@@ -44,6 +44,29 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(B.FmmStats) == 8 * 4 + 8 * 3 + 8 * 4 + 8 * 4 + 8 * 4 + 4 * 6 + 8 * 16 + 8 * 16
 
 
+def test_struct_sizes_match_the_c_compiler(tmp_path):
+    """The binding's structures have the sizes the C compiler gives the
+    header's (a layout drift would pass garbage through the ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = ["fmm_config", "fmm_node_desc", "fmm_sizes", "fmm_stats", "fmm_tuning",
+             "fmm_scf_params", "fmm_scf_result"]
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "fmm_gb300.h"\nint main(void){\n' +
+                   "".join(f'printf("%zu\\n", sizeof({n}));\n' for n in names) + "return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    ours = [ctypes.sizeof(B.FmmConfig), 14 * 4, ctypes.sizeof(B.FmmSizes),
+            ctypes.sizeof(B.FmmStats), ctypes.sizeof(B.FmmTuning),
+            ctypes.sizeof(B.FmmScfParams), ctypes.sizeof(B.FmmScfResult)]
+    assert got == ours
+
+
 def plan(desc, theta):
     return F.fmm_build_tree(desc, theta, host_only=True)
 
@@ -190,14 +213,20 @@ def test_tuning_set_get_and_validation():
     """fmm_set_tuning keeps valid launch shapes, refuses the others and then
     leaves the previous tuning in place (host-only tree: no CUDA)."""
     t = plan(uniform_tree(2), 0.5)
-    assert F.fmm_get_tuning(t) == {"mono_subgrids": 0, "ctas_per_sm": 0}
-    F.fmm_set_tuning(t, mono_subgrids=2, ctas_per_sm=1)
-    assert F.fmm_get_tuning(t) == {"mono_subgrids": 2, "ctas_per_sm": 1}
-    for nb, cap in ((3, 0), (5, 0), (-1, 0), (1, 33), (1, -1)):
+    zero = dict(mono_subgrids=0, ctas_per_sm=0, dataflow=0, wait_budget_us=0,
+                drop_first_producer=0)
+    assert F.fmm_get_tuning(t) == zero
+    good = dict(zero, mono_subgrids=2, ctas_per_sm=1, dataflow=1, wait_budget_us=500)
+    F.fmm_set_tuning(t, **{k: v for k, v in good.items()})
+    assert F.fmm_get_tuning(t) == good
+    bad = [dict(mono_subgrids=3), dict(mono_subgrids=5), dict(mono_subgrids=-1),
+           dict(ctas_per_sm=33), dict(ctas_per_sm=-1), dict(dataflow=2), dict(dataflow=-1),
+           dict(wait_budget_us=-5), dict(drop_first_producer=2)]
+    for b in bad:
         with pytest.raises(F.FmmError) as ei:
-            F.fmm_set_tuning(t, mono_subgrids=nb, ctas_per_sm=cap)
+            F.fmm_set_tuning(t, **b)
         assert ei.value.code == B.FMM_ERR_INVALID_ARG
-        assert F.fmm_get_tuning(t) == {"mono_subgrids": 2, "ctas_per_sm": 1}
+        assert F.fmm_get_tuning(t) == good
     for nb in (0, 1, 2, 4):
         F.fmm_set_tuning(t, mono_subgrids=nb, ctas_per_sm=32)
-        assert F.fmm_get_tuning(t) == {"mono_subgrids": nb, "ctas_per_sm": 32}
+        assert F.fmm_get_tuning(t) == dict(zero, mono_subgrids=nb, ctas_per_sm=32)

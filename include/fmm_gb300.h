@@ -291,7 +291,10 @@ typedef struct {
     int32_t drop_first_producer;     /* test injection, host side: the dataflow queue
                                         leaves out the first node's items, so the waits
                                         on it run out (0 in normal use) */
-    int32_t reserved[3];
+    int32_t mp_pair_targets;         /* FMM_MIXED: 1 walks each thread's two multipole
+                                        target cells through the stencil together
+                                        (same results, more work in flight) */
+    int32_t reserved[2];
 } fmm_tuning;
 
 /* Set / read the tree's tuning (host, immediate; affects later launches).

@@ -4,7 +4,8 @@ Times whole solve steps (``Solver.step``: the passes overlapped on two streams,
 so co-resident kernels share SMs as they will in the real step) on the
 caller's tree for every candidate of
 ``fmm_tuning`` (sub-grids per pass of the monopole kernel, persistent CTAs per
-SM, the dataflow downward pass or the level-by-level one) with CUDA events on the current stream, keeps the fastest and leaves it
+SM, the dataflow downward pass or the level-by-level one, one or two multipole
+target cells per thread in flight) with CUDA events on the current stream, keeps the fastest and leaves it
 set on the tree.  Each candidate is run ``reps`` times after one warm-up; the
 median decides.  Results are cached per tree size and precision for the
 process.
@@ -19,6 +20,7 @@ from . import fmm as B
 MONO_SUBGRIDS = (1, 2, 4)
 CTAS_PER_SM = (0, 1, 2)
 DATAFLOW = (0, 1)
+PAIR_TARGETS = (0, 1)
 _CACHE = {}
 
 
@@ -35,9 +37,10 @@ def tune(solver, reps=5, verbose=False):
         B.fmm_set_tuning(solver.tree, **_CACHE[key][0])
         return _CACHE[key]
     mixed = solver.mixed
-    candidates = [dict(mono_subgrids=nb, ctas_per_sm=cap, dataflow=df)
-                  for nb, cap, df in itertools.product(MONO_SUBGRIDS, CTAS_PER_SM, DATAFLOW)
-                  if mixed or nb != 4]
+    candidates = [dict(mono_subgrids=nb, ctas_per_sm=cap, dataflow=df, mp_pair_targets=pt)
+                  for nb, cap, df, pt in itertools.product(MONO_SUBGRIDS, CTAS_PER_SM, DATAFLOW,
+                                                           PAIR_TARGETS)
+                  if mixed or (nb != 4 and pt == 0)]
     stream = torch.cuda.current_stream()
     results = []
     for cand in candidates:

@@ -512,16 +512,26 @@ static void plan_work(fmm_tree_s *t)
     build_mx_pairs(t, mx);
     P.refined = push_range(refined);
     P.refined_at.assign(size_t(t->max_level) + 2, {});
+    P.leafkids_at.assign(size_t(t->max_level) + 2, {});
+    P.mixedkids_at.assign(size_t(t->max_level) + 2, {});
     P.nodes_at.assign(size_t(t->max_level) + 2, {});
     for (int lev = 1; lev <= t->max_level; ++lev) {
-        std::vector<int32_t> ref, all;
+        std::vector<int32_t> ref, all, leafkids, mixedkids;
         for (int64_t i = 0; i < n; ++i) {
             const NodeInfo &x = t->info[size_t(i)];
             if (x.level != lev) continue;
             all.push_back(int32_t(i));
-            if (x.leaf_row < 0) ref.push_back(int32_t(i));
+            if (x.leaf_row >= 0) continue;
+            ref.push_back(int32_t(i));
+            bool kids_leaves = true;
+            for (int k = 0; k < 8; ++k)
+                kids_leaves = kids_leaves &&
+                              t->info[size_t(t->children[size_t(i) * 8 + k])].leaf_row >= 0;
+            (kids_leaves ? leafkids : mixedkids).push_back(int32_t(i));
         }
         P.refined_at[size_t(lev)] = push_range(ref);
+        P.leafkids_at[size_t(lev)] = push_range(leafkids);
+        P.mixedkids_at[size_t(lev)] = push_range(mixedkids);
         P.nodes_at[size_t(lev)] = push_range(all);
     }
 }
@@ -1016,9 +1026,10 @@ int fmm_set_tuning(fmm_tree_t t, const fmm_tuning *tu)
     if (tu->ctas_per_sm < 0 || tu->ctas_per_sm > 32)
         return fail(FMM_ERR_INVALID_ARG, "ctas_per_sm must lie in 0..32");
     if (tu->dataflow < 0 || tu->dataflow > 1 || tu->drop_first_producer < 0 ||
-        tu->drop_first_producer > 1 || tu->wait_budget_us < 0)
-        return fail(FMM_ERR_INVALID_ARG, "dataflow and drop_first_producer must be 0 or 1, "
-                                         "wait_budget_us not negative");
+        tu->drop_first_producer > 1 || tu->wait_budget_us < 0 || tu->mp_pair_targets < 0 ||
+        tu->mp_pair_targets > 1)
+        return fail(FMM_ERR_INVALID_ARG, "dataflow, drop_first_producer and mp_pair_targets "
+                                         "must be 0 or 1, wait_budget_us not negative");
     t->tuning = *tu;
     return FMM_OK;
 }

@@ -133,6 +133,8 @@ struct Plan {
     // node lists
     ListRange leaves;                // all leaf nodes (P2M, forces)
     std::vector<ListRange> refined_at;   // [level] refined nodes (M2M)
+    std::vector<ListRange> leafkids_at;  // [level] refined nodes whose 8 children are leaves
+    std::vector<ListRange> mixedkids_at; // [level] the other refined nodes
     std::vector<ListRange> nodes_at;     // [level] all nodes (L2L)
     ListRange work_mp, work_mono, work_mx, roots;
     ListRange refined;                    // every refined node (roots included)

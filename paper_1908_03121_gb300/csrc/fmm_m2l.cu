@@ -826,6 +826,125 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
     }
 }
 
+// ----------------------------------------------------------- mp2_kernel
+// The multipole kernel (float) with each thread's two target cells (z and
+// z + 4 of one parity) walked through the stencil together instead of one
+// after the other: one stencil-entry load serves both, and the two cells'
+// independent loads and arithmetic interleave, so each warp has twice the
+// work in flight between its dependent steps.  Two CTAs per SM (at most 128
+// registers) and both cells' compensation pairs in shared memory.  Every
+// cell's operations and their order are those of mp_kernel, so the results
+// are the same bits.
+constexpr int kMp2Pairs = 2 * kMpPairs;
+
+__device__ __forceinline__ void mp2_source(const KParams &P, const float *mp, float wv, Src<float> &src)
+{
+    // masses are not negative, so a mass's decoded offset is out of range
+    const unsigned idx = unsigned(-1 - __float_as_int(wv));
+    if (idx < unsigned(P.mp_limit)) {
+        load_source_at<float>(mp + idx, src);
+    } else {
+        src.m0 = wv;
+        zero_moments<float>(src);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) mp2_kernel(KParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *W = reinterpret_cast<float *>(smem_raw);
+    float *Cs = W + 8 * P.sub_stride + threadIdx.x;
+    __shared__ int s_nbr[27], s_leaf[27], s_row[27], s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = warp;
+    const int px = p & 1, py = (p >> 1) & 1, pz = p >> 2;
+    const int cx = lane & 3, cy = (lane >> 2) & 3, cz0 = lane >> 4;
+    const float4 *ent = P.stencil_f + p * P.ent_stride;
+    const float *mass = static_cast<const float *>(P.mass);
+    const float *mp = static_cast<const float *>(P.mp);
+    for (;;) {
+        const int item = pull_item(P.counter, &s_item);
+        if (item >= P.n_items) break;
+        const int node = P.list[item];
+        const NodeInfo ti = P.info[node];
+        load_slots(node, P, s_nbr, s_leaf, s_row);
+        __syncthreads();
+        stage_window_async<float>(W, s_nbr, s_leaf, mass, P, s_row);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        const int ax = 2 * cx + px, ay = 2 * cy + py;
+        const int az0 = 2 * cz0 + pz, az1 = az0 + 4;
+        const int base0 = cx + P.py * cy + P.pz * cz0, base1 = base0 + 2 * P.pz;
+        float dA0[3], a3A0[7], dA1[3], a3A1[7];
+        load_target<float>(P, ti.mp_row, parity_index(ax, ay, az0), dA0, a3A0);
+        load_target<float>(P, ti.mp_row, parity_index(ax, ay, az1), dA1, a3A1);
+        MpAcc<float, 16>::type L0, L1;
+        MpAcc<float, 3>::type S0, S1;
+        L0.col = Cs;
+        S0.col = Cs + 4 * 2 * kThreads;
+        L1.col = Cs + kMpPairs * 2 * kThreads;
+        S1.col = Cs + (kMpPairs + 4) * 2 * kThreads;
+        L0.zero();
+        S0.zero();
+        L1.zero();
+        S1.zero();
+        for (int e0 = 0; e0 < P.n_far; e0 += kChunk) {
+            const int e1 = min(e0 + kChunk, P.n_far);
+            for (int e = e0; e < e1; ++e) {
+                const float4 E = __ldg(ent + e);
+                const int woff = __float_as_int(E.w);
+                Src<float> s0, s1;
+                mp2_source(P, mp, W[base0 + woff], s0);
+                mp2_source(P, mp, W[base1 + woff], s1);
+                acc_mp<float, true>(dA0[0] - s0.d[0] - E.x, dA0[1] - s0.d[1] - E.y,
+                                    dA0[2] - s0.d[2] - E.z, s0, a3A0, L0, S0);
+                acc_mp<float, true>(dA1[0] - s1.d[0] - E.x, dA1[1] - s1.d[1] - E.y,
+                                    dA1[2] - s1.d[2] - E.z, s1, a3A1, L1, S1);
+            }
+            L0.flush();
+            S0.flush();
+            L1.flush();
+            S1.flush();
+        }
+        for (int e0 = P.n_far; e0 < P.n_far + P.n_near; e0 += kChunk) {
+            const int e1 = min(e0 + kChunk, P.n_far + P.n_near);
+            for (int e = e0; e < e1; ++e) {
+                const float4 E = __ldg(ent + e);
+                const int woff = __float_as_int(E.w);
+                const float w0 = W[base0 + woff], w1 = W[base1 + woff];
+                Src<float> s0, s1;
+                s0.m0 = unsigned(-1 - __float_as_int(w0)) < unsigned(P.mp_limit) ? 0.f : w0;
+                s1.m0 = unsigned(-1 - __float_as_int(w1)) < unsigned(P.mp_limit) ? 0.f : w1;
+                acc_mp<float, false>(dA0[0] - E.x, dA0[1] - E.y, dA0[2] - E.z, s0, a3A0, L0, S0);
+                acc_mp<float, false>(dA1[0] - E.x, dA1[1] - E.y, dA1[2] - E.z, s1, a3A1, L1, S1);
+            }
+            L0.flush();
+            S0.flush();
+            L1.flush();
+            S1.flush();
+        }
+        const int cell0 = ax + 8 * ay + 64 * az0, cell1 = ax + 8 * ay + 64 * az1;
+        store_target<float>(P, node, cell0, L0);
+        store_target<float>(P, node, cell1, L1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            P.dL1[(size_t(node) * 3 + i) * NCELL + cell0] = acc_value<float>(S0, i);
+            P.dL1[(size_t(node) * 3 + i) * NCELL + cell1] = acc_value<float>(S1, i);
+        }
+        __syncthreads();
+    }
+    if (P.n_mx > 0) {
+        for (;;) {
+            int w = 0;
+            if (lane == 0) w = atomicAdd(P.mx_counter, 1);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (w * 32 >= P.n_mx) break;
+            if (w * 32 + lane < P.n_mx) mx_target<float>(P, w * 32 + lane);
+        }
+    }
+}
+
 // ---------------------------------------------------------- mono_kernel
 // Leaf target, leaf sources: R = -o exactly, so L0 += c0(o) m and
 // L1 += c1(o) m with per-offset weights c0 = -1/|o|, c1 = -o/|o|^3.
@@ -1105,6 +1224,11 @@ struct Kernels {
         static size_t done = 0;
         return allow_smem(mp_kernel<T>, bytes, done);
     }
+    static cudaError_t mp2(size_t bytes)
+    {
+        static size_t done = 0;
+        return allow_smem(mp2_kernel, bytes, done);
+    }
     template <int NB, int RR>
     static cudaError_t mono(size_t bytes)
     {
@@ -1220,9 +1344,17 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
             K.n_mx = int32_t(Pl.n_mx_targets);
             K.mx_counter = d.counters + Q_MX;
         }
-        int g = persistent_grid(mp_kernel<T>, mp_bytes, Pl.work_mp.count, sms, cap);
         timing_begin(t, FMM_K_MULTIPOLE, s);
-        mp_kernel<T><<<g, kThreads, mp_bytes, s>>>(K);
+        if (kF32<T> && t->tuning.mp_pair_targets) {
+            // both target cells of a thread together (float only)
+            const size_t b2 = wbytes + size_t(kMp2Pairs) * 2 * kThreads * sizeof(float);
+            if ((e = Kernels<T>::mp2(b2)) != cudaSuccess) return e;
+            int g = persistent_grid(mp2_kernel, b2, Pl.work_mp.count, sms, cap);
+            mp2_kernel<<<g, kThreads, b2, s>>>(K);
+        } else {
+            int g = persistent_grid(mp_kernel<T>, mp_bytes, Pl.work_mp.count, sms, cap);
+            mp_kernel<T><<<g, kThreads, mp_bytes, s>>>(K);
+        }
         timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

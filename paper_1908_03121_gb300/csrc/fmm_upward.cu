@@ -222,7 +222,13 @@ __device__ __forceinline__ void write_up(const NodeInfo &ni, int node, int c, in
     for (int t = 0; t < 10; ++t) ou[(10 + t) * NCELL] = M3[t];
 }
 
-// one thread per parent cell, 8 CTAs of 64 threads per node
+// one thread per parent cell, 8 CTAs of 64 threads per node.  LEAF_KIDS:
+// every child of the launch's nodes is a leaf (the deepest refined level,
+// the bulk of the upward pass's cells), so only the leaf-children branch is
+// compiled: far fewer registers than the general kernel, which lets the
+// launch share its SMs with the persistent monopole kernel that runs beside
+// the upward pass in fmm_step.
+template <bool LEAF_KIDS>
 __global__ void __launch_bounds__(kSliceThreads) m2m_df_kernel(const NodeInfo *__restrict__ info,
                                                                const int32_t *__restrict__ children,
                                                                const int32_t *__restrict__ nodes,
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(kSliceThreads) m2m_df_kernel(const NodeInfo *_
     const dfloat q = df_from_double(0.25 * hp);           // half a child cell width
     const int c0 = 2 * (x & 3) + 16 * (y & 3) + 128 * (z & 3);   // child cell of j = 0
     dfloat m0, d[3], M2[6], M3[10];
-    if (ci.leaf_row >= 0) {
+    if (LEAF_KIDS || ci.leaf_row >= 0) {
         // child j sits at ref + q (e_x, e_y, e_z), e = +-1 from the bits of j
         const size_t cbase = size_t(ch) * NCOMP * NCELL;
         dfloat m[8];
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(kSliceThreads) m2m_df_kernel(const NodeInfo *_
         const dfloat q3x = q3 * e[1], q3y = q3 * e[2], q3z = q3 * e[4];
         const dfloat S3[10] = {q3x, q3y, q3z, q3x, q3 * e[7], q3x, q3y, q3z, q3y, q3z};
         central_from_raw(m0, d, S2, S3, M2, M3);
-    } else {
+    } else if constexpr (!LEAF_KIDS) {
         const dfloat *cu = up + size_t(ci.mp_row) * 20 * NCELL;
         dfloat mj[8], X[8][3];
         m0 = dfloat(0.f);
@@ -439,8 +445,19 @@ cudaError_t launch_m2m_level(const fmm_tree_s *t, int level, double *M, double *
     const ListRange &r = t->plan.refined_at[size_t(level)];
     if (r.count == 0) return cudaSuccess;
     if (t->cfg.precision != FMM_FP64 && r.count >= kLanesBelow) {
-        m2m_df_kernel<<<unsigned(r.count * 8), kSliceThreads, 0, s>>>(
-            t->dev.info, t->dev.children, t->dev.lists + r.off, t->dev.levels, M, com,
+        // nodes with only leaf children through the lean kernel, the others
+        // through the general one
+        const ListRange &rl = t->plan.leafkids_at[size_t(level)];
+        const ListRange &rm = t->plan.mixedkids_at[size_t(level)];
+        if (rl.count)
+            m2m_df_kernel<true><<<unsigned(rl.count * 8), kSliceThreads, 0, s>>>(
+                t->dev.info, t->dev.children, t->dev.lists + rl.off, t->dev.levels, M, com,
+                reinterpret_cast<dfloat *>(t->dev.up), t->cfg.box_lo[0], t->cfg.box_lo[1],
+                t->cfg.box_lo[2]);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess || rm.count == 0) return e;
+        m2m_df_kernel<false><<<unsigned(rm.count * 8), kSliceThreads, 0, s>>>(
+            t->dev.info, t->dev.children, t->dev.lists + rm.off, t->dev.levels, M, com,
             reinterpret_cast<dfloat *>(t->dev.up), t->cfg.box_lo[0], t->cfg.box_lo[1],
             t->cfg.box_lo[2]);
         return cudaGetLastError();

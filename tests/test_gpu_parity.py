@@ -9,6 +9,8 @@ relative 1e-12 (1e-11 on the full-size samples) with net force and torque
 1e-12 of sum |f| and sum |x cross f|.
 """
 
+import itertools
+
 import numpy as np
 import pytest
 
@@ -474,22 +476,21 @@ def test_tunings_agree_bitwise(precision):
     c, _ = oracle_solution("adaptive4")
     s = solve_gpu(c, precision)
     ref = None
-    for nb in (1, 2, 4):
-        if precision != "mixed" and nb == 4:
+    for nb, cap, pair in itertools.product((1, 2, 4), (0, 1), (0, 1)):
+        if precision != "mixed" and (nb == 4 or pair):
             continue
-        for cap in (0, 1):
-            F.fmm_set_tuning(s.tree, mono_subgrids=nb, ctas_per_sm=cap)
-            got = F.fmm_get_tuning(s.tree)
-            assert (got["mono_subgrids"], got["ctas_per_sm"]) == (nb, cap)
-            s.L.zero_()
-            s.m2l()
-            torch.cuda.synchronize()
-            got = (host(s.L).copy(), None if s.Lc is None else host(s.Lc).copy(), host(s.dL1).copy())
-            if ref is None:
-                ref = got
-            else:
-                for a, b in zip(got, ref):
-                    assert a is None or np.array_equal(a, b)
+        F.fmm_set_tuning(s.tree, mono_subgrids=nb, ctas_per_sm=cap, mp_pair_targets=pair)
+        got = F.fmm_get_tuning(s.tree)
+        assert (got["mono_subgrids"], got["ctas_per_sm"], got["mp_pair_targets"]) == (nb, cap, pair)
+        s.L.zero_()
+        s.m2l()
+        torch.cuda.synchronize()
+        got = (host(s.L).copy(), None if s.Lc is None else host(s.Lc).copy(), host(s.dL1).copy())
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(got, ref):
+                assert a is None or np.array_equal(a, b)
     s.close()
 
 

@@ -438,8 +438,8 @@ typedef struct {
  *   phi:     device double [n_leaf][512], the potential of rho (read);
  *   rho:     device double [n_leaf][512], the density that phi belongs to;
  *   rho_out: device double [n_leaf][512], receives
- *            rho_max,i (H / H_max,i)^n where H > 0 in star i, else rho_floor
- *            (may be rho itself).
+ *            max(rho_floor, rho_max,i (H / H_max,i)^n) where H > 0 in star i,
+ *            else rho_floor (may be rho itself).
  * The centre of mass is summed per leaf node on the device and over the
  * nodes on the host in a fixed order; the surface conditions hold at the
  * centres of the leaf cells containing A, B, C (w measured there); then

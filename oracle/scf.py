@@ -31,8 +31,16 @@ One iteration, from a density rho:
      (a reading: the method needs each star confined to its own volume,
      because far from the axis the centrifugal term makes H positive again);
   5. each star's maximum density is held fixed:
-        rho' = rho_max,i (H / H_max,i)^n where H > 0, rho_floor elsewhere,
-     (which fixes K_i = H_max,i / ((n + 1) rho_max,i^(1/n))).
+        rho' = max(rho_floor, rho_max,i (H / H_max,i)^n) where H > 0,
+        rho_floor elsewhere
+     (which fixes K_i = H_max,i / ((n + 1) rho_max,i^(1/n))).  The floor
+     bounds the density from below everywhere (a reading): the new density
+     is then continuous in H, so a cell whose H is zero to rounding takes
+     the floor whichever sign the rounding gives.  Without it, such a cell
+     would switch between the floor and a density of order 1e-24, which
+     moves the centre of mass of its near-vacuum parent cells and, through
+     the expansions about them, the next potential by about 1e-6 (measured
+     on the level-3 binary).
 A single star is star 1 alone (rho_max[1] = 0: no cell is assigned to star 2).
 """
 
@@ -114,7 +122,8 @@ def iterate(c, rho, params):
         if not live.any():
             continue
         hmax[i] = H[live].max()
-        out[live] = params["rho_max"][i] * (H[live] / hmax[i]) ** n
+        out[live] = np.maximum(params["rho_floor"],
+                               params["rho_max"][i] * (H[live] / hmax[i]) ** n)
     return out, dict(omega2=omega2, C=(C1, C2), com=com, H_max=tuple(hmax), phi=phi)
 
 

@@ -9,7 +9,7 @@
 //   H = C_i - Phi + Omega^2 w^2 / 2   (the enthalpy (n + 1) K_i rho^(1/n)
 //                                     inside star i, w the axis distance),
 //   Omega^2, C_1, C_2 from H = 0 at surface points A, B (star 1) and C
-//   (star 2),  rho' = rho_max,i (H / H_max,i)^n where H > 0.
+//   (star 2),  rho' = max(rho_floor, rho_max,i (H / H_max,i)^n) where H > 0.
 // The per-cell work (centre of mass, H and its per-star maximum, the new
 // density) runs in three kernels over the leaf nodes; the host reads back
 // per-node partial sums and the potential at the three surface cells, and
@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(kScfThreads) scf_hmax_kernel(const NodeInfo *_
     }
 }
 
-// the new density: rho_max,i (H / H_max,i)^n inside star i where H > 0,
-// the floor elsewhere
+// the new density: max(floor, rho_max,i (H / H_max,i)^n) inside star i where
+// H > 0, the floor elsewhere (continuous in H: a cell whose H is zero to
+// rounding takes the floor on either side of zero)
 __global__ void __launch_bounds__(kScfThreads) scf_density_kernel(
     const NodeInfo *__restrict__ info, const int32_t *__restrict__ leaves,
     const double *__restrict__ levels, const double *__restrict__ phi, double *__restrict__ rho_out,
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(kScfThreads) scf_density_kernel(
         double r = floor_value;
         if (star >= 0) {
             const double H = enthalpy(x, phi[idx], star, s);
-            if (H > 0.0) r = (star ? rho_max1 : rho_max0) * pow(H * (star ? ih1 : ih0), n);
+            if (H > 0.0)
+                r = fmax(floor_value, (star ? rho_max1 : rho_max0) * pow(H * (star ? ih1 : ih0), n));
         }
         rho_out[idx] = r;
     }

@@ -399,6 +399,38 @@ int fmm_check_conversions(const double *values, int64_t n, int32_t *mismatch,
                           fmm_stream_t stream);
 
 /*
+ * Time derivative of the potential and field (Sec. 2: the solver also needs
+ * the time derivative of the gravitational field, which couples to the
+ * hydrodynamics so that total energy is conserved; the paper gives no
+ * formula).  Returned: the exact time derivative of this library's solve
+ * along the density's rate of change,
+ *   phi_dot = d/dt phi(rho + t rho_dot) at t = 0,   g_dot likewise,
+ * including the motion of every refined cell's centre of mass, formed from
+ * four fmm_step solves at rho + a rho_dot, a = +-eps, +-2 eps, by the
+ * fourth-order central difference
+ *   f'(0) ~ [8 (f(eps) - f(-eps)) - (f(2 eps) - f(-2 eps))] / (12 eps)
+ * (truncation O(eps^4), rounding about the solve's relative precision / eps:
+ * use FMM_FP64 or FMM_DFLOAT; the mixed precision's 1e-7 rounding makes it
+ * unsuitable).
+ *   rho, rho_dot: device double [n_leaf][512] (read); rho + a rho_dot must
+ *            stay positive for |a| <= 2 eps (otherwise
+ *            FMM_STATUS_BAD_DENSITY is set and the result is undefined).
+ *   eps:     time step of the differences, > 0, in the units of rho_dot.
+ *   rho_work: device double [n_leaf][512], 16-byte aligned: scratch.
+ *   M ... totals: the buffers of fmm_step, used as scratch (on return they
+ *            hold the solve at rho - 2 eps rho_dot).
+ *   phi_dot: device double [n_leaf][512], written.
+ *   g_dot:   device double [n_leaf][3][512], written.
+ * Asynchronous on `stream` (no allocation).  Errors: as fmm_step, and
+ * FMM_ERR_INVALID_ARG for eps not positive and finite or a NULL buffer.
+ */
+int fmm_field_time_derivative(fmm_tree_t tree, const double *rho, const double *rho_dot,
+                              double eps, double *rho_work, double *M, double *com, void *L,
+                              float *L_comp, double *dL1, double *L64, double *dL1_acc,
+                              double *phi, double *g, double *totals, double *phi_dot,
+                              double *g_dot, fmm_stream_t stream);
+
+/*
  * Self-consistent-field initial models (Sec. 3 and Sec. 4.2: the initial
  * scenario is assembled with the self-consistent field technique alongside
  * the FMM solver; the method is Hachisu's 1986 SCF).  Polytropes

@@ -48,6 +48,20 @@
  */
 #include <math.h>
 #include <stdint.h>
+/* The solve's arithmetic type.  Built as double (the oracle); built with
+ * ORACLE_COMPLEX_STEP as double complex, so that a density rho + i h rho_dot
+ * carries the exact time derivative of every stage in the imaginary parts
+ * (complex-step differentiation: every operation of the solve is analytic in
+ * the density, and no difference is formed, so the derivative has no
+ * cancellation error). */
+#ifdef ORACLE_COMPLEX_STEP
+#include <complex.h>
+typedef double complex real;
+#define SQRT_R csqrt
+#else
+typedef double real;
+#define SQRT_R sqrt
+#endif
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -91,11 +105,11 @@ static void o_gcell(const otree *t, int64_t i, int c, int64_t g[3])
     for (int a = 0; a < 3; ++a) g[a] = (int64_t)NSIDE * o_coord(t, i, a) + loc[a];
 }
 
-static void o_centre(const otree *t, int64_t i, int c, double x[3])
+static void o_centre(const otree *t, int64_t i, int c, real x[3])
 {
     int64_t g[3];
     o_gcell(t, i, c, g);
-    double h = o_width(t, o_level(t, i));
+    real h = o_width(t, o_level(t, i));
     for (int a = 0; a < 3; ++a) x[a] = t->lo[a] + ((double)g[a] + 0.5) * h;
 }
 
@@ -157,7 +171,7 @@ static const int PK3[10][3] = { {0,0,0},{0,0,1},{0,0,2},{0,1,1},{0,1,2},
                                 {0,2,2},{1,1,1},{1,1,2},{1,2,2},{2,2,2} };
 
 /* unpack the 20 packed components of order k into a full 3^k tensor */
-static void unpack(const double *p20, int k, double *full)
+static void unpack(const real *p20, int k, real *full)
 {
     if (k == 0) { full[0] = p20[0]; return; }
     if (k == 1) { for (int i = 0; i < 3; ++i) full[i] = p20[1 + i]; return; }
@@ -177,7 +191,7 @@ static void unpack(const double *p20, int k, double *full)
 }
 
 /* pack a full symmetric tensor of order k into the 20-component layout */
-static void pack(const double *full, int k, double *p20)
+static void pack(const real *full, int k, real *p20)
 {
     if (k == 0) { p20[0] = full[0]; return; }
     if (k == 1) { for (int i = 0; i < 3; ++i) p20[1 + i] = full[i]; return; }
@@ -202,13 +216,13 @@ static int ipow3(int k) { int r = 1; while (k-- > 0) r *= 3; return r; }
  *                   + R_j R_k d_il + R_j R_l d_ik + R_k R_l d_ij) / r^7
  *             + 3 (d_ij d_kl + d_ik d_jl + d_il d_jk) / r^5
  */
-void oracle_dtensors(const double R[3], double *D0, double *D1, double *D2,
-                     double *D3, double *D4)
+void oracle_dtensors(const real R[3], real *D0, real *D1, real *D2,
+                     real *D3, real *D4)
 {
-    double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
-    double r = sqrt(r2);
-    double i1 = 1.0 / r;
-    double i3 = i1 / r2, i5 = i3 / r2, i7 = i5 / r2, i9 = i7 / r2;
+    real r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    real r = SQRT_R(r2);
+    real i1 = 1.0 / r;
+    real i3 = i1 / r2, i5 = i3 / r2, i7 = i5 / r2, i9 = i7 / r2;
 #define DL(a, b) ((a) == (b) ? 1.0 : 0.0)
     D0[0] = i1;
     for (int i = 0; i < 3; ++i) D1[i] = -R[i] * i3;
@@ -242,14 +256,14 @@ static const double INV_FACT[5] = { 1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0 };
  * nmax: highest Taylor order wanted at A (1 for a leaf target, 3 otherwise).
  * Adds to Lfull[n] (full tensors) and dL1[3].
  */
-static void o_interact(double G, const double *MA, const double XA[3],
-                       const double *MB, const double XB[3], int nmax,
-                       double *Lfull[4], double dL1[3])
+static void o_interact(double G, const real *MA, const real XA[3],
+                       const real *MB, const real XB[3], int nmax,
+                       real *Lfull[4], real dL1[3])
 {
-    double R[3] = { XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2] };
-    double D[5][81];
+    real R[3] = { XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2] };
+    real D[5][81];
     oracle_dtensors(R, D[0], D[1], D[2], D[3], D[4]);
-    double Mf[4][27];
+    real Mf[4][27];
     for (int m = 0; m < 4; ++m) unpack(MB, m, Mf[m]);
     /* L^(n)_alpha += -G ((-1)^m / m!) sum_beta M^(m)_beta D^(n+m)_{alpha beta} */
     for (int n = 0; n <= nmax; ++n) {
@@ -259,18 +273,18 @@ static void o_interact(double G, const double *MA, const double XA[3],
             double sgn = (m % 2) ? -1.0 : 1.0;
             double coef = -G * sgn * INV_FACT[m];
             for (int a = 0; a < na; ++a) {
-                double s = 0.0;
+                real s = 0.0;
                 for (int b = 0; b < nb; ++b) s += Mf[m][b] * D[n + m][a + na * b];
                 Lfull[n][a] += coef * s;
             }
         }
     }
     /* angular-momentum correction */
-    double M3A[27];
+    real M3A[27];
     unpack(MA, 3, M3A);
-    double ratio = MB[0] / MA[0];
+    real ratio = MB[0] / MA[0];
     for (int i = 0; i < 3; ++i) {
-        double s = 0.0;
+        real s = 0.0;
         for (int b = 0; b < 27; ++b)
             s += D[4][i + 3 * b] * (Mf[3][b] - ratio * M3A[b]);
         dL1[i] += G / 6.0 * s;
@@ -332,20 +346,20 @@ static int o_nodes_near(const otree *t, int64_t i, int64_t j)
  * rho: [n_leaf][512]; M: [n][20][512]; com: [n][3][512].
  */
 int oracle_upward(const int32_t *desc, int64_t n, const double *cfg,
-                  const double *rho, double *M, double *com)
+                  const real *rho, real *M, real *com)
 {
     otree T, *t = &T;
     o_init(t, desc, n, cfg);
-    memset(M, 0, sizeof(double) * (size_t)n * NCOMP * NCELL);
-    memset(com, 0, sizeof(double) * (size_t)n * 3 * NCELL);
-    double *mx = (double *)calloc((size_t)n * 3 * NCELL, sizeof(double));
+    memset(M, 0, sizeof(real) * (size_t)n * NCOMP * NCELL);
+    memset(com, 0, sizeof(real) * (size_t)n * 3 * NCELL);
+    real *mx = (real *)calloc((size_t)n * 3 * NCELL, sizeof(real));
     /* pass 1: mass and first moment about the origin for every ancestor */
     for (int64_t i = 0; i < n; ++i) {
         if (!o_is_leaf(t, i)) continue;
-        double h = o_width(t, o_level(t, i));
+        real h = o_width(t, o_level(t, i));
         for (int c = 0; c < NCELL; ++c) {
-            double m = rho[t->leaf_row[i] * NCELL + c] * h * h * h;
-            double x[3];
+            real m = rho[t->leaf_row[i] * NCELL + c] * h * h * h;
+            real x[3];
             o_centre(t, i, c, x);
             int64_t node = i;
             int cell = c;
@@ -361,9 +375,9 @@ int oracle_upward(const int32_t *desc, int64_t n, const double *cfg,
     }
     for (int64_t i = 0; i < n; ++i)
         for (int c = 0; c < NCELL; ++c) {
-            double m0 = M[(i * NCOMP + 0) * NCELL + c];
+            real m0 = M[(i * NCOMP + 0) * NCELL + c];
             if (o_is_leaf(t, i)) {
-                double x[3];
+                real x[3];
                 o_centre(t, i, c, x);
                 for (int a = 0; a < 3; ++a) com[(i * 3 + a) * NCELL + c] = x[a];
             } else {
@@ -375,10 +389,10 @@ int oracle_upward(const int32_t *desc, int64_t n, const double *cfg,
     /* pass 2: second and third central moments of every refined ancestor */
     for (int64_t i = 0; i < n; ++i) {
         if (!o_is_leaf(t, i)) continue;
-        double h = o_width(t, o_level(t, i));
+        real h = o_width(t, o_level(t, i));
         for (int c = 0; c < NCELL; ++c) {
-            double m = rho[t->leaf_row[i] * NCELL + c] * h * h * h;
-            double x[3];
+            real m = rho[t->leaf_row[i] * NCELL + c] * h * h * h;
+            real x[3];
             o_centre(t, i, c, x);
             int64_t node = i;
             int cell = c;
@@ -386,7 +400,7 @@ int oracle_upward(const int32_t *desc, int64_t n, const double *cfg,
                 int64_t pn; int pc;
                 o_parent_cell(t, node, cell, &pn, &pc);
                 node = pn; cell = pc;
-                double s[3];
+                real s[3];
                 for (int a = 0; a < 3; ++a) s[a] = x[a] - com[(node * 3 + a) * NCELL + cell];
                 for (int q = 0; q < 6; ++q)
                     M[(node * NCOMP + 4 + q) * NCELL + cell] += m * s[PK2[q][0]] * s[PK2[q][1]];
@@ -404,21 +418,21 @@ int oracle_upward(const int32_t *desc, int64_t n, const double *cfg,
 
 /* all same-level interactions of target cell c of node i: packed L20 and
  * dL1 (orders above the target's need are zero) */
-static void o_m2l_target(const otree *t, const double *M, const double *com,
-                         int64_t i, int c, double L20[NCOMP], double dL13[3], int64_t cnt[4])
+static void o_m2l_target(const otree *t, const real *M, const real *com,
+                         int64_t i, int c, real L20[NCOMP], real dL13[3], int64_t cnt[4])
 {
     int level = o_level(t, i);
     int a_leaf = o_is_leaf(t, i);
     int nmax = a_leaf ? 1 : 3;
     int64_t gA[3];
     o_gcell(t, i, c, gA);
-    double MA[NCOMP], XA[3];
+    real MA[NCOMP], XA[3];
     for (int k = 0; k < NCOMP; ++k) MA[k] = M[(i * NCOMP + k) * NCELL + c];
     for (int a = 0; a < 3; ++a) XA[a] = com[(i * 3 + a) * NCELL + c];
-    double Lf[4][27];
+    real Lf[4][27];
     memset(Lf, 0, sizeof Lf);
-    double *Lp[4] = { Lf[0], Lf[1], Lf[2], Lf[3] };
-    double d1[3] = { 0.0, 0.0, 0.0 };
+    real *Lp[4] = { Lf[0], Lf[1], Lf[2], Lf[3] };
+    real d1[3] = { 0.0, 0.0, 0.0 };
     int64_t g = (int64_t)o_tree(t, i) * (t->max_level + 1) + level;
     for (int64_t q = t->grp_off[g]; q < t->grp_off[g + 1]; ++q) {
         int64_t j = t->grp_nodes[q];
@@ -430,14 +444,14 @@ static void o_m2l_target(const otree *t, const double *M, const double *com,
             int far;
             int kind = o_pair(t, level, gA, a_leaf, gB, b_leaf, &far);
             if (!kind) continue;
-            double MB[NCOMP], XB[3];
+            real MB[NCOMP], XB[3];
             for (int k = 0; k < NCOMP; ++k) MB[k] = M[(j * NCOMP + k) * NCELL + cb];
             for (int a = 0; a < 3; ++a) XB[a] = com[(j * 3 + a) * NCELL + cb];
             o_interact(t->G, MA, XA, MB, XB, nmax, Lp, d1);
             cnt[kind - 1]++;
         }
     }
-    memset(L20, 0, sizeof(double) * NCOMP);
+    memset(L20, 0, sizeof(real) * NCOMP);
     for (int n = 0; n <= nmax; ++n) pack(Lf[n], n, L20);
     for (int a = 0; a < 3; ++a) dL13[a] = d1[a];
 }
@@ -450,7 +464,7 @@ static void o_m2l_target(const otree *t, const double *M, const double *com,
  * compact != 0 (targets given), L is [n_targets][20] and dL1 [n_targets][3].
  */
 int oracle_m2l(const int32_t *desc, int64_t n, const double *cfg,
-               const double *M, const double *com, double *L, double *dL1,
+               const real *M, const real *com, real *L, real *dL1,
                int64_t *counts, const int64_t *targets, int64_t n_targets,
                int n_threads, int compact)
 {
@@ -468,7 +482,7 @@ int oracle_m2l(const int32_t *desc, int64_t n, const double *cfg,
         int64_t cnt[4] = { 0, 0, 0, 0 };
         int64_t i = tc / NCELL;
         int c = (int)(tc % NCELL);
-        double L20[NCOMP], d3[3];
+        real L20[NCOMP], d3[3];
         o_m2l_target(t, M, com, i, c, L20, d3, cnt);
         if (compact) {
             for (int q = 0; q < NCOMP; ++q) L[k * NCOMP + q] = L20[q];
@@ -529,16 +543,16 @@ int64_t oracle_sources(const int32_t *desc, int64_t n, const double *cfg,
  * covered exactly once iff this equals sum(w) - w_a.
  */
 int oracle_coverage(const int32_t *desc, int64_t n, const double *cfg,
-                    const double *w, double *out)
+                    const real *w, real *out)
 {
     otree T, *t = &T;
     o_init(t, desc, n, cfg);
-    double *W = (double *)calloc((size_t)n * NCELL, sizeof(double));
-    double *cov = (double *)calloc((size_t)n * NCELL, sizeof(double));
+    real *W = (real *)calloc((size_t)n * NCELL, sizeof(real));
+    real *cov = (real *)calloc((size_t)n * NCELL, sizeof(real));
     for (int64_t i = 0; i < n; ++i) {
         if (!o_is_leaf(t, i)) continue;
         for (int c = 0; c < NCELL; ++c) {
-            double v = w[t->leaf_row[i] * NCELL + c];
+            real v = w[t->leaf_row[i] * NCELL + c];
             int64_t node = i; int cell = c;
             for (;;) {
                 W[node * NCELL + cell] += v;
@@ -573,7 +587,7 @@ int oracle_coverage(const int32_t *desc, int64_t n, const double *cfg,
     for (int64_t i = 0; i < n; ++i) {
         if (!o_is_leaf(t, i)) continue;
         for (int c = 0; c < NCELL; ++c) {
-            double s = 0.0;
+            real s = 0.0;
             int64_t node = i; int cell = c;
             for (;;) {
                 s += cov[node * NCELL + cell];
@@ -602,22 +616,22 @@ int oracle_coverage(const int32_t *desc, int64_t n, const double *cfg,
  * Leaf cells only receive orders 0 and 1.
  */
 int oracle_downward(const int32_t *desc, int64_t n, const double *cfg,
-                    const double *com, const double *L, const double *dL1,
-                    double *L64, double *dL1acc)
+                    const real *com, const real *L, const real *dL1,
+                    real *L64, real *dL1acc)
 {
     otree T, *t = &T;
     o_init(t, desc, n, cfg);
-    memset(L64, 0, sizeof(double) * (size_t)n * NCOMP * NCELL);
+    memset(L64, 0, sizeof(real) * (size_t)n * NCOMP * NCELL);
     for (int level = 1; level <= t->max_level; ++level) {
         for (int64_t i = 0; i < n; ++i) {
             if (o_level(t, i) != level) continue;
             int nmax = o_is_leaf(t, i) ? 1 : 3;
             for (int c = 0; c < NCELL; ++c) {
-                double own[NCOMP];
+                real own[NCOMP];
                 for (int k = 0; k < NCOMP; ++k) own[k] = L[(i * NCOMP + k) * NCELL + c];
-                double out[NCOMP];
+                real out[NCOMP];
                 memset(out, 0, sizeof out);
-                double corr[3];
+                real corr[3];
                 for (int a = 0; a < 3; ++a) corr[a] = dL1[(i * 3 + a) * NCELL + c];
                 if (o_parent(t, i) < 0) {
                     for (int k = 0; k < NCOMP; ++k) out[k] = own[k];
@@ -625,33 +639,33 @@ int oracle_downward(const int32_t *desc, int64_t n, const double *cfg,
                 } else {
                     int64_t pn; int pc;
                     o_parent_cell(t, i, c, &pn, &pc);
-                    double Pp[NCOMP];
+                    real Pp[NCOMP];
                     for (int k = 0; k < NCOMP; ++k) Pp[k] = L64[(pn * NCOMP + k) * NCELL + pc];
-                    double Pf[4][27];
+                    real Pf[4][27];
                     for (int k = 0; k < 4; ++k) unpack(Pp, k, Pf[k]);
-                    double d[3];
+                    real d[3];
                     for (int a = 0; a < 3; ++a)
                         d[a] = com[(i * 3 + a) * NCELL + c] - com[(pn * 3 + a) * NCELL + pc];
                     /* powers d^k as full tensors */
-                    double dk[4][27];
+                    real dk[4][27];
                     dk[0][0] = 1.0;
                     for (int a = 0; a < 3; ++a) dk[1][a] = d[a];
                     for (int a = 0; a < 9; ++a) dk[2][a] = d[a % 3] * d[a / 3];
                     for (int a = 0; a < 27; ++a) dk[3][a] = d[a % 3] * d[(a / 3) % 3] * d[a / 9];
                     for (int nn = 0; nn <= nmax; ++nn) {
                         int na = ipow3(nn);
-                        double shifted[27];
+                        real shifted[27];
                         for (int a = 0; a < na; ++a) {
-                            double s = 0.0;
+                            real s = 0.0;
                             for (int k = 0; nn + k <= 3; ++k) {
                                 int nb = ipow3(k);
-                                double part = 0.0;
+                                real part = 0.0;
                                 for (int b = 0; b < nb; ++b) part += Pf[nn + k][a + na * b] * dk[k][b];
                                 s += INV_FACT[k] * part;
                             }
                             shifted[a] = s;
                         }
-                        double p20[NCOMP];
+                        real p20[NCOMP];
                         pack(shifted, nn, p20);
                         int k0 = nn == 0 ? 0 : nn == 1 ? 1 : nn == 2 ? 4 : 10;
                         int k1 = nn == 0 ? 1 : nn == 1 ? 4 : nn == 2 ? 10 : 20;
@@ -676,23 +690,23 @@ int oracle_downward(const int32_t *desc, int64_t n, const double *cfg,
  * the box centre.  phi: [n_leaf][512]; g: [n_leaf][3][512].
  */
 int oracle_forces(const int32_t *desc, int64_t n, const double *cfg,
-                  const double *L64, const double *dL1acc, const double *rho,
-                  double *phi, double *g, double *totals)
+                  const real *L64, const real *dL1acc, const real *rho,
+                  real *phi, real *g, real *totals)
 {
     otree T, *t = &T;
     o_init(t, desc, n, cfg);
-    memset(totals, 0, sizeof(double) * 8 * (size_t)t->n_trees);
-    double ctr[3];
+    memset(totals, 0, sizeof(real) * 8 * (size_t)t->n_trees);
+    real ctr[3];
     for (int a = 0; a < 3; ++a) ctr[a] = t->lo[a] + 0.5 * t->size;
     for (int64_t i = 0; i < n; ++i) {
         if (!o_is_leaf(t, i)) continue;
         int64_t row = t->leaf_row[i];
-        double h = o_width(t, o_level(t, i));
-        double *tot = totals + 8 * o_tree(t, i);
+        real h = o_width(t, o_level(t, i));
+        real *tot = totals + 8 * o_tree(t, i);
         for (int c = 0; c < NCELL; ++c) {
-            double m = rho[row * NCELL + c] * h * h * h;
+            real m = rho[row * NCELL + c] * h * h * h;
             phi[row * NCELL + c] = L64[(i * NCOMP + 0) * NCELL + c];
-            double gv[3], f[3], x[3], xf[3];
+            real gv[3], f[3], x[3], xf[3];
             for (int a = 0; a < 3; ++a) {
                 gv[a] = -(L64[(i * NCOMP + 1 + a) * NCELL + c] + dL1acc[(i * 3 + a) * NCELL + c]);
                 g[(row * 3 + a) * NCELL + c] = gv[a];
@@ -704,8 +718,8 @@ int oracle_forces(const int32_t *desc, int64_t n, const double *cfg,
             xf[1] = x[2] * f[0] - x[0] * f[2];
             xf[2] = x[0] * f[1] - x[1] * f[0];
             for (int a = 0; a < 3; ++a) { tot[a] += f[a]; tot[3 + a] += xf[a]; }
-            tot[6] += sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-            tot[7] += sqrt(xf[0] * xf[0] + xf[1] * xf[1] + xf[2] * xf[2]);
+            tot[6] += SQRT_R(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+            tot[7] += SQRT_R(xf[0] * xf[0] + xf[1] * xf[1] + xf[2] * xf[2]);
         }
     }
     o_free(t);
@@ -718,17 +732,17 @@ int oracle_forces(const int32_t *desc, int64_t n, const double *cfg,
  * 20-component Taylor coefficients (orders above nmax left zero) and the
  * correction dL1[3].
  */
-int oracle_pair_m2l(double G, const double *MA, const double *XA,
-                    const double *MB, const double *XB, int a_leaf,
-                    double *L20, double *dL1)
+int oracle_pair_m2l(double G, const real *MA, const real *XA,
+                    const real *MB, const real *XB, int a_leaf,
+                    real *L20, real *dL1)
 {
     int nmax = a_leaf ? 1 : 3;
-    double Lf[4][27];
+    real Lf[4][27];
     memset(Lf, 0, sizeof Lf);
-    double *Lp[4] = { Lf[0], Lf[1], Lf[2], Lf[3] };
-    double d1[3] = { 0.0, 0.0, 0.0 };
+    real *Lp[4] = { Lf[0], Lf[1], Lf[2], Lf[3] };
+    real d1[3] = { 0.0, 0.0, 0.0 };
     o_interact(G, MA, XA, MB, XB, nmax, Lp, d1);
-    memset(L20, 0, sizeof(double) * NCOMP);
+    memset(L20, 0, sizeof(real) * NCOMP);
     for (int n = 0; n <= nmax; ++n) pack(Lf[n], n, L20);
     for (int a = 0; a < 3; ++a) dL1[a] = d1[a];
     return 0;

@@ -20,29 +20,39 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fmm_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+# the same source built on double complex numbers (complex-step derivatives)
+_LIB_CS_PATH = os.path.join(_OUT_DIR, "liboracle_cs.so")
 _LOCK = threading.Lock()
 _LIB = None
+_LIB_CS = None
 
 NCELL = 512
 NCOMP = 20
 
 
-def _compile(src, out):
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", out, src, "-lm"]
+def _compile(src, out, defines=()):
+    cmd = (["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+            "-ffp-contract=off", "-fno-fast-math"] + [f"-D{d}" for d in defines]
+           + ["-o", out, src, "-lm"])
     subprocess.run(cmd, check=True)
 
 
-def build(force=False):
-    """Compile the oracle with gcc (OpenMP over target cells, IEEE FP64)."""
+def _build_one(path, defines, force):
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    _compile(_SRC, tmp)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".{os.getpid()}.tmp"
+    _compile(_SRC, tmp, defines)
+    os.replace(tmp, path)
+    return path
+
+
+def build(force=False):
+    """Compile the oracle with gcc (OpenMP over target cells, IEEE FP64), and
+    its complex-step build."""
+    _build_one(_LIB_CS_PATH, ("ORACLE_COMPLEX_STEP",), force)
+    return _build_one(_LIB_PATH, (), force)
 
 
 def _bind(lib):
@@ -66,6 +76,15 @@ def _lib():
         if _LIB is None:
             _LIB = _bind(ctypes.CDLL(build()))
         return _LIB
+
+
+def _lib_cs():
+    global _LIB_CS
+    with _LOCK:
+        if _LIB_CS is None:
+            build()
+            _LIB_CS = _bind(ctypes.CDLL(_LIB_CS_PATH))
+        return _LIB_CS
 
 
 def source_text():
@@ -232,3 +251,38 @@ def dtensors(R):
     _lib().oracle_dtensors(_p(R), *(_p(x) for x in D))
     return (D[0][0], D[1], D[2].reshape(3, 3), D[3].reshape(3, 3, 3),
             D[4].reshape(3, 3, 3, 3))
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def solve_tangent(tree, rho, rho_dot, h=1e-40):
+    """The time derivative of the whole solve along rho(t) = rho + t rho_dot
+    at t = 0, by complex-step differentiation: the complex-number build of
+    the same oracle solves the density rho + i h rho_dot, and every output's
+    imaginary part over h is its exact derivative (no differences are formed,
+    so there is no cancellation; the O(h^2) remainder is below double
+    precision for any h this small).  Returns dict(phi, g, phi_dot, g_dot,
+    totals, totals_dot)."""
+    lib = _lib_cs()
+    rc = _c128(np.asarray(rho, dtype=np.float64) + 1j * h * np.asarray(rho_dot, dtype=np.float64))
+    M = np.empty((tree.n, NCOMP, NCELL), dtype=np.complex128)
+    com = np.empty((tree.n, 3, NCELL), dtype=np.complex128)
+    lib.oracle_upward(_p(tree.desc), tree.n, _p(tree.cfg), _p(rc), _p(M), _p(com))
+    L = np.zeros((tree.n, NCOMP, NCELL), dtype=np.complex128)
+    dL1 = np.zeros((tree.n, 3, NCELL), dtype=np.complex128)
+    counts = np.zeros(4, dtype=np.int64)
+    lib.oracle_m2l(_p(tree.desc), tree.n, _p(tree.cfg), _p(M), _p(com), _p(L), _p(dL1),
+                   _p(counts), None, 0, 0, 0)
+    L64 = np.empty((tree.n, NCOMP, NCELL), dtype=np.complex128)
+    acc = np.empty((tree.n, 3, NCELL), dtype=np.complex128)
+    lib.oracle_downward(_p(tree.desc), tree.n, _p(tree.cfg), _p(com), _p(L), _p(dL1), _p(L64),
+                        _p(acc))
+    phi = np.empty((tree.n_leaf, NCELL), dtype=np.complex128)
+    g = np.empty((tree.n_leaf, 3, NCELL), dtype=np.complex128)
+    tot = np.empty((tree.n_trees, 8), dtype=np.complex128)
+    lib.oracle_forces(_p(tree.desc), tree.n, _p(tree.cfg), _p(L64), _p(acc), _p(rc), _p(phi),
+                      _p(g), _p(tot))
+    return dict(phi=phi.real.copy(), g=g.real.copy(), phi_dot=phi.imag / h, g_dot=g.imag / h,
+                totals=tot.real.copy(), totals_dot=tot.imag / h)

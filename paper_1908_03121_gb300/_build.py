@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfmm_gb300.so")
 SOURCES = ["fmm_host.cpp", "fmm_upward.cu", "fmm_m2l.cu", "fmm_downward.cu", "fmm_noalloc.cu",
-           "fmm_check.cu", "fmm_scf.cu"]
+           "fmm_check.cu", "fmm_scf.cu", "fmm_tangent.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -34,7 +34,7 @@ KERNEL_SLOTS = ("p2m", "m2m", "pack", "root", "multipole", "monopole", "mono_mul
 EXPORTED = ("fmm_build_tree", "fmm_get_sizes", "fmm_get_stats", "fmm_upward",
             "fmm_m2l", "fmm_downward", "fmm_forces", "fmm_step", "fmm_set_tuning", "fmm_get_tuning",
             "fmm_forces_noalloc", "fmm_check_conversions", "fmm_peak_rate", "fmm_scf_update",
-            "fmm_get_status", "fmm_destroy_tree", "fmm_last_error")
+            "fmm_field_time_derivative", "fmm_get_status", "fmm_destroy_tree", "fmm_last_error")
 
 NCELL = 512
 NCOMP = 20
@@ -126,6 +126,7 @@ def load(build=True):
         lib.fmm_downward.argtypes = [P, P, P, P, P, P, P, P]
         lib.fmm_forces.argtypes = [P, P, P, P, P, P, P, P]
         lib.fmm_step.argtypes = [P] * 13
+        lib.fmm_field_time_derivative.argtypes = [P, P, P, ctypes.c_double] + [P] * 14
         lib.fmm_destroy_tree.argtypes = [P]
         lib.fmm_destroy_tree.restype = None
         lib.fmm_forces_noalloc.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
@@ -256,6 +257,17 @@ def fmm_step(tree, rho, M, com, L, L_comp, dL1, L64, dL1_acc, phi, g, totals, st
     _check(load().fmm_step(tree.handle, _ptr(rho), _ptr(M), _ptr(com), _ptr(L), _ptr(L_comp),
                            _ptr(dL1), _ptr(L64), _ptr(dL1_acc), _ptr(phi), _ptr(g), _ptr(totals),
                            _stream(stream)))
+
+
+def fmm_field_time_derivative(tree, rho, rho_dot, eps, rho_work, M, com, L, L_comp, dL1, L64,
+                              dL1_acc, phi, g, totals, phi_dot, g_dot, stream=None):
+    """phi_dot, g_dot: the time derivative of the solve along rho + t rho_dot
+    (four solves, fourth-order central differences of step eps; the step's
+    buffers are scratch)."""
+    _check(load().fmm_field_time_derivative(
+        tree.handle, _ptr(rho), _ptr(rho_dot), float(eps), _ptr(rho_work), _ptr(M), _ptr(com),
+        _ptr(L), _ptr(L_comp), _ptr(dL1), _ptr(L64), _ptr(dL1_acc), _ptr(phi), _ptr(g),
+        _ptr(totals), _ptr(phi_dot), _ptr(g_dot), _stream(stream)))
 
 
 def fmm_destroy_tree(tree):
@@ -410,6 +422,18 @@ class Solver:
         self.m2l(stream)
         self.downward(stream)
         self.forces(rho, stream)
+
+    def time_derivative(self, rho_dot, eps, phi_dot, g_dot, rho=None, rho_work=None,
+                        stream=None):
+        """phi_dot, g_dot (device tensors shaped like phi and g): the time
+        derivative of the solve along rho + t rho_dot (fmm_field_time_derivative;
+        this solver's step buffers are used as scratch)."""
+        import torch
+        if rho_work is None:
+            rho_work = torch.empty_like(self.rho)
+        fmm_field_time_derivative(self.tree, self.rho if rho is None else rho, rho_dot, eps,
+                                  rho_work, self.M, self.com, self.L, self.Lc, self.dL1, self.L64,
+                                  self.dacc, self.phi, self.g, self.totals, phi_dot, g_dot, stream)
 
     def status(self, clear=True):
         """FMM_STATUS_* bits recorded by the kernels since the last clear

@@ -62,8 +62,8 @@ MUTANTS = [
     # the angular-momentum correction
     ("correction: sign flipped", "dL1[i] += G / 6.0 * s;", "dL1[i] -= G / 6.0 * s;",
      ["torque_pair", "invariants_cfg1"]),
-    ("correction: mass ratio inverted", "double ratio = MB[0] / MA[0];",
-     "double ratio = MA[0] / MB[0];", ["torque_pair", "invariants_cfg1"]),
+    ("correction: mass ratio inverted", "real ratio = MB[0] / MA[0];",
+     "real ratio = MA[0] / MB[0];", ["torque_pair", "invariants_cfg1"]),
     ("correction: factor 1/2 instead of 1/6", "dL1[i] += G / 6.0 * s;",
      "dL1[i] += G / 2.0 * s;", ["torque_pair", "invariants_cfg1"]),
     # the opening rule

@@ -71,7 +71,7 @@ def parse_args():
     p.add_argument("--dfloat-steps", type=int, default=5)
     p.add_argument("--theta035-steps", type=int, default=5)
     # the other full-size workloads reported beside the headline one
-    p.add_argument("--extra-workloads", default="cfg3,cfg4")
+    p.add_argument("--extra-workloads", default="cfg3,cfg4", help="comma-separated, or none")
     p.add_argument("--extra-steps", type=int, default=20)
     # the full FP64 oracle solve of the adaptive level-5 binary (cfg3), for
     # each precision's error against the oracle itself (about 20-40 s of CPU)
@@ -717,7 +717,7 @@ def run_ours(args):
         # the other full-size workloads: each precision through the captured,
         # autotuned step (median of --extra-steps), with its error against
         # the FP64 GPU path and its net force and torque
-        extra = [w for w in args.extra_workloads.split(",") if w and w != args.workload]
+        extra = [w for w in args.extra_workloads.split(",") if w not in ("", "none", args.workload)]
         accuracy_ref = {}
         for wname in extra:
             result[wname] = other_workload(torch, F, autotune, wname, args, flush, stream,

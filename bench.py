@@ -76,6 +76,8 @@ def parse_args():
     # the full FP64 oracle solve of the adaptive level-5 binary (cfg3), for
     # each precision's error against the oracle itself (about 20-40 s of CPU)
     p.add_argument("--no-oracle-accuracy", action="store_true")
+    # leave out the dataflow, time-derivative and SCF timings
+    p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     # other modes (no bench line): a minimal run of one pass for profiler
@@ -347,6 +349,83 @@ def measure_peaks(torch, F, pci=None):
     out["clocks"] = clocks.stop()
     out["how"] = ("fmm_peak_rate: fused multiply-add loop on every SM (8 CTAs x 256 threads, "
                   "8 independent chains per thread), CUDA events, best launch")
+    return out
+
+
+# ------------------------------------------------------------ next rows
+def _graph_ms(torch, solver, steps, flush, stream):
+    solver.capture()
+    _, per, _ = time_graph(torch, solver, steps, 2, flush, stream, label="extras")
+    return float(np.median(per))
+
+
+def dataflow_ab(torch, F, solver, best, flush, stream, steps=30):
+    """The headline step with the dataflow downward pass on and off (all
+    else at the tuned values), median ms of each."""
+    out = {}
+    for df in (0, 1):
+        F.fmm_set_tuning(solver.tree, **dict(best, dataflow=df))
+        out[f"ms_per_step_dataflow_{df}"] = _graph_ms(torch, solver, steps, flush, stream)
+    F.fmm_set_tuning(solver.tree, **best)
+    solver.graph = None
+    return out
+
+
+def time_derivative_timing(torch, F, autotune, c, flush, reps=3):
+    """fmm_field_time_derivative on the headline workload (four solves) in
+    FP64 and double-float, device ms per call, with rho_dot = rho sin(7 x)."""
+    out = {}
+    x = np.linspace(0.0, 1.0, c["rho"].size).reshape(c["rho"].shape)
+    rd = torch.from_numpy(c["rho"] * np.sin(7.0 * x)).cuda()
+    for prec in ("fp64", "dfloat"):
+        s = F.Solver(c["desc"], c["theta"], precision=prec)
+        s.rho.copy_(torch.from_numpy(c["rho"]).cuda())
+        s.step()
+        autotune.tune(s)
+        pd, gd, work = torch.empty_like(s.phi), torch.empty_like(s.g), torch.empty_like(s.rho)
+        s.time_derivative(rd, 1e-3, pd, gd, rho_work=work)
+        ms = []
+        for _ in range(reps):
+            flush()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            s.time_derivative(rd, 1e-3, pd, gd, rho_work=work)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[prec] = {"ms_per_call": float(np.median(ms)), "solves_per_call": 4}
+        s.close()
+    return out
+
+
+def scf_timing(torch, F):
+    """Self-consistent-field binary on a uniform level-4 tree (64^3 cells),
+    FP64 and mixed solves: iterations to settle (Omega^2 and C to 1e-6) and
+    wall ms per iteration (solve, the update's two host reads, the density
+    kernels)."""
+    from paper_1908_03121_gb300 import scf as D
+    from workloads import uniform_tree
+    from workloads.density import polytrope
+    desc = uniform_tree(4)
+    leaves = desc[desc[:, 5] < 0]
+    h = 1.0 / 64.0
+    cc = np.arange(512)
+    loc = np.stack([cc & 7, (cc >> 3) & 7, cc >> 6], axis=1)
+    pos = (8.0 * leaves[:, None, 1:4] + loc[None] + 0.5) * h
+    c1, c2 = np.array([0.3, 0.5, 0.5]), np.array([0.72, 0.5, 0.5])
+    rho0 = polytrope(pos, c1, 0.15, 1.0) + polytrope(pos, c2, 0.13, 0.5) + 1e-10
+    p = D.binary_params(c1, 0.15, c2, 0.13, (1.0, 0.5), h)
+    out = {"workload": "binary of two n=1.5 polytropes on a uniform level-4 tree (262144 cells)"}
+    for prec in ("fp64", "mixed"):
+        s = F.Solver(desc, 0.5, precision=prec)
+        s.rho.copy_(torch.from_numpy(rho0).cuda())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, k = D.solve(s, p, iters=80, tol=1e-6)
+        torch.cuda.synchronize()
+        out[prec] = {"iterations": k, "ms_per_iteration": 1000.0 * (time.perf_counter() - t0) / k,
+                     "omega2": res["omega2"]}
+        s.close()
     return out
 
 
@@ -713,6 +792,14 @@ def run_ours(args):
                         "paper_gflops = the same points x 455 (multipole targets) or 12 "
                         "(monopole targets) / step time, the paper's own accounting"}
             s35.close()
+
+        # the next rows on the headline workload: the dataflow downward pass
+        # against the level launches (N3), the field's time derivative (N2),
+        # and self-consistent-field iterations (N4)
+        if not args.no_extras:
+            result["dataflow"] = dataflow_ab(torch, F, solver, best, flush, stream)
+            result["time_derivative"] = time_derivative_timing(torch, F, autotune, c, flush)
+            result["scf"] = scf_timing(torch, F)
 
         # the other full-size workloads: each precision through the captured,
         # autotuned step (median of --extra-steps), with its error against

@@ -78,6 +78,9 @@ def parse_args():
     p.add_argument("--no-oracle-accuracy", action="store_true")
     # leave out the dataflow, time-derivative and SCF timings
     p.add_argument("--no-extras", action="store_true")
+    # a fixed launch tuning (JSON object of fmm_tuning fields) instead of the
+    # autotuner's pick, e.g. so that a profiler's run has the plain run's shapes
+    p.add_argument("--tuning", default=None)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     # other modes (no bench line): a minimal run of one pass for profiler
@@ -556,7 +559,11 @@ def run_ours(args):
     solver.rho.copy_(rho_host.cuda())
     from paper_1908_03121_gb300 import autotune
     solver.step()
-    best, tune_results = autotune.tune(solver)
+    if args.tuning:
+        best = json.loads(args.tuning)
+        F.fmm_set_tuning(solver.tree, **best)
+    else:
+        best, tune_results = autotune.tune(solver)
     solver.capture()
     pci = None
     try:

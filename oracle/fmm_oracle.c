@@ -79,6 +79,7 @@ typedef struct {
     int64_t n;
     const int32_t *d;
     double theta, G, lo[3], size;
+    int order;              /* expansion order p: 3, or 2 (the truncation n + m <= p) */
     int64_t *leaf_row;      /* node -> density/force row, -1 if refined */
     int max_level;
     int n_trees;
@@ -134,6 +135,7 @@ static int o_init(otree *t, const int32_t *desc, int64_t n, const double *cfg)
     t->G = cfg[1];
     t->lo[0] = cfg[2]; t->lo[1] = cfg[3]; t->lo[2] = cfg[4];
     t->size = cfg[5];
+    t->order = (int)cfg[6];
     t->leaf_row = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int64_t rows = 0;
     for (int64_t i = 0; i < n; ++i) {
@@ -253,11 +255,18 @@ static const double INV_FACT[5] = { 1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0 };
 /*
  * One same-level interaction, target A <- source B, in FP64.
  * MA, MB: packed 20-component moments; XA, XB: centres of mass.
- * nmax: highest Taylor order wanted at A (1 for a leaf target, 3 otherwise).
+ * nmax: highest Taylor order wanted at A (1 for a leaf target, the order p
+ * otherwise); order: the expansion order p (3, or 2).
  * Adds to Lfull[n] (full tensors) and dL1[3].
+ * The correction is the n = 1, m = p term that the truncation drops, in the
+ * form that keeps each pair's forces opposite:
+ *   dL1_A = -G ((-1)^p / p!) D^(p+1) : [M_B^(p) + (-1)^p (M0_B / M0_A) M_A^(p)]
+ * (D^(p+1) is odd for even p and even for odd p, hence the sign of the
+ * target's share); p = 3 is the reading the paper's solver is given, p = 2
+ * the same construction one order lower.
  */
 static void o_interact(double G, const real *MA, const real XA[3],
-                       const real *MB, const real XB[3], int nmax,
+                       const real *MB, const real XB[3], int nmax, int order,
                        real *Lfull[4], real dL1[3])
 {
     real R[3] = { XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2] };
@@ -268,7 +277,7 @@ static void o_interact(double G, const real *MA, const real XA[3],
     /* L^(n)_alpha += -G ((-1)^m / m!) sum_beta M^(m)_beta D^(n+m)_{alpha beta} */
     for (int n = 0; n <= nmax; ++n) {
         int na = ipow3(n);
-        for (int m = 0; n + m <= 3; ++m) {
+        for (int m = 0; n + m <= order; ++m) {
             int nb = ipow3(m);
             double sgn = (m % 2) ? -1.0 : 1.0;
             double coef = -G * sgn * INV_FACT[m];
@@ -280,14 +289,27 @@ static void o_interact(double G, const real *MA, const real XA[3],
         }
     }
     /* angular-momentum correction */
-    real M3A[27];
-    unpack(MA, 3, M3A);
-    real ratio = MB[0] / MA[0];
-    for (int i = 0; i < 3; ++i) {
-        real s = 0.0;
-        for (int b = 0; b < 27; ++b)
-            s += D[4][i + 3 * b] * (Mf[3][b] - ratio * M3A[b]);
-        dL1[i] += G / 6.0 * s;
+    if (order == 3) {
+        real M3A[27];
+        unpack(MA, 3, M3A);
+        real ratio = MB[0] / MA[0];
+        for (int i = 0; i < 3; ++i) {
+            real s = 0.0;
+            for (int b = 0; b < 27; ++b)
+                s += D[4][i + 3 * b] * (Mf[3][b] - ratio * M3A[b]);
+            dL1[i] += G / 6.0 * s;
+        }
+    } else {
+        /* p = 2: -(G/2) D3 : [M2_B + (M0_B / M0_A) M2_A] */
+        real M2A[9];
+        unpack(MA, 2, M2A);
+        real ratio2 = MB[0] / MA[0];
+        for (int i = 0; i < 3; ++i) {
+            real s = 0.0;
+            for (int b = 0; b < 9; ++b)
+                s += D[3][i + 3 * b] * (Mf[2][b] + ratio2 * M2A[b]);
+            dL1[i] -= G / 2.0 * s;
+        }
     }
 }
 
@@ -423,7 +445,7 @@ static void o_m2l_target(const otree *t, const real *M, const real *com,
 {
     int level = o_level(t, i);
     int a_leaf = o_is_leaf(t, i);
-    int nmax = a_leaf ? 1 : 3;
+    int nmax = a_leaf ? 1 : t->order;
     int64_t gA[3];
     o_gcell(t, i, c, gA);
     real MA[NCOMP], XA[3];
@@ -447,7 +469,7 @@ static void o_m2l_target(const otree *t, const real *M, const real *com,
             real MB[NCOMP], XB[3];
             for (int k = 0; k < NCOMP; ++k) MB[k] = M[(j * NCOMP + k) * NCELL + cb];
             for (int a = 0; a < 3; ++a) XB[a] = com[(j * 3 + a) * NCELL + cb];
-            o_interact(t->G, MA, XA, MB, XB, nmax, Lp, d1);
+            o_interact(t->G, MA, XA, MB, XB, nmax, t->order, Lp, d1);
             cnt[kind - 1]++;
         }
     }
@@ -732,16 +754,16 @@ int oracle_forces(const int32_t *desc, int64_t n, const double *cfg,
  * 20-component Taylor coefficients (orders above nmax left zero) and the
  * correction dL1[3].
  */
-int oracle_pair_m2l(double G, const real *MA, const real *XA,
+int oracle_pair_m2l(double G, int order, const real *MA, const real *XA,
                     const real *MB, const real *XB, int a_leaf,
                     real *L20, real *dL1)
 {
-    int nmax = a_leaf ? 1 : 3;
+    int nmax = a_leaf ? 1 : order;
     real Lf[4][27];
     memset(Lf, 0, sizeof Lf);
     real *Lp[4] = { Lf[0], Lf[1], Lf[2], Lf[3] };
     real d1[3] = { 0.0, 0.0, 0.0 };
-    o_interact(G, MA, XA, MB, XB, nmax, Lp, d1);
+    o_interact(G, MA, XA, MB, XB, nmax, order, Lp, d1);
     memset(L20, 0, sizeof(real) * NCOMP);
     for (int n = 0; n <= nmax; ++n) pack(Lf[n], n, L20);
     for (int a = 0; a < 3; ++a) dL1[a] = d1[a];

@@ -65,7 +65,7 @@ def _bind(lib):
     lib.oracle_coverage.argtypes = [P, I64, P, P, P]
     lib.oracle_downward.argtypes = [P, I64, P, P, P, P, P, P]
     lib.oracle_forces.argtypes = [P, I64, P, P, P, P, P, P, P]
-    lib.oracle_pair_m2l.argtypes = [ctypes.c_double, P, P, P, P, ctypes.c_int, P, P]
+    lib.oracle_pair_m2l.argtypes = [ctypes.c_double, ctypes.c_int, P, P, P, P, ctypes.c_int, P, P]
     lib.oracle_dtensors.argtypes = [P, P, P, P, P, P]
     return lib
 
@@ -123,8 +123,8 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def _cfg(theta, G, box_lo, box_size):
-    return np.array([theta, G, box_lo[0], box_lo[1], box_lo[2], box_size],
+def _cfg(theta, G, box_lo, box_size, order=3):
+    return np.array([theta, G, box_lo[0], box_lo[1], box_lo[2], box_size, order],
                     dtype=np.float64)
 
 
@@ -133,18 +133,22 @@ def n_trees(desc):
 
 
 class Tree:
-    """A node-descriptor array plus the solve parameters (theta, G, box)."""
+    """A node-descriptor array plus the solve parameters (theta, G, box, and
+    the expansion order: 3, or 2)."""
 
-    def __init__(self, desc, theta, G=1.0, box_lo=(0.0, 0.0, 0.0), box_size=1.0):
+    def __init__(self, desc, theta, G=1.0, box_lo=(0.0, 0.0, 0.0), box_size=1.0, order=3):
+        if order not in (2, 3):
+            raise ValueError("order must be 2 or 3")
         self.desc = np.ascontiguousarray(desc, dtype=np.int32)
         self.n = len(self.desc)
-        self.cfg = _cfg(theta, G, box_lo, box_size)
+        self.order = order
+        self.cfg = _cfg(theta, G, box_lo, box_size, order)
         self.n_leaf = int((self.desc[:, 5] < 0).sum())
         self.n_trees = n_trees(self.desc)
 
     @classmethod
     def from_config(cls, c):
-        return cls(c["desc"], c["theta"], c["G"], c["box_lo"], c["box_size"])
+        return cls(c["desc"], c["theta"], c["G"], c["box_lo"], c["box_size"], c.get("order", 3))
 
 
 def upward(tree, rho):
@@ -231,11 +235,11 @@ def solve(tree, rho, n_threads=0):
                 phi=phi, g=g, totals=tot)
 
 
-def pair_m2l(MA, XA, MB, XB, a_leaf, G=1.0):
-    """One interaction A <- B: returns (L20, dL1)."""
+def pair_m2l(MA, XA, MB, XB, a_leaf, G=1.0, order=3):
+    """One interaction A <- B at expansion order 3 (or 2): returns (L20, dL1)."""
     L = np.zeros(NCOMP)
     d = np.zeros(3)
-    _lib().oracle_pair_m2l(float(G), _p(_f64(MA)), _p(_f64(XA)), _p(_f64(MB)),
+    _lib().oracle_pair_m2l(float(G), int(order), _p(_f64(MA)), _p(_f64(XA)), _p(_f64(MB)),
                            _p(_f64(XB)), int(bool(a_leaf)), _p(L), _p(d))
     return L, d
 

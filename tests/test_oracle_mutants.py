@@ -56,8 +56,8 @@ MUTANTS = [
      "double coef = -G * sgn * INV_FACT[m];", "double coef = -G * sgn * INV_FACT[m + 1];",
      ["multipole_orders", "monopole_fourth_order", "all_near"]),
     ("M2L: truncation n + m < 3 instead of <= 3",
-     "for (int m = 0; n + m <= 3; ++m) {\n            int nb = ipow3(m);\n            double sgn",
-     "for (int m = 0; n + m < 3; ++m) {\n            int nb = ipow3(m);\n            double sgn",
+     "for (int m = 0; n + m <= order; ++m) {\n            int nb = ipow3(m);\n            double sgn",
+     "for (int m = 0; n + m < order; ++m) {\n            int nb = ipow3(m);\n            double sgn",
      ["monopole_fourth_order", "multipole_orders"]),
     # the angular-momentum correction
     ("correction: sign flipped", "dL1[i] += G / 6.0 * s;", "dL1[i] -= G / 6.0 * s;",
@@ -66,6 +66,10 @@ MUTANTS = [
      "real ratio = MA[0] / MB[0];", ["torque_pair", "invariants_cfg1"]),
     ("correction: factor 1/2 instead of 1/6", "dL1[i] += G / 6.0 * s;",
      "dL1[i] += G / 2.0 * s;", ["torque_pair", "invariants_cfg1"]),
+    ("order-2 correction: the target's share with the order-3 sign",
+     "(Mf[2][b] + ratio2 * M2A[b])", "(Mf[2][b] - ratio2 * M2A[b])", ["order2_pair"]),
+    ("order-2 correction: sign flipped", "dL1[i] -= G / 2.0 * s;", "dL1[i] += G / 2.0 * s;",
+     ["order2_pair"]),
     # the opening rule
     ("opening: well separated at equality", "*far = th2 * o2 > 1.0;",
      "*far = th2 * o2 >= 1.0;", ["stencil_05", "stencil_035"]),
@@ -105,6 +109,7 @@ MUTANTS = [
 ]
 
 PINS = {
+    "order2_pair": pins.test_order2_two_cluster_momentum_and_torque,
     "dtensors_fd": pins.test_dtensors_match_finite_differences,
     "dtensors_first_order": pins.test_dtensors_first_order_closed_form,
     "multipole_orders": pins.test_multipole_source_far_field_orders,

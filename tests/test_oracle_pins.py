@@ -205,11 +205,11 @@ def test_multipole_source_far_field_orders():
         assert 6.5 < a / b < 9.5
 
 
-def _pair_forces(xa, ma, xb, mb, use_corr=True, corr_sign=1.0):
+def _pair_forces(xa, ma, xb, mb, use_corr=True, corr_sign=1.0, order=3):
     MA, XA = _moments20(xa, ma)
     MB, XB = _moments20(xb, mb)
-    LA, dA = O.pair_m2l(MA, XA, MB, XB, a_leaf=False)
-    LB, dB = O.pair_m2l(MB, XB, MA, XA, a_leaf=False)
+    LA, dA = O.pair_m2l(MA, XA, MB, XB, a_leaf=False, order=order)
+    LB, dB = O.pair_m2l(MB, XB, MA, XA, a_leaf=False, order=order)
     f = []
     for x, m, L, dl, X in ((xa, ma, LA, dA, XA), (xb, mb, LB, dB, XB)):
         for p in range(len(x)):
@@ -238,6 +238,64 @@ def test_two_cluster_momentum_and_torque():
     assert T0 > 1e-6
     _, Tm = _pair_forces(xa, ma, xb, mb, corr_sign=-1.0)
     assert Tm > 1e-6
+
+
+# ------------------------------------------------ expansion order 2
+
+def test_order2_two_cluster_momentum_and_torque():
+    """At order 2 (truncation n + m <= 2) the correction is the dropped
+    n = 1, m = 2 term with the target's share added, because D3 is odd:
+    net force and torque then vanish to rounding; without the correction
+    the torque is large (the order-3 sign of the target's share would break
+    even the net force: a planted mistake in test_oracle_mutants)."""
+    rng = np.random.default_rng(12)
+    xa, ma = _cluster(rng, 30, np.array([0.1, 0.2, 0.3]), 0.3)
+    xb, mb = _cluster(rng, 25, np.array([1.4, -0.7, 0.9]), 0.35)
+    F, T = _pair_forces(xa, ma, xb, mb, order=2)
+    assert F < 1e-14 and T < 1e-14
+    F0, T0 = _pair_forces(xa, ma, xb, mb, use_corr=False, order=2)
+    assert F0 < 1e-14 and T0 > 1e-4
+
+
+def test_order2_point_source_error_orders():
+    """A point source at order 2: the local quadratic misses 1/|x| by O(r^3)
+    and the field by O(r^2)."""
+    G, m = 1.7, 2.3
+    XB = np.array([0.1, 0.2, -0.3])
+    XA = XB + np.array([1.0, -0.6, 0.8])
+    MA, _ = _point(1.0, XA)
+    MB, _ = _point(m, XB)
+    L, _ = O.pair_m2l(MA, XA, MB, XB, a_leaf=False, G=G, order=2)
+    assert np.all(L[10:20] == 0.0)                  # no third-order coefficients
+    direction = np.array([0.37, 0.51, -0.78])
+    errs, gerrs = [], []
+    for eps in (0.04, 0.02, 0.01):
+        r = eps * direction
+        d = XA + r - XB
+        errs.append(abs(taylor_phi(L, r) + G * m / np.linalg.norm(d)))
+        gerrs.append(np.linalg.norm(-taylor_grad(L, r) + G * m * d / np.linalg.norm(d) ** 3))
+    for a, b in zip(errs, errs[1:]):
+        assert 6.5 < a / b < 9.5
+    for a, b in zip(gerrs, gerrs[1:]):
+        assert 3.2 < a / b < 4.8
+
+
+def test_order2_solve_conserves_and_is_less_accurate():
+    """The whole order-2 solve of cfg1: net force and torque at rounding
+    level; against the direct sum its field error lies above order 3's."""
+    c = make_config("cfg1")
+    pos = leaf_cell_centres(c["desc"]).reshape(-1, 3)
+    m = leaf_masses(c["desc"], c["rho"]).reshape(-1)
+    _, g_direct = direct_sum(pos, m)
+    errs = {}
+    for order in (2, 3):
+        t = O.Tree(c["desc"], c["theta"], order=order)
+        sol = O.solve(t, c["rho"])
+        tot = sol["totals"][0]
+        assert np.linalg.norm(tot[0:3]) / tot[6] < 1e-13
+        assert np.linalg.norm(tot[3:6]) / tot[7] < 1e-13
+        errs[order] = np.abs(flat_g(sol["g"]) - g_direct).max() / np.abs(g_direct).max()
+    assert errs[3] < errs[2] < 1e-1, errs
 
 
 # ---------------------------------------------------------- upward

@@ -97,7 +97,13 @@ typedef struct {
     int32_t precision;               /* FMM_FP64, FMM_MIXED or FMM_DFLOAT */
     int32_t max_level;               /* deepest level allowed (1..20) */
     int32_t flags;                   /* FMM_FLAG_* */
-    int32_t reserved;
+    int32_t order;                   /* expansion order p: 3 (0 selects it), or 2: the
+                                        same-level truncation n + m <= p, Taylor
+                                        coefficients up to order p (the third-order
+                                        slots of L stay zero at p = 2), and the
+                                        correction's dropped term n = 1, m = p with
+                                        the target's share signed (-1)^p (see
+                                        fmm_m2l) */
 } fmm_config;
 
 /* One octree node.  child[k] covers octant (k&1, (k>>1)&1, (k>>2)&1) of the
@@ -207,10 +213,14 @@ int fmm_upward(fmm_tree_t tree, const double *rho, double *M, double *com,
 /*
  * Same-level pass (Sec. 4.3, second step; Sec. 5.1 runs it on the GPU).
  * Every cell A gathers, from every source cell B the opening rule selects,
- *   L^(n)_A += -G sum_{m: n+m<=3} ((-1)^m/m!) M_B^(m) . D^(n+m)(X_A - X_B),
- * D^(k) the k-th derivative tensor of 1/|R|, plus the angular-momentum
- * correction
- *   dL1_A,i += (G/6) sum_jkl D^(4)_ijkl(X_A - X_B) [M_B^(3) - (M_B^(0)/M_A^(0)) M_A^(3)]_jkl.
+ *   L^(n)_A += -G sum_{m: n+m<=p} ((-1)^m/m!) M_B^(m) . D^(n+m)(X_A - X_B),
+ * D^(k) the k-th derivative tensor of 1/|R|, p the expansion order (3 by
+ * default), plus the angular-momentum correction
+ *   p = 3:  dL1_A,i += (G/6) sum_jkl D^(4)_ijkl(X_A - X_B) [M_B^(3) - (M_B^(0)/M_A^(0)) M_A^(3)]_jkl,
+ *   p = 2:  dL1_A,i -= (G/2) sum_jk D^(3)_ijk(X_A - X_B) [M_B^(2) + (M_B^(0)/M_A^(0)) M_A^(2)]_jk
+ * (the term n = 1, m = p that the truncation drops; the target's share
+ * makes each pair's forces and torques cancel, its sign following the
+ * parity of D^(p+1)).
  * Leaf targets only get orders 0 and 1 (nothing below them needs more).
  *   M, com: as written by fmm_upward (read).
  *   L:      device [n_nodes][20][512], written: double (FMM_FP64) or the

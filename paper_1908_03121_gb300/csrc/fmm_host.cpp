@@ -135,6 +135,8 @@ static int validate_config(const fmm_config *cfg)
         return fail(FMM_ERR_INVALID_ARG, "precision must be FMM_FP64, FMM_MIXED or FMM_DFLOAT");
     if (cfg->max_level < 1 || cfg->max_level > 20)
         return fail(FMM_ERR_INVALID_ARG, "max_level must lie in 1..20");
+    if (cfg->order != 0 && cfg->order != 2 && cfg->order != 3)
+        return fail(FMM_ERR_INVALID_ARG, "order must be 2 or 3 (0 selects 3)");
     return FMM_OK;
 }
 
@@ -347,7 +349,12 @@ static void slot_tables(const fmm_tree_s *t, std::vector<int64_t> &tab)
 //   monopole<-monopole:   tabulated weights, 4 FMAs                        ->   8
 //   monopole<-multipole:  orders 0-1 (62) + correction sum (42)            -> 199
 // (Sec. 4.3 quotes 455 and 12 for the paper's own kernels.)
+// Order 2 (no D4, no third orders): derivative tensors 51; multipole<-
+// multipole 6 + 51 + orders 0-2 (28) + correction weights and sum (40) -> 125;
+// multipole<-monopole 3 + 51 + 18 + 35 -> 107; monopole<-multipole
+// 3 + 51 + 18 + 30 -> 102.
 static const double kFlops[4] = {240.0, 176.0, 8.0, 199.0};
+static const double kFlops2[4] = {125.0, 107.0, 8.0, 102.0};
 
 // Monopole<-multipole work as pair lists: for every cell of a leaf node next
 // to a refined node, the stencil entries whose source cell is refined, each
@@ -655,6 +662,7 @@ int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config
     fmm_tree_s *t = new (std::nothrow) fmm_tree_s();
     if (!t) return fail(FMM_ERR_NOMEM, "host allocation failed");
     t->cfg = *cfg;
+    if (t->cfg.order == 0) t->cfg.order = 3;
     t->n = n_nodes;
     t->host_only = (cfg->flags & FMM_FLAG_HOST_ONLY) != 0;
     std::vector<std::unordered_map<uint64_t, int32_t>> maps;
@@ -792,7 +800,7 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     const Plan &P = t->plan;
     for (int k = 0; k < 4; ++k) {
         o->interactions[k] = P.interactions[k];
-        o->flops_per_interaction[k] = kFlops[k];
+        o->flops_per_interaction[k] = t->cfg.order == 2 ? kFlops2[k] : kFlops[k];
     }
     o->stencil_far = P.n_far[0];
     o->stencil_near = P.n_near[0];

@@ -555,30 +555,54 @@ __device__ __forceinline__ void zero_moments(Src<T> &s)
 // add that sum to the chunk sum once, so every source costs one rounding at
 // the chunk sum's magnitude; orders 2-3 and the correction take each product
 // straight into their sums as one fused multiply-add.
-template <typename T, bool SRC_MP, class LA, class SA>
-__device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const T a3A[7], LA &L,
+//
+// Expansion order 2 (ORDER = 2; truncation n + m <= 2): L0 -= M0 D0 + B2.D2,
+// L1 -= M0 D1, L2 -= M0 D2, no L3, and the correction is the dropped
+// n = 1, m = 2 term with the target's share added (D3 is odd):
+//   S_i -= sum_k (B2_B + M0_B a2_A)_k D3[i, k],  a2_A = B2_A / M0_A
+// (aA holds a2_A in its first five entries then).
+template <typename T, bool SRC_MP, int ORDER = 3, class LA, class SA>
+__device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const T aA[7], LA &L,
                                        SA &S)
 {
     DTraceless<T> D;
-    D.template eval<true>(Rx, Ry, Rz);
+    D.template eval<ORDER == 3>(Rx, Ry, Rz);
     const T nm0 = -s.m0;
     T a = nm0 * D.D0;
     if (SRC_MP) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) a = fmadd_u(-s.B2[k], D.D2[k], a);
+        if (ORDER == 3) {
 #pragma unroll
-        for (int q = 0; q < 7; ++q) a = fmadd_u(s.B3[q], D.D3[q], a);
+            for (int q = 0; q < 7; ++q) a = fmadd_u(s.B3[q], D.D3[q], a);
+        }
     }
     L.part[0] = add_u(L.part[0], renorm(a));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         T b = nm0 * D.D1[i];
-        if (SRC_MP) {
+        if (SRC_MP && ORDER == 3) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) b = fmadd_u(-s.B2[k], D.d3slice(i, k), b);
         }
         L.part[1 + i] = add_u(L.part[1 + i], renorm(b));
     }
+    if constexpr (ORDER == 2) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) L.part[4 + k] = fmadd_u(nm0, D.D2[k], L.part[4 + k]);
+        T wn[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) wn[k] = SRC_MP ? fmadd(nm0, aA[k], -s.B2[k]) : nm0 * aA[k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T c = S.part[i];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) c = fmadd_u(wn[k], D.d3slice(i, k), c);
+            S.part[i] = renorm(c);
+        }
+        return;
+    }
+    const T *a3A = aA;
     if constexpr (kF32<T>) {
         // orders 2-3 (12 components): the pairs in which the derivative
         // tensors come out of DTraceless<float> (xx yy | xz yz of D2, xxx yyy
@@ -621,42 +645,57 @@ __device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const 
 
 // One multipole source into a leaf target (orders 0-1 and the correction;
 // the target has no third moment)
-template <typename T>
+// (ORDER = 2: L0 -= M0 D0 + B2.D2, L1 -= M0 D1, S_i -= B2 . D3[i, .])
+template <typename T, int ORDER = 3>
 __device__ __forceinline__ void acc_mx(T Rx, T Ry, T Rz, const Src<T> &s, Acc<T, 4> &L,
                                        Acc<T, 3> &S)
 {
     DTraceless<T> D;
-    D.template eval<true>(Rx, Ry, Rz);
+    D.template eval<ORDER == 3>(Rx, Ry, Rz);
     T a = -s.m0 * D.D0;
 #pragma unroll
     for (int k = 0; k < 5; ++k) a = fmadd_u(-s.B2[k], D.D2[k], a);
+    if (ORDER == 3) {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) a = fmadd_u(s.B3[q], D.D3[q], a);
+        for (int q = 0; q < 7; ++q) a = fmadd_u(s.B3[q], D.D3[q], a);
+    }
     L.part[0] = add_u(L.part[0], renorm(a));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         T b = -s.m0 * D.D1[i];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) b = fmadd_u(-s.B2[k], D.d3slice(i, k), b);
-        L.part[1 + i] = add_u(L.part[1 + i], renorm(b));
         T c = S.part[i];
+        if (ORDER == 3) {
 #pragma unroll
-        for (int q = 0; q < 7; ++q) c = fmadd_u(s.B3[q], D.U[i][q], c);
+            for (int k = 0; k < 5; ++k) b = fmadd_u(-s.B2[k], D.d3slice(i, k), b);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) c = fmadd_u(s.B3[q], D.U[i][q], c);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) c = fmadd_u(-s.B2[k], D.d3slice(i, k), c);
+        }
+        L.part[1 + i] = add_u(L.part[1 + i], renorm(b));
         S.part[i] = renorm(c);
     }
 }
 
-// own packed data of a multipole target: centre-of-mass offset and a3 = B3/M0
-template <typename T>
-__device__ __forceinline__ void load_target(const KParams &P, int row, int pi, T dA[3], T a3A[7])
+// own packed data of a multipole target: centre-of-mass offset and
+// a3 = B3/M0 (order 3) or a2 = B2/M0 in the first five entries (order 2)
+template <typename T, int ORDER = 3>
+__device__ __forceinline__ void load_target(const KParams &P, int row, int pi, T dA[3], T aA[7])
 {
     Src<T> own;
     load_source<T>(P, row, pi, own);
     const T im0 = T(1) / own.m0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) dA[a] = own.d[a];
+    if (ORDER == 3) {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) a3A[q] = own.B3[q] * im0;
+        for (int q = 0; q < 7; ++q) aA[q] = own.B3[q] * im0;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) aA[q] = own.B2[q] * im0;
+        aA[5] = aA[6] = T(0);
+    }
 }
 
 __device__ __forceinline__ double to_double(float v) { return double(v); }
@@ -673,7 +712,7 @@ __device__ __forceinline__ double acc_value(const SA &S, int i)
 // One leaf target cell with refined sources (one lane): its own list of
 // (packed-moment offset, stencil entry) pairs, orders 0-1 and the correction
 // added to what the monopole kernel stored for the cell.
-template <typename T>
+template <typename T, int ORDER = 3>
 __device__ __forceinline__ void mx_target(const KParams &P, int t)
 {
     const T *mp = static_cast<const T *>(P.mp);
@@ -691,7 +730,7 @@ __device__ __forceinline__ void mx_target(const KParams &P, int t)
         const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + pr.y));
         Src<T> src;
         load_source_at<T>(mp + pr.x, src);
-        acc_mx<T>(-T(E.x) - src.d[0], -T(E.y) - src.d[1], -T(E.z) - src.d[2], src, L, S);
+        acc_mx<T, ORDER>(-T(E.x) - src.d[0], -T(E.y) - src.d[1], -T(E.z) - src.d[2], src, L, S);
         if (++done == kChunk) {
             L.flush();
             S.flush();
@@ -726,7 +765,7 @@ __device__ __forceinline__ void mx_target(const KParams &P, int t)
 }
 
 // ------------------------------------------------------------ mp_kernel
-template <typename T>
+template <typename T, int ORDER>
 // float: three CTAs per SM (at most 85 registers): the compensation pairs,
 // touched once per chunk, live in shared memory after the window
 __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P)
@@ -758,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
             const int ax = 2 * cx + px, ay = 2 * cy + py, az = 2 * cz + pz;
             const int base = cx + P.py * cy + P.pz * cz;
             T dA[3], a3A[7];
-            load_target<T>(P, ti.mp_row, parity_index(ax, ay, az), dA, a3A);
+            load_target<T, ORDER>(P, ti.mp_row, parity_index(ax, ay, az), dA, a3A);
             typename MpAcc<T, 16>::type L;
             typename MpAcc<T, 3>::type S;
             if constexpr (kF32<T>) {
@@ -781,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
                         src.m0 = wv;
                         zero_moments<T>(src);
                     }
-                    acc_mp<T, true>(dA[0] - src.d[0] - T(E.x), dA[1] - src.d[1] - T(E.y),
+                    acc_mp<T, true, ORDER>(dA[0] - src.d[0] - T(E.x), dA[1] - src.d[1] - T(E.y),
                                     dA[2] - src.d[2] - T(E.z), src, a3A, L, S);
                 }
                 L.flush();
@@ -796,7 +835,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
                     const T wv = W[base + __float_as_int(E.w)];
                     Src<T> src;
                     src.m0 = window_decode<T>(wv) >= 0 ? T(0) : wv;
-                    acc_mp<T, false>(dA[0] - T(E.x), dA[1] - T(E.y), dA[2] - T(E.z), src, a3A,
+                    acc_mp<T, false, ORDER>(dA[0] - T(E.x), dA[1] - T(E.y), dA[2] - T(E.z), src, a3A,
                                      L, S);
                 }
                 L.flush();
@@ -821,7 +860,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
             if (lane == 0) w = atomicAdd(P.mx_counter, 1);
             w = __shfl_sync(0xffffffffu, w, 0);
             if (w * 32 >= P.n_mx) break;
-            if (w * 32 + lane < P.n_mx) mx_target<T>(P, w * 32 + lane);
+            if (w * 32 + lane < P.n_mx) mx_target<T, ORDER>(P, w * 32 + lane);
         }
     }
 }
@@ -1104,7 +1143,7 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
 // lanes masked off, each lane takes one target cell and walks that cell's
 // own list of (packed-moment offset, stencil entry) pairs, built on the
 // host; targets are sorted by list length, so a warp's lanes finish together.
-template <typename T>
+template <typename T, int ORDER>
 __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
 {
     const int lane = threadIdx.x & 31;
@@ -1112,7 +1151,7 @@ __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
     for (int w = int(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); w * 32 < P.n_items;
          w += warps) {
         const int t = w * 32 + lane;
-        if (t < P.n_items) mx_target<T>(P, t);
+        if (t < P.n_items) mx_target<T, ORDER>(P, t);
     }
 }
 
@@ -1126,7 +1165,7 @@ constexpr int kRootSlices = 8;
 constexpr int kRootThreads = 32 * kRootSlices;
 constexpr int kRootGroups = NCELL / 32;
 
-template <typename T>
+template <typename T, int ORDER>
 __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
 {
     constexpr int NV = 16 + 3;                      // L (traceless), S
@@ -1140,7 +1179,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
     const int cell = blockIdx.y * 32 + lane;
     const int ax = cell & 7, ay = (cell >> 3) & 7, az = cell >> 6;
     T dA[3] = {T(0), T(0), T(0)}, a3A[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-    if (!leaf) load_target<T>(P, ti.mp_row, parity_index(ax, ay, az), dA, a3A);
+    if (!leaf) load_target<T, ORDER>(P, ti.mp_row, parity_index(ax, ay, az), dA, a3A);
     Acc<T, 16> L;
     Acc<T, 3> S;
     L.zero();
@@ -1159,7 +1198,7 @@ __global__ void __launch_bounds__(kRootThreads) root_kernel(KParams P)
             src.m0 = mass[size_t(node) * NCELL + pi];
             zero_moments<T>(src);
         }
-        acc_mp<T, true>(dA[0] - src.d[0] - T(ox), dA[1] - src.d[1] - T(oy),
+        acc_mp<T, true, ORDER>(dA[0] - src.d[0] - T(ox), dA[1] - src.d[1] - T(oy),
                         dA[2] - src.d[2] - T(oz), src, a3A, L, S);
         if (++done == kChunk) {
             L.flush();
@@ -1219,10 +1258,11 @@ cudaError_t allow_smem(Kern k, size_t bytes, size_t &done)
 
 template <typename T>
 struct Kernels {
+    template <int ORDER>
     static cudaError_t mp(size_t bytes)
     {
         static size_t done = 0;
-        return allow_smem(mp_kernel<T>, bytes, done);
+        return allow_smem(mp_kernel<T, ORDER>, bytes, done);
     }
     static cudaError_t mp2(size_t bytes)
     {
@@ -1278,7 +1318,7 @@ cudaError_t launch_mono(const KParams &K, size_t wbytes, int sms, int cap, cudaS
     }
 }
 
-template <typename T>
+template <typename T, int ORDER>
 cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cudaStream_t s,
                        int *n_launches, int parts)
 {
@@ -1314,7 +1354,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     // mp_kernel: one window (masses of leaf sources, moment offsets of
     // refined ones); float adds its compensation pairs, [7][2][threads]
     const size_t mp_bytes = wbytes + (kF32<T> ? size_t(kMpPairs) * 2 * kThreads * sizeof(float) : 0);
-    cudaError_t e = Kernels<T>::mp(mp_bytes);
+    cudaError_t e = Kernels<T>::template mp<ORDER>(mp_bytes);
     if (e != cudaSuccess) return e;
     if (parts & M2L_RESET) {
         e = cudaMemsetAsync(d.counters, 0, 4 * sizeof(int32_t), s);
@@ -1330,7 +1370,7 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         R.list = d.lists + Pl.roots.off;
         R.n_items = int32_t(Pl.roots.count);
         timing_begin(t, FMM_K_ROOT, s);
-        root_kernel<T><<<dim3(unsigned(Pl.roots.count), kRootGroups), kRootThreads, 0, s>>>(R);
+        root_kernel<T, ORDER><<<dim3(unsigned(Pl.roots.count), kRootGroups), kRootThreads, 0, s>>>(R);
         timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1345,15 +1385,15 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
             K.mx_counter = d.counters + Q_MX;
         }
         timing_begin(t, FMM_K_MULTIPOLE, s);
-        if (kF32<T> && t->tuning.mp_pair_targets) {
+        if (kF32<T> && ORDER == 3 && t->tuning.mp_pair_targets) {
             // both target cells of a thread together (float only)
             const size_t b2 = wbytes + size_t(kMp2Pairs) * 2 * kThreads * sizeof(float);
             if ((e = Kernels<T>::mp2(b2)) != cudaSuccess) return e;
             int g = persistent_grid(mp2_kernel, b2, Pl.work_mp.count, sms, cap);
             mp2_kernel<<<g, kThreads, b2, s>>>(K);
         } else {
-            int g = persistent_grid(mp_kernel<T>, mp_bytes, Pl.work_mp.count, sms, cap);
-            mp_kernel<T><<<g, kThreads, mp_bytes, s>>>(K);
+            int g = persistent_grid(mp_kernel<T, ORDER>, mp_bytes, Pl.work_mp.count, sms, cap);
+            mp_kernel<T, ORDER><<<g, kThreads, mp_bytes, s>>>(K);
         }
         timing_end(t, s);
         ++nl;
@@ -1382,10 +1422,10 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
         KParams K = P;
         K.n_items = int32_t(Pl.n_mx_targets);
         const int64_t warps = (K.n_items + 31) / 32;
-        int g = persistent_grid(mx_kernel<T>, 0, (warps + kThreads / 32 - 1) / (kThreads / 32), sms,
+        int g = persistent_grid(mx_kernel<T, ORDER>, 0, (warps + kThreads / 32 - 1) / (kThreads / 32), sms,
                                 cap);
         timing_begin(t, FMM_K_MONO_MULTI, s);
-        mx_kernel<T><<<g, kThreads, 0, s>>>(K);
+        mx_kernel<T, ORDER><<<g, kThreads, 0, s>>>(K);
         timing_end(t, s);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1431,10 +1471,17 @@ cudaError_t launch_pack(const fmm_tree_s *t, const double *M, const double *com,
 cudaError_t launch_m2l(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cudaStream_t s,
                        int *n_launches, int parts)
 {
+    const bool o2 = t->cfg.order == 2;
     switch (t->cfg.precision) {
-    case FMM_MIXED: return launch_all<float>(t, L, Lc, dL1, s, n_launches, parts);
-    case FMM_DFLOAT: return launch_all<dfloat>(t, L, Lc, dL1, s, n_launches, parts);
-    default: return launch_all<double>(t, L, Lc, dL1, s, n_launches, parts);
+    case FMM_MIXED:
+        return o2 ? launch_all<float, 2>(t, L, Lc, dL1, s, n_launches, parts)
+                  : launch_all<float, 3>(t, L, Lc, dL1, s, n_launches, parts);
+    case FMM_DFLOAT:
+        return o2 ? launch_all<dfloat, 2>(t, L, Lc, dL1, s, n_launches, parts)
+                  : launch_all<dfloat, 3>(t, L, Lc, dL1, s, n_launches, parts);
+    default:
+        return o2 ? launch_all<double, 2>(t, L, Lc, dL1, s, n_launches, parts)
+                  : launch_all<double, 3>(t, L, Lc, dL1, s, n_launches, parts);
     }
 }
 

@@ -50,7 +50,7 @@ class FmmConfig(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("G", ctypes.c_double),
                 ("box_lo", ctypes.c_double * 3), ("box_size", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("max_level", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("order", ctypes.c_int32)]
 
 
 class FmmSizes(ctypes.Structure):
@@ -199,7 +199,7 @@ class Tree:
 
 
 def fmm_build_tree(desc, theta, G=1.0, box_lo=(0.0, 0.0, 0.0), box_size=1.0,
-                   precision=FMM_FP64, max_level=20, host_only=False, timing=False):
+                   precision=FMM_FP64, max_level=20, host_only=False, timing=False, order=3):
     lib = load()
     d = np.ascontiguousarray(desc, dtype=np.int32)
     if d.ndim != 2 or d.shape[1] != 14:
@@ -208,7 +208,7 @@ def fmm_build_tree(desc, theta, G=1.0, box_lo=(0.0, 0.0, 0.0), box_size=1.0,
         precision = PRECISIONS[precision]
     flags = (FMM_FLAG_HOST_ONLY if host_only else 0) | (FMM_FLAG_TIMING if timing else 0)
     cfg = FmmConfig(float(theta), float(G), (ctypes.c_double * 3)(*box_lo), float(box_size),
-                    int(precision), int(max_level), flags, 0)
+                    int(precision), int(max_level), flags, int(order))
     h = ctypes.c_void_p()
     _check(lib.fmm_build_tree(d.ctypes.data_as(ctypes.c_void_p), len(d), ctypes.byref(cfg),
                               ctypes.byref(h)))
@@ -370,9 +370,10 @@ class Solver:
     """
 
     def __init__(self, desc, theta, precision="mixed", G=1.0, box_lo=(0.0, 0.0, 0.0),
-                 box_size=1.0, device="cuda", timing=False):
+                 box_size=1.0, device="cuda", timing=False, order=3):
         import torch
-        self.tree = fmm_build_tree(desc, theta, G, box_lo, box_size, precision, timing=timing)
+        self.tree = fmm_build_tree(desc, theta, G, box_lo, box_size, precision, timing=timing,
+                                   order=order)
         s = self.tree.sizes
         n, nl, nt = s["n_nodes"], s["n_leaf"], s["n_trees"]
         self.precision = s["precision"]

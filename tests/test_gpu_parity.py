@@ -575,3 +575,57 @@ def test_full_size_sampled(name):
     assert np.all(tree_force(tot) <= DFLOAT_CONSERVATION), tree_force(tot)
     assert np.all(tree_torque(tot) <= DFLOAT_CONSERVATION), tree_torque(tot)
     s.close()
+
+
+# ------------------------------------------------- expansion order 2
+_ORACLE2 = {}
+
+
+def oracle_solution_order2(name):
+    if name not in _ORACLE2:
+        c = dict(small_case(name), order=2)
+        _ORACLE2[name] = (c, O.solve(O.Tree.from_config(c), c["rho"]))
+    return _ORACLE2[name]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "dfloat", "mixed"])
+@pytest.mark.parametrize("name", ["cfg1", "adaptive4", "batch3", "cfg2"])
+def test_order2_end_to_end(name, precision):
+    """Order 2 (truncation n + m <= 2, its own correction) against the
+    oracle at order 2: FP64 and double-float to 1e-12 with net force and
+    torque 1e-12; mixed to force error 1e-6.  The step goes through fmm_step
+    and equals the four pass calls bit for bit."""
+    c, ref = oracle_solution_order2(name)
+    s = F.Solver(c["desc"], c["theta"], precision=precision, order=2)
+    s.rho.copy_(dev(c["rho"]))
+    s.step()
+    torch.cuda.synchronize()
+    g, phi, tot = host(s.g).copy(), host(s.phi).copy(), host(s.totals).copy()
+    tol = FORCE_TOL if precision == "mixed" else FP64_TOL
+    assert rel_err(g, ref["g"]) <= tol
+    assert rel_err(phi, ref["phi"]) <= tol
+    if precision != "mixed":
+        assert np.all(tree_force(tot) <= CONSERVATION_TARGET), tree_force(tot)
+        assert np.all(tree_torque(tot) <= CONSERVATION_TARGET), tree_torque(tot)
+    s.step_passes()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(s.g), g) and np.array_equal(host(s.totals), tot)
+    s.close()
+
+
+def test_order2_same_level_fp64():
+    """The order-2 same-level pass from the oracle's moments: every order
+    each node defines (the third-order slots zero) and the correction."""
+    c, ref = oracle_solution_order2("adaptive4")
+    s = F.Solver(c["desc"], c["theta"], precision="fp64", order=2)
+    s.M.copy_(dev(ref["M"]))
+    s.com.copy_(dev(ref["com"]))
+    s.m2l()
+    torch.cuda.synchronize()
+    L = level_to_phys(host(s.L), c["desc"])
+    assert_L_close(L, ref["L"], c["desc"], FP64_TOL)
+    refined = c["desc"][:, 5] >= 0
+    assert np.all(L[refined][:, 10:20] == 0.0) and np.all(ref["L"][:, 10:20] == 0.0)
+    h = widths(c["desc"])[:, None, None]
+    assert rel_err(host(s.dL1) * h ** -2, ref["dL1"]) <= FP64_TOL
+    s.close()

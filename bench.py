@@ -362,6 +362,54 @@ def _graph_ms(torch, solver, steps, flush, stream):
     return float(np.median(per))
 
 
+def _direct_field(pos, m, G=1.0):
+    """O(N^2) point-mass field at the points (self term excluded), numpy."""
+    g = np.zeros_like(pos)
+    for s0 in range(0, len(pos), 256):
+        d = pos[s0:s0 + 256, None, :] - pos[None, :, :]
+        r2 = (d * d).sum(-1)
+        idx = np.arange(s0, min(s0 + 256, len(pos)))
+        r2[idx - s0, idx] = np.inf
+        g[s0:s0 + 256] = -G * ((m[None, :] / r2 ** 1.5)[:, :, None] * d).sum(1)
+    return g
+
+
+def order_sweep(torch, F, autotune, c, flush, stream, steps=10):
+    """Expansion orders 2 and 3: the headline workload's mixed-precision step
+    (median ms, interactions/s; the field of order 2 against order 3), and
+    each order's FP64 field against the O(N^2) direct sum on the 4096-cell
+    two-Gaussian workload (cfg1)."""
+    from workloads import make_config, leaf_cell_centres
+    out = {}
+    g = {}
+    for order in (2, 3):
+        s = F.Solver(c["desc"], c["theta"], precision="mixed", order=order)
+        s.rho.copy_(torch.from_numpy(c["rho"]).cuda())
+        s.step()
+        autotune.tune(s)
+        ms = _graph_ms(torch, s, steps, flush, stream)
+        inter = int(sum(s.tree.stats["interactions"]))
+        fl = s.tree.stats["flops_per_interaction"]
+        g[order] = s.g.clone()
+        out[f"order_{order}"] = {"ms_per_step": ms, "value": inter / (ms / 1000.0), "unit": UNIT,
+                                 "flops_per_interaction": fl}
+        s.close()
+    out["field_difference_order2_vs_order3"] = float((g[2] - g[3]).abs().max() / g[3].abs().max())
+    c1 = make_config("cfg1")
+    pos = leaf_cell_centres(c1["desc"]).reshape(-1, 3)
+    h = 1.0 / 16.0
+    gd = _direct_field(pos, (c1["rho"] * h ** 3).reshape(-1))
+    for order in (2, 3):
+        s = F.Solver(c1["desc"], c1["theta"], precision="fp64", order=order)
+        s.rho.copy_(torch.from_numpy(c1["rho"]).cuda())
+        s.step()
+        gg = s.g.cpu().numpy().transpose(0, 2, 1).reshape(-1, 3)
+        out[f"order_{order}"]["cfg1_field_err_vs_direct_sum"] = float(
+            np.abs(gg - gd).max() / np.abs(gd).max())
+        s.close()
+    return out
+
+
 def dataflow_ab(torch, F, solver, best, flush, stream, steps=30):
     """The headline step with the dataflow downward pass on and off (all
     else at the tuned values), median ms of each."""
@@ -804,6 +852,7 @@ def run_ours(args):
         # against the level launches (N3), the field's time derivative (N2),
         # and self-consistent-field iterations (N4)
         if not args.no_extras:
+            result["order_sweep"] = order_sweep(torch, F, autotune, c, flush, stream)
             result["dataflow"] = dataflow_ab(torch, F, solver, best, flush, stream)
             result["time_derivative"] = time_derivative_timing(torch, F, autotune, c, flush)
             result["scf"] = scf_timing(torch, F)
@@ -816,12 +865,11 @@ def run_ours(args):
         for wname in extra:
             result[wname] = other_workload(torch, F, autotune, wname, args, flush, stream,
                                            accuracy_ref)
-        # the headline path against the FP64 oracle itself (cfg3 solved
-        # completely on the host)
-        if world == 1 and not args.no_oracle_accuracy and "cfg3" in accuracy_ref:
-            result["accuracy_vs_oracle"] = oracle_accuracy("cfg3", accuracy_ref["cfg3"])
-
         if world == 1 and not args.no_cpu_baseline:
+            # the CPU-oracle leg: the oracle's rate on the host cores, and its
+            # complete solve of cfg3 for every precision's error against it
+            if not args.no_oracle_accuracy and "cfg3" in accuracy_ref:
+                result["accuracy_vs_oracle"] = oracle_accuracy("cfg3", accuracy_ref["cfg3"])
             rate, info = oracle_rate(c, args.cpu_seconds)
             rate1, info1 = oracle_rate(c, max(2.0, args.cpu_seconds / 2), batch=256, n_threads=1)
             result["cpu_baseline"] = {

@@ -386,7 +386,7 @@ def order_sweep(torch, F, autotune, c, flush, stream, steps=10):
         s = F.Solver(c["desc"], c["theta"], precision="mixed", order=order)
         s.rho.copy_(torch.from_numpy(c["rho"]).cuda())
         s.step()
-        autotune.tune(s)
+        autotune.tune(s, flush=flush)
         ms = _graph_ms(torch, s, steps, flush, stream)
         inter = int(sum(s.tree.stats["interactions"]))
         fl = s.tree.stats["flops_per_interaction"]
@@ -432,7 +432,7 @@ def time_derivative_timing(torch, F, autotune, c, flush, reps=3):
         s = F.Solver(c["desc"], c["theta"], precision=prec)
         s.rho.copy_(torch.from_numpy(c["rho"]).cuda())
         s.step()
-        autotune.tune(s)
+        autotune.tune(s, flush=flush)
         pd, gd, work = torch.empty_like(s.phi), torch.empty_like(s.g), torch.empty_like(s.rho)
         s.time_derivative(rd, 1e-3, pd, gd, rho_work=work)
         ms = []
@@ -503,7 +503,7 @@ def other_workload(torch, F, autotune, name, args, flush, stream, keep):
         st, sz = sw.tree.stats, sw.tree.sizes
         sw.rho.copy_(rho)
         sw.step()
-        tuning = autotune.tune(sw)[0]
+        tuning = autotune.tune(sw, flush=flush)[0]
         sw.capture()
         steps = max(1, args.fp64_steps) if prec == "fp64" else args.extra_steps
         ms, _, _ = time_graph(torch, sw, steps, 2, flush, stream, label=f"{name}_{prec}")
@@ -611,7 +611,7 @@ def run_ours(args):
         best = json.loads(args.tuning)
         F.fmm_set_tuning(solver.tree, **best)
     else:
-        best, tune_results = autotune.tune(solver)
+        best, tune_results = autotune.tune(solver, reps=7, flush=flush)
     solver.capture()
     pci = None
     try:
@@ -776,7 +776,7 @@ def run_ours(args):
             s64 = F.Solver(c["desc"], c["theta"], precision="fp64")
             s64.rho.copy_(solver.rho)
             s64.step()
-            autotune.tune(s64)
+            autotune.tune(s64, flush=flush)
             s64.capture()
             ms64, _, _ = time_graph(torch, s64, args.fp64_steps, 1, flush, stream,
                                    label="fp64_steps")
@@ -797,7 +797,7 @@ def run_ours(args):
                 sdf = F.Solver(c["desc"], c["theta"], precision="dfloat")
                 sdf.rho.copy_(solver.rho)
                 sdf.step()
-                best_df = autotune.tune(sdf)[0]
+                best_df = autotune.tune(sdf, flush=flush)[0]
                 sdf.capture()
                 msdf, _, _ = time_graph(torch, sdf, args.dfloat_steps, 1, flush, stream,
                                         label="dfloat_steps")
@@ -821,7 +821,7 @@ def run_ours(args):
             s35 = F.Solver(c["desc"], 0.35, precision="mixed")
             s35.rho.copy_(solver.rho)
             s35.step()
-            autotune.tune(s35)
+            autotune.tune(s35, flush=flush)
             s35.capture()
             ms35, _, _ = time_graph(torch, s35, args.theta035_steps, 1, flush, stream,
                                     label="theta035_steps")
@@ -949,7 +949,7 @@ def run_theta_sweep(args):
         inter = int(sum(st["interactions"]))
         s.rho.copy_(rho)
         s.step()
-        autotune.tune(s)
+        autotune.tune(s, flush=flush)
         s.capture()
         _, per, _ = time_graph(torch, s, args.steps, 2, flush, stream, label="theta_sweep")
         ms = float(np.median(per))

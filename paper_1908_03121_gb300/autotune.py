@@ -26,11 +26,14 @@ _CACHE = {}
 
 def _key(solver):
     s = solver.tree.sizes
-    return (s["n_nodes"], s["n_leaf"], s["n_refined"], s["precision"])
+    return (s["n_nodes"], s["n_leaf"], s["n_refined"], s["precision"],
+            int(solver.tree.stats["stencil_union"]), getattr(solver, "order", 3))
 
 
-def tune(solver, reps=5, verbose=False):
-    """Pick and set the fastest tuning for ``solver`` (an ``fmm.Solver``)."""
+def tune(solver, reps=5, verbose=False, flush=None):
+    """Pick and set the fastest tuning for ``solver`` (an ``fmm.Solver``).
+    ``flush``, if given, is called before every timed step (the benchmark's
+    L2 flush, so that candidates are compared as the benchmark times them)."""
     import torch
     key = _key(solver)
     if key in _CACHE:
@@ -48,6 +51,8 @@ def tune(solver, reps=5, verbose=False):
         solver.step()
         times = []
         for _ in range(reps):
+            if flush is not None:
+                flush()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)

@@ -568,7 +568,9 @@ __device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const 
     DTraceless<T> D;
     D.template eval<ORDER == 3>(Rx, Ry, Rz);
     const T nm0 = -s.m0;
-    T a = nm0 * D.D0;
+    // float: each term straight into the chunk sum (one fused multiply-add
+    // per term); double-float and double: each source's terms summed first
+    T a = kF32<T> ? fmadd(nm0, D.D0, L.part[0]) : nm0 * D.D0;
     if (SRC_MP) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) a = fmadd_u(-s.B2[k], D.D2[k], a);
@@ -577,15 +579,15 @@ __device__ __forceinline__ void acc_mp(T Rx, T Ry, T Rz, const Src<T> &s, const 
             for (int q = 0; q < 7; ++q) a = fmadd_u(s.B3[q], D.D3[q], a);
         }
     }
-    L.part[0] = add_u(L.part[0], renorm(a));
+    L.part[0] = kF32<T> ? a : add_u(L.part[0], renorm(a));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        T b = nm0 * D.D1[i];
+        T b = kF32<T> ? fmadd(nm0, D.D1[i], L.part[1 + i]) : nm0 * D.D1[i];
         if (SRC_MP && ORDER == 3) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) b = fmadd_u(-s.B2[k], D.d3slice(i, k), b);
         }
-        L.part[1 + i] = add_u(L.part[1 + i], renorm(b));
+        L.part[1 + i] = kF32<T> ? b : add_u(L.part[1 + i], renorm(b));
     }
     if constexpr (ORDER == 2) {
 #pragma unroll

@@ -374,6 +374,7 @@ class Solver:
         import torch
         self.tree = fmm_build_tree(desc, theta, G, box_lo, box_size, precision, timing=timing,
                                    order=order)
+        self.order = order
         s = self.tree.sizes
         n, nl, nt = s["n_nodes"], s["n_leaf"], s["n_trees"]
         self.precision = s["precision"]

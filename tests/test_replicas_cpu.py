@@ -115,3 +115,15 @@ def test_per_cell_force_errors():
     assert out["cells"] == 500
     assert out["median"] == rel[249].item()
     assert out["p99"] == rel[int(0.99 * 499)].item()
+
+
+def test_direct_field_of_two_masses():
+    """The bench's O(N^2) reference field (order sweep): two point masses
+    attract each other with G m / r^2, self term excluded, in blocks."""
+    import numpy as np
+    pos = np.array([[0.0, 0.0, 0.0], [3.0, 0.0, 4.0]] + [[10.0 + i, 0.0, 0.0] for i in range(300)])
+    m = np.zeros(len(pos))
+    m[0], m[1] = 2.0, 5.0
+    g = bench._direct_field(pos, m, G=1.5)
+    np.testing.assert_allclose(g[0], 1.5 * 5.0 / 125.0 * np.array([3.0, 0.0, 4.0]), rtol=1e-14)
+    np.testing.assert_allclose(g[1], -1.5 * 2.0 / 125.0 * np.array([3.0, 0.0, 4.0]), rtol=1e-14)

@@ -297,10 +297,12 @@ __device__ __forceinline__ void stage_window_async(T *W, const int *s_nbr, const
     }
 }
 
-// neighbour tables of the current target node into shared memory
-__device__ __forceinline__ void load_slots(int node, const KParams &P, int *s_nbr, int *s_leaf,
-                                           int *s_row)
+// neighbour tables of the current target node into shared memory; returns,
+// in threads 0-26, whether that thread's neighbour is a leaf (0 elsewhere)
+__device__ __forceinline__ int load_slots(int node, const KParams &P, int *s_nbr, int *s_leaf,
+                                          int *s_row)
 {
+    int is_leaf = 0;
     if (threadIdx.x < 27) {
         const int nb = P.nbr[node * 27 + threadIdx.x];
         s_nbr[threadIdx.x] = nb;
@@ -312,6 +314,20 @@ __device__ __forceinline__ void load_slots(int node, const KParams &P, int *s_nb
         }
         s_leaf[threadIdx.x] = leaf;
         s_row[threadIdx.x] = row;
+        is_leaf = leaf;
+    }
+    return is_leaf;
+}
+
+// a window value that is a nonzero mass or a moment offset (an absent
+// source's cell holds 0 and contributes nothing)
+template <typename T>
+__device__ __forceinline__ bool window_nonzero(T v)
+{
+    if constexpr (kDF<T>) {
+        return v.hi != 0.f;
+    } else {
+        return v != T(0);
     }
 }
 
@@ -788,8 +804,8 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
         if (item >= P.n_items) break;
         const int node = P.list[item];
         const NodeInfo ti = P.info[node];
-        load_slots(node, P, s_nbr, s_leaf, s_row);
-        __syncthreads();
+        // near sources contribute only if some neighbour is a leaf
+        const int any_leaf = __syncthreads_or(load_slots(node, P, s_nbr, s_leaf, s_row));
         stage_window_async<T>(W, s_nbr, s_leaf, mass, P, s_row);
         cp_async_commit();
         cp_async_wait_all();
@@ -808,35 +824,64 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
             }
             L.zero();
             S.zero();
-            // well-separated sources: refined (full moments) or leaf (mass)
+            // well-separated sources: refined (full moments) or leaf (mass).
+            // In float, a vote classifies the warp's 32 sources of one
+            // entry: all refined take the moments without a branch, all
+            // leaves the mass-only form (the same operations less the zero
+            // moments' terms, so the same values), a mix the general form
+            // with zero moments for the leaves; an entry with only absent
+            // sources (mass 0) is skipped.
             for (int e0 = 0; e0 < P.n_far; e0 += kChunk) {
                 const int e1 = min(e0 + kChunk, P.n_far);
                 for (int e = e0; e < e1; ++e) {
                     const float4 E = __ldg(ent + e);
                     const T wv = W[base + __float_as_int(E.w)];
                     const int idx = window_decode<T>(wv);
+                    const bool is_mp = idx >= 0 && idx < P.mp_limit;
+                    // (the double-float and double bodies are several times
+                    // larger, and extra copies of them cost more in
+                    // instruction fetch than they save: general form only)
+                    const unsigned mp_lanes = kF32<T> ? __ballot_sync(0xffffffffu, is_mp) : 1u;
                     Src<T> src;
-                    if (idx >= 0 && idx < P.mp_limit) {
+                    if (mp_lanes == 0xffffffffu) {
                         load_source_at<T>(mp + idx, src);
+                        acc_mp<T, true, ORDER>(dA[0] - src.d[0] - T(E.x),
+                                               dA[1] - src.d[1] - T(E.y),
+                                               dA[2] - src.d[2] - T(E.z), src, a3A, L, S);
+                    } else if (mp_lanes == 0u) {
+                        if (__any_sync(0xffffffffu, window_nonzero<T>(wv))) {
+                            src.m0 = wv;
+                            acc_mp<T, false, ORDER>(dA[0] - T(E.x), dA[1] - T(E.y),
+                                                    dA[2] - T(E.z), src, a3A, L, S);
+                        }
                     } else {
-                        src.m0 = wv;
-                        zero_moments<T>(src);
+                        if (is_mp) {
+                            load_source_at<T>(mp + idx, src);
+                        } else {
+                            src.m0 = wv;
+                            zero_moments<T>(src);
+                        }
+                        acc_mp<T, true, ORDER>(dA[0] - src.d[0] - T(E.x),
+                                               dA[1] - src.d[1] - T(E.y),
+                                               dA[2] - src.d[2] - T(E.z), src, a3A, L, S);
                     }
-                    acc_mp<T, true, ORDER>(dA[0] - src.d[0] - T(E.x), dA[1] - src.d[1] - T(E.y),
-                                    dA[2] - src.d[2] - T(E.z), src, a3A, L, S);
                 }
                 L.flush();
                 S.flush();
             }
             // near sources: leaf cells only (refined ones contribute nothing
-            // here: their children interact one level down)
-            for (int e0 = P.n_far; e0 < P.n_far + P.n_near; e0 += kChunk) {
+            // here: their children interact one level down); skipped when no
+            // neighbour is a leaf, and entry by entry when none of the
+            // warp's 32 sources is a leaf with mass (skipping exact zeros
+            // changes no sum)
+            for (int e0 = P.n_far; any_leaf && e0 < P.n_far + P.n_near; e0 += kChunk) {
                 const int e1 = min(e0 + kChunk, P.n_far + P.n_near);
                 for (int e = e0; e < e1; ++e) {
                     const float4 E = __ldg(ent + e);
                     const T wv = W[base + __float_as_int(E.w)];
                     Src<T> src;
                     src.m0 = window_decode<T>(wv) >= 0 ? T(0) : wv;
+                    if (!__any_sync(0xffffffffu, window_nonzero<T>(src.m0))) continue;
                     acc_mp<T, false, ORDER>(dA[0] - T(E.x), dA[1] - T(E.y), dA[2] - T(E.z), src, a3A,
                                      L, S);
                 }
@@ -908,8 +953,7 @@ __global__ void __launch_bounds__(kThreads, 2) mp2_kernel(KParams P)
         if (item >= P.n_items) break;
         const int node = P.list[item];
         const NodeInfo ti = P.info[node];
-        load_slots(node, P, s_nbr, s_leaf, s_row);
-        __syncthreads();
+        const int any_leaf = __syncthreads_or(load_slots(node, P, s_nbr, s_leaf, s_row));
         stage_window_async<float>(W, s_nbr, s_leaf, mass, P, s_row);
         cp_async_commit();
         cp_async_wait_all();
@@ -935,9 +979,19 @@ __global__ void __launch_bounds__(kThreads, 2) mp2_kernel(KParams P)
             for (int e = e0; e < e1; ++e) {
                 const float4 E = __ldg(ent + e);
                 const int woff = __float_as_int(E.w);
+                const float w0 = W[base0 + woff], w1 = W[base1 + woff];
+                const unsigned i0 = unsigned(-1 - __float_as_int(w0));
+                const unsigned i1 = unsigned(-1 - __float_as_int(w1));
                 Src<float> s0, s1;
-                mp2_source(P, mp, W[base0 + woff], s0);
-                mp2_source(P, mp, W[base1 + woff], s1);
+                // the warp's 64 sources all refined: the moments without a
+                // branch (the same values as the general form)
+                if (__all_sync(0xffffffffu, i0 < unsigned(P.mp_limit) && i1 < unsigned(P.mp_limit))) {
+                    load_source_at<float>(mp + i0, s0);
+                    load_source_at<float>(mp + i1, s1);
+                } else {
+                    mp2_source(P, mp, w0, s0);
+                    mp2_source(P, mp, w1, s1);
+                }
                 acc_mp<float, true>(dA0[0] - s0.d[0] - E.x, dA0[1] - s0.d[1] - E.y,
                                     dA0[2] - s0.d[2] - E.z, s0, a3A0, L0, S0);
                 acc_mp<float, true>(dA1[0] - s1.d[0] - E.x, dA1[1] - s1.d[1] - E.y,
@@ -948,7 +1002,7 @@ __global__ void __launch_bounds__(kThreads, 2) mp2_kernel(KParams P)
             L1.flush();
             S1.flush();
         }
-        for (int e0 = P.n_far; e0 < P.n_far + P.n_near; e0 += kChunk) {
+        for (int e0 = P.n_far; any_leaf && e0 < P.n_far + P.n_near; e0 += kChunk) {
             const int e1 = min(e0 + kChunk, P.n_far + P.n_near);
             for (int e = e0; e < e1; ++e) {
                 const float4 E = __ldg(ent + e);
@@ -957,6 +1011,7 @@ __global__ void __launch_bounds__(kThreads, 2) mp2_kernel(KParams P)
                 Src<float> s0, s1;
                 s0.m0 = unsigned(-1 - __float_as_int(w0)) < unsigned(P.mp_limit) ? 0.f : w0;
                 s1.m0 = unsigned(-1 - __float_as_int(w1)) < unsigned(P.mp_limit) ? 0.f : w1;
+                if (!__any_sync(0xffffffffu, s0.m0 != 0.f || s1.m0 != 0.f)) continue;
                 acc_mp<float, false>(dA0[0] - E.x, dA0[1] - E.y, dA0[2] - E.z, s0, a3A0, L0, S0);
                 acc_mp<float, false>(dA1[0] - E.x, dA1[1] - E.y, dA1[2] - E.z, s1, a3A1, L1, S1);
             }

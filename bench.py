@@ -55,6 +55,7 @@ WORKLOAD_TEXT = {
     "cfg3": "adaptive octree to level 5 around a polytrope binary (q=0.3)",
     "cfg4": "16 independent adaptive octrees (levels 4-7, q=0.1..1.0) batched in one solve",
     "cfg5": "contact binary of two n=1.5 polytropes (q=0.3), adaptive octree to level 7",
+    "cfg5_small": "cfg5's binary refined to level 6 (profiler captures)",
 }
 
 
@@ -900,7 +901,10 @@ def run_profile_pass(args):
 
     c = make_config(args.workload)
     s = F.Solver(c["desc"], c["theta"], precision=args.precision)
-    F.fmm_set_tuning(s.tree, mono_subgrids=args.mono_subgrids)
+    if args.tuning:
+        F.fmm_set_tuning(s.tree, **json.loads(args.tuning))
+    else:
+        F.fmm_set_tuning(s.tree, mono_subgrids=args.mono_subgrids)
     s.rho.copy_(torch.from_numpy(c["rho"]).cuda())
     s.upward()
     if args.profile_pass in ("downward", "forces"):

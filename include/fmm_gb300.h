@@ -304,7 +304,13 @@ typedef struct {
     int32_t mp_pair_targets;         /* FMM_MIXED: 1 walks each thread's two multipole
                                         target cells through the stencil together
                                         (same results, more work in flight) */
-    int32_t reserved[2];
+    int32_t mp_items;                /* work item of the multipole kernel: 1 a whole
+                                        sub-grid, 2 half a sub-grid (256 cells; more
+                                        items to balance a tree with few refined
+                                        nodes, the halo staged twice); 0 = 2 when the
+                                        tree has fewer refined nodes than twice the
+                                        kernel's resident CTAs, else 1.  Same results. */
+    int32_t reserved;
 } fmm_tuning;
 
 /* Set / read the tree's tuning (host, immediate; affects later launches).

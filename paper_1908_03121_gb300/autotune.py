@@ -5,7 +5,8 @@ so co-resident kernels share SMs as they will in the real step) on the
 caller's tree for every candidate of
 ``fmm_tuning`` (sub-grids per pass of the monopole kernel, persistent CTAs per
 SM, the dataflow downward pass or the level-by-level one, one or two multipole
-target cells per thread in flight) with CUDA events on the current stream, keeps the fastest and leaves it
+target cells per thread in flight, whole or half sub-grids per multipole work
+item) with CUDA events on the current stream, keeps the fastest and leaves it
 set on the tree.  Each candidate is run ``reps`` times after one warm-up; the
 median decides.  Results are cached per tree size and precision for the
 process.
@@ -21,6 +22,7 @@ MONO_SUBGRIDS = (1, 2, 4)
 CTAS_PER_SM = (0, 1, 2)
 DATAFLOW = (0, 1)
 PAIR_TARGETS = (0, 1)
+MP_ITEMS = (1, 2)
 _CACHE = {}
 
 
@@ -40,10 +42,13 @@ def tune(solver, reps=5, verbose=False, flush=None):
         B.fmm_set_tuning(solver.tree, **_CACHE[key][0])
         return _CACHE[key]
     mixed = solver.mixed
-    candidates = [dict(mono_subgrids=nb, ctas_per_sm=cap, dataflow=df, mp_pair_targets=pt)
-                  for nb, cap, df, pt in itertools.product(MONO_SUBGRIDS, CTAS_PER_SM, DATAFLOW,
-                                                           PAIR_TARGETS)
-                  if mixed or (nb != 4 and pt == 0)]
+    # the FP64 kernels' steps are long: their multipole items stay automatic
+    items = MP_ITEMS if solver.tree.sizes["precision"] != B.FMM_FP64 else (0,)
+    candidates = [dict(mono_subgrids=nb, ctas_per_sm=cap, dataflow=df, mp_pair_targets=pt,
+                       mp_items=it)
+                  for nb, cap, df, pt, it in itertools.product(MONO_SUBGRIDS, CTAS_PER_SM,
+                                                               DATAFLOW, PAIR_TARGETS, items)
+                  if (mixed or (nb != 4 and pt == 0)) and not (pt and it == 2)]
     stream = torch.cuda.current_stream()
     results = []
     for cand in candidates:

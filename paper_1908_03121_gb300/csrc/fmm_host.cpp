@@ -1038,6 +1038,8 @@ int fmm_set_tuning(fmm_tree_t t, const fmm_tuning *tu)
         tu->mp_pair_targets > 1)
         return fail(FMM_ERR_INVALID_ARG, "dataflow, drop_first_producer and mp_pair_targets "
                                          "must be 0 or 1, wait_budget_us not negative");
+    if (tu->mp_items < 0 || tu->mp_items > 2)
+        return fail(FMM_ERR_INVALID_ARG, "mp_items must be 0, 1 or 2");
     t->tuning = *tu;
     return FMM_OK;
 }

@@ -254,6 +254,42 @@ __device__ __forceinline__ int window_decode(T v)
     }
 }
 
+// whether a window value is a refined source's moment offset below limit,
+// and that offset: -1 - bits is the offset for a refined source and
+// negative (a large unsigned value) for a mass, whose bits are not
+// negative, so one unsigned comparison tells both apart and bounds the
+// offset
+template <typename T>
+__device__ __forceinline__ bool window_moments(T v, int limit, int &idx)
+{
+    if constexpr (kF32<T>) {
+        const unsigned u = unsigned(-1 - __float_as_int(v));
+        idx = int(u);
+        return u < unsigned(limit);
+    } else if constexpr (kDF<T>) {
+        const unsigned u = unsigned(-1 - __float_as_int(v.hi));
+        idx = int(u);
+        return u < unsigned(limit);
+    } else {
+        const unsigned long long u = static_cast<unsigned long long>(-1ll - __double_as_longlong(v));
+        idx = int(u);
+        return u < static_cast<unsigned long long>(limit);
+    }
+}
+
+// whether a window value encodes a refined source (sign bit set)
+template <typename T>
+__device__ __forceinline__ bool window_refined(T v)
+{
+    if constexpr (kF32<T>) {
+        return __float_as_int(v) < 0;
+    } else if constexpr (kDF<T>) {
+        return __float_as_int(v.hi) < 0;
+    } else {
+        return __double_as_longlong(v) < 0;
+    }
+}
+
 // Window geometry of reach R: the host's pitches (same pad_to), as
 // compile-time constants; RR = 0 takes them from the kernel parameters.
 template <int RR>
@@ -783,7 +819,9 @@ __device__ __forceinline__ void mx_target(const KParams &P, int t)
 }
 
 // ------------------------------------------------------------ mp_kernel
-template <typename T, int ORDER>
+// HALVES: item k is half k & 1 (cells of z < 4 or z >= 4) of node list[k >> 1],
+// else item k is all of node list[k]
+template <typename T, int ORDER, bool HALVES>
 // float: three CTAs per SM (at most 85 registers): the compensation pairs,
 // touched once per chunk, live in shared memory after the window
 __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P)
@@ -802,7 +840,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
     for (;;) {
         const int item = pull_item(P.counter, &s_item);
         if (item >= P.n_items) break;
-        const int node = P.list[item];
+        const int node = P.list[HALVES ? item >> 1 : item];
         const NodeInfo ti = P.info[node];
         // near sources contribute only if some neighbour is a leaf
         const int any_leaf = __syncthreads_or(load_slots(node, P, s_nbr, s_leaf, s_row));
@@ -810,7 +848,9 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
-        for (int half = 0; half < 2; ++half) {
+        const int half0 = HALVES ? item & 1 : 0;
+        const int half1 = HALVES ? half0 + 1 : 2;
+        for (int half = half0; half < half1; ++half) {
             const int cz = cz0 + 2 * half;
             const int ax = 2 * cx + px, ay = 2 * cy + py, az = 2 * cz + pz;
             const int base = cx + P.py * cy + P.pz * cz;
@@ -836,8 +876,8 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
                 for (int e = e0; e < e1; ++e) {
                     const float4 E = __ldg(ent + e);
                     const T wv = W[base + __float_as_int(E.w)];
-                    const int idx = window_decode<T>(wv);
-                    const bool is_mp = idx >= 0 && idx < P.mp_limit;
+                    int idx;
+                    const bool is_mp = window_moments<T>(wv, P.mp_limit, idx);
                     // (the double-float and double bodies are several times
                     // larger, and extra copies of them cost more in
                     // instruction fetch than they save: general form only)
@@ -880,7 +920,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
                     const float4 E = __ldg(ent + e);
                     const T wv = W[base + __float_as_int(E.w)];
                     Src<T> src;
-                    src.m0 = window_decode<T>(wv) >= 0 ? T(0) : wv;
+                    src.m0 = window_refined<T>(wv) ? T(0) : wv;
                     if (!__any_sync(0xffffffffu, window_nonzero<T>(src.m0))) continue;
                     acc_mp<T, false, ORDER>(dA[0] - T(E.x), dA[1] - T(E.y), dA[2] - T(E.z), src, a3A,
                                      L, S);
@@ -1315,11 +1355,11 @@ cudaError_t allow_smem(Kern k, size_t bytes, size_t &done)
 
 template <typename T>
 struct Kernels {
-    template <int ORDER>
+    template <int ORDER, bool HALVES>
     static cudaError_t mp(size_t bytes)
     {
         static size_t done = 0;
-        return allow_smem(mp_kernel<T, ORDER>, bytes, done);
+        return allow_smem(mp_kernel<T, ORDER, HALVES>, bytes, done);
     }
     static cudaError_t mp2(size_t bytes)
     {
@@ -1411,7 +1451,8 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
     // mp_kernel: one window (masses of leaf sources, moment offsets of
     // refined ones); float adds its compensation pairs, [7][2][threads]
     const size_t mp_bytes = wbytes + (kF32<T> ? size_t(kMpPairs) * 2 * kThreads * sizeof(float) : 0);
-    cudaError_t e = Kernels<T>::template mp<ORDER>(mp_bytes);
+    cudaError_t e = Kernels<T>::template mp<ORDER, false>(mp_bytes);
+    if (e == cudaSuccess) e = Kernels<T>::template mp<ORDER, true>(mp_bytes);
     if (e != cudaSuccess) return e;
     if (parts & M2L_RESET) {
         e = cudaMemsetAsync(d.counters, 0, 4 * sizeof(int32_t), s);
@@ -1449,8 +1490,19 @@ cudaError_t launch_all(const fmm_tree_s *t, void *L, float *Lc, double *dL1, cud
             int g = persistent_grid(mp2_kernel, b2, Pl.work_mp.count, sms, cap);
             mp2_kernel<<<g, kThreads, b2, s>>>(K);
         } else {
-            int g = persistent_grid(mp_kernel<T, ORDER>, mp_bytes, Pl.work_mp.count, sms, cap);
-            mp_kernel<T, ORDER><<<g, kThreads, mp_bytes, s>>>(K);
+            // half sub-grids per item where whole ones would leave CTA slots
+            // idle or unbalanced (fewer nodes than twice the slots)
+            const int64_t slots =
+                persistent_grid(mp_kernel<T, ORDER, false>, mp_bytes, INT32_MAX, sms, cap);
+            const int mode = t->tuning.mp_items;
+            if (mode == 2 || (mode == 0 && Pl.work_mp.count < 2 * slots)) {
+                K.n_items = int32_t(2 * Pl.work_mp.count);
+                int g = persistent_grid(mp_kernel<T, ORDER, true>, mp_bytes, K.n_items, sms, cap);
+                mp_kernel<T, ORDER, true><<<g, kThreads, mp_bytes, s>>>(K);
+            } else {
+                int g = persistent_grid(mp_kernel<T, ORDER, false>, mp_bytes, K.n_items, sms, cap);
+                mp_kernel<T, ORDER, false><<<g, kThreads, mp_bytes, s>>>(K);
+            }
         }
         timing_end(t, s);
         ++nl;

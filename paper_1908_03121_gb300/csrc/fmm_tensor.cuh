@@ -70,7 +70,18 @@ __device__ __forceinline__ float renorm(float a) { return a; }
 __device__ __forceinline__ double renorm(double a) { return a; }
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T v);
-template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
+// float: the hardware's approximate reciprocal square root with subnormal
+// inputs flushed to zero (the PTX instruction itself), which spares the
+// subnormal-input handling around it; the kernels give it squared
+// distances of about a cell width or more, always normal numbers, for
+// which flushing changes nothing
+__device__ __forceinline__ float rsqrt_ftz(float v)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+template <> __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrt_ftz(v); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
 template <> __device__ __forceinline__ dfloat rsqrt_t<dfloat>(dfloat v) { return df_rsqrt(v); }
 
@@ -230,7 +241,7 @@ struct DTraceless<float> {
     __device__ __forceinline__ void eval(float x, float y, float z)
     {
         const float r2 = fmaf(x, x, fmaf(y, y, z * z));
-        const float ri = rsqrtf(r2);
+        const float ri = rsqrt_ftz(r2);
         const float ri2 = ri * ri;
         const float d1 = -ri * ri2;
         const float d2 = d1 * (-3.f * ri2);

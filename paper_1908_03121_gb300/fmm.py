@@ -78,11 +78,11 @@ class FmmTuning(ctypes.Structure):
     _fields_ = [("mono_subgrids", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("dataflow", ctypes.c_int32), ("wait_budget_us", ctypes.c_int32),
                 ("drop_first_producer", ctypes.c_int32), ("mp_pair_targets", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("mp_items", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 TUNING_KEYS = ("mono_subgrids", "ctas_per_sm", "dataflow", "wait_budget_us",
-               "drop_first_producer", "mp_pair_targets")
+               "drop_first_producer", "mp_pair_targets", "mp_items")
 
 
 class FmmScfParams(ctypes.Structure):
@@ -337,9 +337,9 @@ def fmm_scf_update(tree, params, phi, rho, rho_out, stream=None):
 
 
 def fmm_set_tuning(tree, mono_subgrids=0, ctas_per_sm=0, dataflow=0, wait_budget_us=0,
-                   drop_first_producer=0, mp_pair_targets=0):
+                   drop_first_producer=0, mp_pair_targets=0, mp_items=0):
     t = FmmTuning(int(mono_subgrids), int(ctas_per_sm), int(dataflow), int(wait_budget_us),
-                  int(drop_first_producer), int(mp_pair_targets))
+                  int(drop_first_producer), int(mp_pair_targets), int(mp_items))
     _check(load().fmm_set_tuning(tree.handle, ctypes.byref(t)))
 
 

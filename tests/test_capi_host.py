@@ -214,15 +214,16 @@ def test_tuning_set_get_and_validation():
     leaves the previous tuning in place (host-only tree: no CUDA)."""
     t = plan(uniform_tree(2), 0.5)
     zero = dict(mono_subgrids=0, ctas_per_sm=0, dataflow=0, wait_budget_us=0,
-                drop_first_producer=0, mp_pair_targets=0)
+                drop_first_producer=0, mp_pair_targets=0, mp_items=0)
     assert F.fmm_get_tuning(t) == zero
     good = dict(zero, mono_subgrids=2, ctas_per_sm=1, dataflow=1, wait_budget_us=500,
-                mp_pair_targets=1)
+                mp_pair_targets=1, mp_items=2)
     F.fmm_set_tuning(t, **{k: v for k, v in good.items()})
     assert F.fmm_get_tuning(t) == good
     bad = [dict(mono_subgrids=3), dict(mono_subgrids=5), dict(mono_subgrids=-1),
            dict(ctas_per_sm=33), dict(ctas_per_sm=-1), dict(dataflow=2), dict(dataflow=-1),
-           dict(wait_budget_us=-5), dict(drop_first_producer=2), dict(mp_pair_targets=2)]
+           dict(wait_budget_us=-5), dict(drop_first_producer=2), dict(mp_pair_targets=2),
+           dict(mp_items=3), dict(mp_items=-1)]
     for b in bad:
         with pytest.raises(F.FmmError) as ei:
             F.fmm_set_tuning(t, **b)

@@ -476,12 +476,16 @@ def test_tunings_agree_bitwise(precision):
     c, _ = oracle_solution("adaptive4")
     s = solve_gpu(c, precision)
     ref = None
-    for nb, cap, pair in itertools.product((1, 2, 4), (0, 1), (0, 1)):
+    for nb, cap, pair, items in itertools.product((1, 2, 4), (0, 1), (0, 1), (1, 2)):
         if precision != "mixed" and (nb == 4 or pair):
             continue
-        F.fmm_set_tuning(s.tree, mono_subgrids=nb, ctas_per_sm=cap, mp_pair_targets=pair)
+        if pair and items == 2:     # the paired kernel always takes whole sub-grids
+            continue
+        F.fmm_set_tuning(s.tree, mono_subgrids=nb, ctas_per_sm=cap, mp_pair_targets=pair,
+                         mp_items=items)
         got = F.fmm_get_tuning(s.tree)
-        assert (got["mono_subgrids"], got["ctas_per_sm"], got["mp_pair_targets"]) == (nb, cap, pair)
+        assert ((got["mono_subgrids"], got["ctas_per_sm"], got["mp_pair_targets"], got["mp_items"])
+                == (nb, cap, pair, items))
         s.L.zero_()
         s.m2l()
         torch.cuda.synchronize()

@@ -111,6 +111,16 @@ def make_config(name, theta=None):
         rho = np.concatenate(rhos, axis=0)
         th = 0.5
         info = dict(trees=infos)
+    elif name == "cfg5_small":
+        # cfg5's binary refined to level 6 (5129 sub-grids, 641 refined):
+        # a small case of the same kernels, for profiler captures
+        q = 0.3
+        r2 = R1 * q ** (-1.0 / 3.0)
+        p = _binary_params(q, R1 + r2 - 0.1 * R1, seed=5)
+        desc = _binary_tree(p, 1.2, 6)
+        rho = _binary_rho(desc, p)
+        th = 0.5
+        info = p
     elif name == "cfg5":
         q = 0.3
         r2 = R1 * q ** (-1.0 / 3.0)

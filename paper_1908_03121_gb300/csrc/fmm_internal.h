@@ -9,8 +9,8 @@
 //   - packed same-level source data (workspace), in level units:
 //       mass[node][512]            cell mass (all nodes)
 //       mp[mp_row][4][512][4]      refined nodes only, four groups of four:
-//                                  (M0, centre-of-mass offset from the cell
-//                                  centre in cell widths), then the traceless
+//                                  (centre-of-mass offset from the cell
+//                                  centre in cell widths, M0), then the traceless
 //                                  projections B2 (5) and B3 (7) of
 //                                  A2 = mult * M2 / (2 h^2), A3 = mult * M3 / (6 h^3)
 //     where mult is the number of index permutations of a symmetric

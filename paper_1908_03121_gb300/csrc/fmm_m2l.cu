@@ -129,7 +129,7 @@ __device__ __forceinline__ void pack_float(const NodeInfo &ni, const double *__r
     for (int q = 0; q < 6; ++q) A2[q] = d2f_rn(Mn[(4 + q) * NCELL]) * (float(mult2(q)) * w2);
 #pragma unroll
     for (int q = 0; q < 10; ++q) A3[q] = d2f_rn(Mn[(10 + q) * NCELL]) * (float(mult3(q)) * w3);
-    const float v[16] = {mass_node[pi], d[0],          d[1],          d[2],
+    const float v[16] = {d[0],          d[1],          d[2],          mass_node[pi],
                          A2[0] - A2[5], A2[3] - A2[5], A2[1],         A2[2],
                          A2[4],         A3[0] - A3[5], A3[1] - A3[8], A3[2] - A3[9],
                          A3[3] - A3[5], A3[4],         A3[6] - A3[8], A3[7] - A3[9]};
@@ -141,7 +141,8 @@ __device__ __forceinline__ void pack_float(const NodeInfo &ni, const double *__r
 
 // mass[node][pi] = M0 for every node.  Refined nodes also get, in level
 // units, four groups of four values at mp[row][g][pi][0..3]:
-//   g0 = (M0, delta), delta = (X - centre) / h,
+//   g0 = (delta, M0), delta = (X - centre) / h (first, so that its x and y
+//        land in an aligned register pair for the paired FP32 subtraction),
 //   g1 = B2[0..3], g2 = (B2[4], B3[0..2]), g3 = B3[3..6],
 // the traceless projections of A2 = mult M2 / (2 h^2), A3 = mult M3 / (6 h^3).
 template <typename T>
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(512) pack_kernel(const NodeInfo *__restrict__ 
 #pragma unroll
     for (int q = 0; q < 10; ++q) A3[q] = mult3(q) * w3 * Mn[(10 + q) * NCELL];
     // symmetric order: A2 xx xy xz yy yz zz; A3 xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
-    const double v[16] = {Mn[0],         d[0],          d[1],          d[2],
+    const double v[16] = {d[0],          d[1],          d[2],          Mn[0],
                           A2[0] - A2[5], A2[3] - A2[5], A2[1],         A2[2],
                           A2[4],         A3[0] - A3[5], A3[1] - A3[8], A3[2] - A3[9],
                           A3[3] - A3[5], A3[4],         A3[6] - A3[8], A3[7] - A3[9]};
@@ -573,8 +574,8 @@ __device__ __forceinline__ void load_source_at(const T *base, Src<T> &s)
     T v[16];
 #pragma unroll
     for (int g = 0; g < 4; ++g) load4<T>(base + size_t(g) * NCELL * 4, v + 4 * g);
-    s.m0 = v[0];
-    s.d[0] = v[1]; s.d[1] = v[2]; s.d[2] = v[3];
+    s.d[0] = v[0]; s.d[1] = v[1]; s.d[2] = v[2];
+    s.m0 = v[3];
 #pragma unroll
     for (int k = 0; k < 5; ++k) s.B2[k] = v[4 + k];
 #pragma unroll
@@ -732,6 +733,25 @@ __device__ __forceinline__ void acc_mx(T Rx, T Ry, T Rz, const Src<T> &s, Acc<T,
     }
 }
 
+// target-to-source separation in cell widths, R = (dA - d) - E, in that
+// order; float takes x and y as one pair (the offsets' x and y sit in
+// aligned register pairs: first in their 16-byte groups)
+template <typename T>
+__device__ __forceinline__ void separation(const T dA[3], const T d[3], const float4 &E, T R[3])
+{
+    if constexpr (kF32<T>) {
+        const float2 u = fsub2_rn(make_float2(dA[0], dA[1]), make_float2(d[0], d[1]));
+        const float2 r = fsub2_rn(u, make_float2(E.x, E.y));
+        R[0] = r.x;
+        R[1] = r.y;
+        R[2] = dA[2] - d[2] - E.z;
+    } else {
+        R[0] = dA[0] - d[0] - T(E.x);
+        R[1] = dA[1] - d[1] - T(E.y);
+        R[2] = dA[2] - d[2] - T(E.z);
+    }
+}
+
 // own packed data of a multipole target: centre-of-mass offset and
 // a3 = B3/M0 (order 3) or a2 = B2/M0 in the first five entries (order 2)
 template <typename T, int ORDER = 3>
@@ -881,14 +901,14 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
                     // (the double-float and double bodies are several times
                     // larger, and extra copies of them cost more in
                     // instruction fetch than they save: general form only)
-                    const unsigned mp_lanes = kF32<T> ? __ballot_sync(0xffffffffu, is_mp) : 1u;
+                    const bool all_mp = kF32<T> && __all_sync(0xffffffffu, is_mp);
                     Src<T> src;
-                    if (mp_lanes == 0xffffffffu) {
+                    T R[3];
+                    if (all_mp) {
                         load_source_at<T>(mp + idx, src);
-                        acc_mp<T, true, ORDER>(dA[0] - src.d[0] - T(E.x),
-                                               dA[1] - src.d[1] - T(E.y),
-                                               dA[2] - src.d[2] - T(E.z), src, a3A, L, S);
-                    } else if (mp_lanes == 0u) {
+                        separation<T>(dA, src.d, E, R);
+                        acc_mp<T, true, ORDER>(R[0], R[1], R[2], src, a3A, L, S);
+                    } else if (kF32<T> && !__any_sync(0xffffffffu, is_mp)) {
                         if (__any_sync(0xffffffffu, window_nonzero<T>(wv))) {
                             src.m0 = wv;
                             acc_mp<T, false, ORDER>(dA[0] - T(E.x), dA[1] - T(E.y),
@@ -901,9 +921,8 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
                             src.m0 = wv;
                             zero_moments<T>(src);
                         }
-                        acc_mp<T, true, ORDER>(dA[0] - src.d[0] - T(E.x),
-                                               dA[1] - src.d[1] - T(E.y),
-                                               dA[2] - src.d[2] - T(E.z), src, a3A, L, S);
+                        separation<T>(dA, src.d, E, R);
+                        acc_mp<T, true, ORDER>(R[0], R[1], R[2], src, a3A, L, S);
                     }
                 }
                 L.flush();
@@ -1032,10 +1051,11 @@ __global__ void __launch_bounds__(kThreads, 2) mp2_kernel(KParams P)
                     mp2_source(P, mp, w0, s0);
                     mp2_source(P, mp, w1, s1);
                 }
-                acc_mp<float, true>(dA0[0] - s0.d[0] - E.x, dA0[1] - s0.d[1] - E.y,
-                                    dA0[2] - s0.d[2] - E.z, s0, a3A0, L0, S0);
-                acc_mp<float, true>(dA1[0] - s1.d[0] - E.x, dA1[1] - s1.d[1] - E.y,
-                                    dA1[2] - s1.d[2] - E.z, s1, a3A1, L1, S1);
+                float R0[3], R1[3];
+                separation<float>(dA0, s0.d, E, R0);
+                separation<float>(dA1, s1.d, E, R1);
+                acc_mp<float, true>(R0[0], R0[1], R0[2], s0, a3A0, L0, S0);
+                acc_mp<float, true>(R1[0], R1[1], R1[2], s1, a3A1, L1, S1);
             }
             L0.flush();
             S0.flush();

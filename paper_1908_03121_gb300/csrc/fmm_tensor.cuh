@@ -225,6 +225,19 @@ struct DTraceless {
     }
 };
 
+// paired FP32 subtraction (sub.rn.f32x2: each half rounds as the scalar
+// subtraction does)
+__device__ __forceinline__ float2 fsub2_rn(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 // float: the same values, bit for bit, with the independent products that
 // share a form issued in pairs on the paired FP32 pipe (mul/fma.rn.f32x2,
 // each half rounding as the scalar instruction does).  The natural pairs are
@@ -286,9 +299,10 @@ struct DTraceless<float> {
             const float xxxx = q4.x, yyyy = q4.y, xxxz = z4.x, yyyz = z4.y;
             const float xxxy = fmaf(d4sq.x, xy, t3xy);
             const float xxyy = fmaf(d4sq.x, sq.y, fmaf(d3, sq.x + sq.y, d2));
-            const float xxyz = fmaf(d4sq.x, xzyz.y, d3 * xzyz.y);
+            const float2 d3z = __fmul2_rn(make_float2(d3, d3), xzyz);    // d3 xz, d3 yz
+            const float xxyz = fmaf(d4sq.x, xzyz.y, d3z.y);
             const float xyyy = fmaf(d4xy, sq.y, t3xy);
-            const float xyyz = fmaf(d4xy, xzyz.y, d3 * xzyz.x);
+            const float xyyz = fmaf(d4xy, xzyz.y, d3z.x);
             const float xxzz = -(xxxx + xxyy), xyzz = -(xxxy + xyyy), yyzz = -(xxyy + yyyy);
             U[0][0] = xxxx; U[0][1] = xxxy; U[0][2] = xxxz; U[0][3] = xxyy;
             U[0][4] = xxyz; U[0][5] = xyyy; U[0][6] = xyyz;

@@ -599,7 +599,10 @@ static int upload_tree(fmm_tree_s *t)
     size_t es = t->cfg.precision == FMM_MIXED ? sizeof(float) : 2 * sizeof(float);
     static_assert(2 * sizeof(float) == sizeof(double), "packed element sizes");
     size_t mass_b = size_t(t->n) * NCELL * es;
-    size_t mp_b = size_t(std::max<int64_t>(t->n_refined, 1)) * NMP * NCELL * es;
+    // one row past the refined nodes' rows stays zero: the multipole
+    // kernel reads a leaf source's (absent) moments there
+    const size_t mp_row_b = size_t(NMP) * NCELL * es;
+    size_t mp_b = size_t(t->n_refined + 1) * mp_row_b;
     size_t part_b = size_t(std::max<int64_t>(t->n_leaf, 1)) * 8 * sizeof(double);
     size_t chunk_b = size_t(t->n_trees) * t->plan.reduce_chunks * 8 * sizeof(double);
     cudaError_t e;
@@ -614,7 +617,9 @@ static int upload_tree(fmm_tree_s *t)
     d.workspace_bytes = mass_b + mp_b + part_b + chunk_b + 64 * sizeof(int32_t) +
                         size_t(t->n) * sizeof(int32_t);
     // work queues and the status word start at zero
-    if ((e = cudaMemset(d.counters, 0, 64 * sizeof(int32_t))) != cudaSuccess)
+    if ((e = cudaMemset(d.counters, 0, 64 * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMemset(static_cast<char *>(d.mp) + size_t(t->n_refined) * mp_row_b, 0, mp_row_b)) !=
+            cudaSuccess)
         return cuda_fail(e, "cudaMemset");
     if (t->cfg.precision != FMM_FP64) {
         size_t up_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 20 * NCELL * 2 * sizeof(float);

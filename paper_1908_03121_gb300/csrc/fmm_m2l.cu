@@ -86,7 +86,8 @@ struct KParams {
     int reach, py, pz, sub_stride;
     const void *mass;
     const void *mp;
-    int mp_limit;            // elements of mp: decoded window offsets below it only
+    int mp_limit;            // elements of mp: decoded window offsets below it only; the
+                             // row starting there holds zeros
     void *L;
     float *Lc;
     double *dL1;
@@ -793,7 +794,7 @@ __device__ __forceinline__ void mx_target(const KParams &P, int t)
     const int4 tg = __ldg(P.mx_targets + t);       // node, cell, pair offset, count
     const int x = tg.y & 7, y = (tg.y >> 3) & 7, z = tg.y >> 6;
     const int p = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
-    const StencilEntry *ent = P.stencil + p * P.ent_stride;
+    const float4 *ent = P.stencil_f + p * P.ent_stride;   // float offsets: no conversions
     Acc<T, 4> L;
     Acc<T, 3> S;
     L.zero();
@@ -801,7 +802,7 @@ __device__ __forceinline__ void mx_target(const KParams &P, int t)
     int done = 0;
     for (int k = 0; k < tg.w; ++k) {
         const int2 pr = __ldg(P.mx_pairs + tg.z + k);
-        const int4 E = __ldg(reinterpret_cast<const int4 *>(ent + pr.y));
+        const float4 E = __ldg(ent + pr.y);
         Src<T> src;
         load_source_at<T>(mp + pr.x, src);
         acc_mx<T, ORDER>(-T(E.x) - src.d[0], -T(E.y) - src.d[1], -T(E.z) - src.d[2], src, L, S);
@@ -889,8 +890,8 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
             // entry: all refined take the moments without a branch, all
             // leaves the mass-only form (the same operations less the zero
             // moments' terms, so the same values), a mix the general form
-            // with zero moments for the leaves; an entry with only absent
-            // sources (mass 0) is skipped.
+            // with zero moments for the leaves, and an entry with only
+            // absent sources (mass 0) is skipped.
             for (int e0 = 0; e0 < P.n_far; e0 += kChunk) {
                 const int e1 = min(e0 + kChunk, P.n_far);
                 for (int e = e0; e < e1; ++e) {
@@ -915,11 +916,19 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
                                                     dA[2] - T(E.z), src, a3A, L, S);
                         }
                     } else {
-                        if (is_mp) {
-                            load_source_at<T>(mp + idx, src);
+                        if constexpr (kF32<T>) {
+                            if (is_mp) {
+                                load_source_at<T>(mp + idx, src);
+                            } else {
+                                src.m0 = wv;
+                                zero_moments<T>(src);
+                            }
                         } else {
-                            src.m0 = wv;
-                            zero_moments<T>(src);
+                            // leaf lanes read zero moments from the zero row
+                            // (no branch; the warp issues the loads anyway):
+                            // faster for the wider types, slower for float
+                            load_source_at<T>(mp + (is_mp ? idx : P.mp_limit), src);
+                            if (!is_mp) src.m0 = wv;
                         }
                         separation<T>(dA, src.d, E, R);
                         acc_mp<T, true, ORDER>(R[0], R[1], R[2], src, a3A, L, S);

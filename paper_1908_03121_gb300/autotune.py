@@ -8,7 +8,8 @@ SM, the dataflow downward pass or the level-by-level one, one or two multipole
 target cells per thread in flight, whole or half sub-grids per multipole work
 item) with CUDA events on the current stream, keeps the fastest and leaves it
 set on the tree.  Each candidate is run ``reps`` times after one warm-up; the
-median decides.  Results are cached per tree size and precision for the
+four fastest are then timed again, round-robin, with about 30 ms of steps
+each, and the median decides.  Results are cached per tree size and precision for the
 process.
 """
 
@@ -69,7 +70,29 @@ def tune(solver, reps=5, verbose=False, flush=None):
         if verbose:
             print(f"  {cand}: {np.median(times):.3f} ms")
     results.sort(key=lambda r: r[0])
-    best = results[0][1]
+    # The four fastest again, round-robin (so that clock or cache drift
+    # falls on all of them alike), with about 30 ms of steps each: on small
+    # trees the first round's few steps cannot tell near-equal shapes apart.
+    top = [c for _, c in results[:4]]
+    more = max(reps, min(60, int(30.0 / max(results[0][0], 1e-3))))
+    again = [[] for _ in top]
+    for _ in range(more):
+        for i, cand in enumerate(top):
+            B.fmm_set_tuning(solver.tree, **cand)
+            if flush is not None:
+                flush()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solver.step()
+            b.record(stream)
+            b.synchronize()
+            again[i].append(a.elapsed_time(b))
+    final = sorted(((float(np.median(t)), c) for t, c in zip(again, top)), key=lambda r: r[0])
+    if verbose:
+        for ms, c in final:
+            print(f"  again {c}: {ms:.3f} ms")
+    best = final[0][1]
     B.fmm_set_tuning(solver.tree, **best)
-    _CACHE[key] = (best, results)
+    _CACHE[key] = (best, final + results[len(top):])
     return _CACHE[key]

@@ -392,16 +392,34 @@ static void build_mx_pairs(fmm_tree_s *t, const std::vector<int32_t> &mx_nodes)
     }
     std::stable_sort(targets.begin(), targets.end(),
                      [](const Target &a, const Target &b) { return a.count > b.count; });
-    t->mx_targets.resize(targets.size() * 4);
-    for (size_t i = 0; i < targets.size(); ++i) {
-        t->mx_targets[4 * i + 0] = targets[i].node;
-        t->mx_targets[4 * i + 1] = targets[i].cell;
-        t->mx_targets[4 * i + 2] = targets[i].off;
-        t->mx_targets[4 * i + 3] = targets[i].count;
-    }
     // the same count as the planner's slot tables (two independent walks)
     if (int64_t(pairs.size() / 2) != P.kernel_interactions[2]) std::abort();
-    t->mx_pairs = std::move(pairs);
+    // Interleave each warp's lists: the 32 consecutive targets of warp w
+    // keep pair k of lane j at base_w + 32 k + j, so a warp's k-th loads are
+    // one contiguous 256-byte read.  Lists are sorted by length, so the
+    // padding (slots past a lane's own count, never read) is small.
+    std::vector<int32_t> inter;
+    t->mx_targets.resize(targets.size() * 4);
+    for (size_t w0 = 0; w0 < targets.size(); w0 += 32) {
+        const size_t w1 = std::min(targets.size(), w0 + 32);
+        const int32_t kmax = targets[w0].count;
+        const int64_t base = int64_t(inter.size() / 2);
+        inter.resize(inter.size() + size_t(kmax) * 32 * 2, -1);
+        for (size_t i = w0; i < w1; ++i) {
+            const int32_t lane = int32_t(i - w0);
+            for (int32_t k = 0; k < targets[i].count; ++k) {
+                const size_t slot = size_t(base + int64_t(k) * 32 + lane);
+                inter[2 * slot] = pairs[2 * size_t(targets[i].off + k)];
+                inter[2 * slot + 1] = pairs[2 * size_t(targets[i].off + k) + 1];
+            }
+            t->mx_targets[4 * i + 0] = targets[i].node;
+            t->mx_targets[4 * i + 1] = targets[i].cell;
+            t->mx_targets[4 * i + 2] = int32_t(base);
+            t->mx_targets[4 * i + 3] = targets[i].count;
+        }
+    }
+    if (inter.size() / 2 > size_t(INT32_MAX)) std::abort();
+    t->mx_pairs = std::move(inter);
     t->plan.n_mx_targets = int64_t(targets.size());
 }
 

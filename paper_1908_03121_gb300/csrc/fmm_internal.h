@@ -83,8 +83,9 @@ struct DeviceTables {
     int32_t *tree_leaf_rows = nullptr;  // [n_leaf]
     double *levels = nullptr;        // [max_level + 1][LEVEL_FIELDS]
     float *levels_df = nullptr;      // [max_level + 1][LEVEL_DF_FIELDS][2]
-    int4 *mx_targets = nullptr;      // monopole<-multipole targets (node, cell, offset, count)
-    int2 *mx_pairs = nullptr;        // their pairs (packed-moment offset, stencil entry)
+    int4 *mx_targets = nullptr;      // monopole<-multipole targets (node, cell, warp base, count)
+    int2 *mx_pairs = nullptr;        // their pairs (packed-moment offset, stencil entry),
+                                     // interleaved by warp (fmm_tree_s::mx_pairs)
     // workspace
     void *mass = nullptr;            // [n][512] float or double
     void *mp = nullptr;              // [n_refined][4][512][4] packed sources: float,
@@ -174,8 +175,9 @@ struct fmm_tree_s {
     std::vector<int32_t> tree_leaf_off, tree_leaf_rows;
     std::vector<double> levels;
     std::vector<float> levels_df;
-    std::vector<int32_t> mx_targets;     // [n_mx_targets][4]: node, cell, pair offset, count
-    std::vector<int32_t> mx_pairs;       // [pairs][2]: packed-moment offset, stencil entry
+    std::vector<int32_t> mx_targets;     // [n_mx_targets][4]: node, cell, the warp's pair base, count
+    std::vector<int32_t> mx_pairs;       // [slots][2]: packed-moment offset, stencil entry; pair k
+                                         // of target 32 w + j at base_w + 32 k + j
     std::vector<int32_t> dflow_items;    // the dataflow downward queue (DeviceTables)
     fmm::Plan plan;
     fmm_tuning tuning{};

@@ -79,10 +79,11 @@ struct KParams {
     const int32_t *mono_woff;  // [8][ent_stride] window offsets in parity 0's order, reflected
     int n_far, n_near;       // identical for every parity
     int ent_stride;          // entries reserved per parity
-    const int4 *mx_targets;  // monopole<-multipole targets (node, cell, pair offset, count)
+    const int4 *mx_targets;  // monopole<-multipole targets (node, cell, warp's pair base, count)
     int32_t n_mx;            // monopole<-multipole targets the multipole launch takes (0: none)
     int32_t *mx_counter;     // their queue head
-    const int2 *mx_pairs;    // (packed-moment offset, stencil entry)
+    const int2 *mx_pairs;    // (packed-moment offset, stencil entry); pair k of target
+                             // 32 w + j at its warp's base + 32 k + j
     int reach, py, pz, sub_stride;
     const void *mass;
     const void *mp;
@@ -800,8 +801,13 @@ __device__ __forceinline__ void mx_target(const KParams &P, int t)
     L.zero();
     S.zero();
     int done = 0;
+    // this lane's pairs, interleaved with its warp's: pair k at base + 32 k + lane;
+    // the next pair is fetched while the current one is evaluated
+    const int2 *pairs = P.mx_pairs + size_t(tg.z) + (t & 31);
+    int2 next = tg.w > 0 ? __ldg(pairs) : make_int2(0, 0);
     for (int k = 0; k < tg.w; ++k) {
-        const int2 pr = __ldg(P.mx_pairs + tg.z + k);
+        const int2 pr = next;
+        if (k + 1 < tg.w) next = __ldg(pairs + size_t(k + 1) * 32);
         const float4 E = __ldg(ent + pr.y);
         Src<T> src;
         load_source_at<T>(mp + pr.x, src);
@@ -1268,7 +1274,9 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
 // on the workloads), so instead of walking every stencil entry with most
 // lanes masked off, each lane takes one target cell and walks that cell's
 // own list of (packed-moment offset, stencil entry) pairs, built on the
-// host; targets are sorted by list length, so a warp's lanes finish together.
+// host; targets are sorted by list length, so a warp's lanes finish together,
+// and a warp's lists are interleaved, so each step of the walk reads the
+// warp's 32 pairs as one contiguous block.
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(kThreads) mx_kernel(KParams P)
 {

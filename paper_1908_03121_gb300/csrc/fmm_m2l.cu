@@ -1227,10 +1227,13 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
             A[b].zero();
             B[b].zero();
         }
+        // float: 32 entries per compensated chunk (the TwoSum folds are a
+        // fifth of this kernel's instructions at 16); double-float keeps 16
+        constexpr int chunk = kF32<T> ? 2 * kChunk : kChunk;
         int e = 0;
-        for (; e + kChunk <= n_ent; e += kChunk) {
+        for (; e + chunk <= n_ent; e += chunk) {
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j)
+            for (int j = 0; j < chunk; ++j)
                 mono_entry<T, NB, wstride, dz1>(W + base0, woff, s_coef, e + j, A, B);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {

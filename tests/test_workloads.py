@@ -90,6 +90,20 @@ def test_contact_binary_cfg5():
     assert abs(m2 / m1 - 0.3) < 0.01
 
 
+def test_cfg5_small_is_cfg5s_binary_at_level_6():
+    """cfg5_small, the profiling case: cfg5's binary (same stars, same
+    seed) refined to level 6, with more refined nodes than the multipole
+    kernel's 456 resident CTAs."""
+    c = make_config("cfg5_small")
+    big = make_config("cfg5")
+    d = c["desc"]
+    assert d[:, 0].max() == 6
+    assert len(d) == 5129 and count_leaves(d) == 4488
+    assert int((d[:, 5] >= 0).sum()) == 641
+    for k in ("c1", "c2", "r1", "r2", "rho_c1", "rho_c2"):
+        assert np.array_equal(np.asarray(c["info"][k]), np.asarray(big["info"][k]))
+
+
 def test_batch_of_sixteen_trees():
     """cfg4: sixteen independent trees, q from 0.1 to 1.0, maximum levels
     cycling 4-7, every tree between 100 and 2000 leaves."""

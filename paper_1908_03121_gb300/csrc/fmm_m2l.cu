@@ -486,6 +486,9 @@ constexpr int kMpPairs = 4 + 3;      // compensated float components of mp_kerne
 
 // store component k of a target cell: level units; (hi, lo) float pairs for
 // float (renormalised) and double-float (lo is zero there), else double
+// Same-level results are stored with the evict-first (streaming) hint: they
+// are read once, much later, by the downward pass, and left in L2 they would
+// push out the packed source moments that the multipole kernel rereads.
 template <typename T>
 __device__ __forceinline__ void store_L(const KParams &P, int node, int k, int cell, T hi, T lo)
 {
@@ -494,13 +497,13 @@ __device__ __forceinline__ void store_L(const KParams &P, int node, int k, int c
         // renormalise so that |lo| <= ulp(hi)/2
         float s = hi + lo;
         float e = lo - (s - hi);
-        static_cast<float *>(P.L)[idx] = s;
-        P.Lc[idx] = e;
+        __stcs(static_cast<float *>(P.L) + idx, s);
+        __stcs(P.Lc + idx, e);
     } else if constexpr (kDF<T>) {
-        static_cast<float *>(P.L)[idx] = hi.hi;
-        P.Lc[idx] = hi.lo;
+        __stcs(static_cast<float *>(P.L) + idx, hi.hi);
+        __stcs(P.Lc + idx, hi.lo);
     } else {
-        static_cast<double *>(P.L)[idx] = hi;
+        __stcs(static_cast<double *>(P.L) + idx, hi);
     }
 }
 
@@ -966,7 +969,7 @@ __global__ void __launch_bounds__(kThreads, kF32<T> ? 3 : 1) mp_kernel(KParams P
             store_target<T>(P, node, cell, L);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-                P.dL1[(size_t(node) * 3 + i) * NCELL + cell] = acc_value<T>(S, i);
+                __stcs(P.dL1 + (size_t(node) * 3 + i) * NCELL + cell, acc_value<T>(S, i));
         }
         __syncthreads();
     }
@@ -1261,8 +1264,8 @@ __global__ void __launch_bounds__(kThreads) mono_kernel(KParams P)
             }
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                P.dL1[(size_t(nodes[b]) * 3 + i) * NCELL + cell0] = 0.0;
-                P.dL1[(size_t(nodes[b]) * 3 + i) * NCELL + cell1] = 0.0;
+                __stcs(P.dL1 + (size_t(nodes[b]) * 3 + i) * NCELL + cell0, 0.0);
+                __stcs(P.dL1 + (size_t(nodes[b]) * 3 + i) * NCELL + cell1, 0.0);
             }
         }
         __syncthreads();

@@ -72,7 +72,7 @@ def tune(solver, reps=5, verbose=False, flush=None):
     results.sort(key=lambda r: r[0])
     # The four fastest again, round-robin (so that clock or cache drift
     # falls on all of them alike), with about 30 ms of steps each: on small
-    # trees the first round's few steps cannot tell near-equal shapes apart.
+    # trees the first pass's few steps cannot tell near-equal shapes apart.
     top = [c for _, c in results[:4]]
     more = max(reps, min(60, int(30.0 / max(results[0][0], 1e-3))))
     again = [[] for _ in top]

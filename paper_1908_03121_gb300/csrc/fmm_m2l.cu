@@ -109,6 +109,9 @@ __device__ __forceinline__ T elem_from_double(double v)
 // the double -> float conversions on the integer pipe (GB300's FP64 unit,
 // which also runs conversions, would otherwise bound this pass); the
 // moments' float rounding is the contraction's own precision.
+// (the FP64 moments are read once, with the evict-first hint, so that they
+// do not push the packed values just written out of L2, where the
+// multipole kernel reads them next)
 __device__ __forceinline__ void pack_float(const NodeInfo &ni, const double *__restrict__ levels,
                                            const double *__restrict__ Mn,
                                            const double *__restrict__ comc, int x, int y, int z,
@@ -116,7 +119,7 @@ __device__ __forceinline__ void pack_float(const NodeInfo &ni, const double *__r
                                            float *__restrict__ mp, double lo_x, double lo_y,
                                            double lo_z)
 {
-    mass_node[pi] = d2f_rn(Mn[0]);
+    mass_node[pi] = d2f_rn(__ldcs(Mn));
     if (ni.mp_row < 0) return;
     const double h = levels[ni.level * LEVEL_FIELDS + LV_H];
     const float ih = d2f_rn(levels[ni.level * LEVEL_FIELDS + LV_IH]);
@@ -124,13 +127,13 @@ __device__ __forceinline__ void pack_float(const NodeInfo &ni, const double *__r
                            lo_z + (8.0 * ni.iz + z + 0.5) * h};
     float d[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = d2f_rn(comc[a * NCELL] - ctr[a]) * ih;
+    for (int a = 0; a < 3; ++a) d[a] = d2f_rn(__ldcs(comc + a * NCELL) - ctr[a]) * ih;
     const float w2 = 0.5f * ih * ih, w3 = (1.0f / 6.0f) * ih * ih * ih;
     float A2[6], A3[10];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) A2[q] = d2f_rn(Mn[(4 + q) * NCELL]) * (float(mult2(q)) * w2);
+    for (int q = 0; q < 6; ++q) A2[q] = d2f_rn(__ldcs(Mn + (4 + q) * NCELL)) * (float(mult2(q)) * w2);
 #pragma unroll
-    for (int q = 0; q < 10; ++q) A3[q] = d2f_rn(Mn[(10 + q) * NCELL]) * (float(mult3(q)) * w3);
+    for (int q = 0; q < 10; ++q) A3[q] = d2f_rn(__ldcs(Mn + (10 + q) * NCELL)) * (float(mult3(q)) * w3);
     const float v[16] = {d[0],          d[1],          d[2],          mass_node[pi],
                          A2[0] - A2[5], A2[3] - A2[5], A2[1],         A2[2],
                          A2[4],         A3[0] - A3[5], A3[1] - A3[8], A3[2] - A3[9],

@@ -8,7 +8,7 @@ SM, the dataflow downward pass or the level-by-level one, one or two multipole
 target cells per thread in flight, whole or half sub-grids per multipole work
 item) with CUDA events on the current stream, keeps the fastest and leaves it
 set on the tree.  Each candidate is run ``reps`` times after one warm-up; the
-four fastest are then timed again, round-robin, with about 30 ms of steps
+four fastest are then timed again, round-robin, with about 100 ms of steps
 each, and the median decides.  Results are cached per tree size and precision for the
 process.
 """
@@ -71,10 +71,10 @@ def tune(solver, reps=5, verbose=False, flush=None):
             print(f"  {cand}: {np.median(times):.3f} ms")
     results.sort(key=lambda r: r[0])
     # The four fastest again, round-robin (so that clock or cache drift
-    # falls on all of them alike), with about 30 ms of steps each: on small
-    # trees the first pass's few steps cannot tell near-equal shapes apart.
+    # falls on all of them alike), with about 100 ms of steps each: the first
+    # pass's few steps cannot tell shapes within a percent apart.
     top = [c for _, c in results[:4]]
-    more = max(reps, min(60, int(30.0 / max(results[0][0], 1e-3))))
+    more = max(reps, min(200, int(100.0 / max(results[0][0], 1e-3))))
     again = [[] for _ in top]
     for _ in range(more):
         for i, cand in enumerate(top):

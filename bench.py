@@ -710,7 +710,8 @@ def run_ours(args):
                              parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                              tuning=best)}
     result["e2e"] = e2e
-    result["gpu_launches"] = int(stats["launches_fused"]) * args.steps
+    # (counted under the tuning the timed steps ran with)
+    result["gpu_launches"] = int(F.fmm_get_stats(solver.tree)["launches_fused"]) * args.steps
     result["clocks"] = clk
 
     if rank == 0:

@@ -151,7 +151,8 @@ typedef struct {
     int32_t launches_m2l;            /* kernel launches per fmm_m2l call */
     int32_t launches_step;           /* kernel launches per upward+m2l+downward+forces */
     int32_t timing;                  /* 1 if the tree was built with FMM_FLAG_TIMING */
-    int32_t launches_fused;          /* kernel launches per fmm_step */
+    int32_t launches_fused;          /* kernel launches per fmm_step under the tree's
+                                        tuning at the time of the call */
     int32_t reserved;
     /* FMM_FLAG_TIMING only: device time (ms) and launch count per kernel slot
      * (FMM_K_*), summed over the launches since the previous fmm_get_stats

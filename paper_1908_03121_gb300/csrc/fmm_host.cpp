@@ -842,14 +842,17 @@ int fmm_get_stats(fmm_tree_t t, fmm_stats *o)
     for (int lev = 1; lev <= t->max_level; ++lev) down += P.nodes_at[size_t(lev)].count > 0;
     o->launches_m2l = m2l;
     o->launches_step = up + m2l + down + 3;
-    // fmm_step: pack in two launches (leaves, refined), the refined levels'
-    // shifts per level, every leaf's shift and forces in one launch
+    // fmm_step: P2M also packs the leaf masses, one pack launch for the
+    // refined nodes; then either the refined levels' shifts per level and
+    // every leaf's shift and forces in one launch, or (dataflow tuning) all
+    // of it in one persistent launch; the two force-sum launches
     int refined_levels = 0;
     for (int lev = 1; lev <= t->max_level; ++lev) refined_levels += P.refined_at[size_t(lev)].count > 0;
     // (the monopole<-multipole targets ride in the multipole launch)
     const int mx_alone = (P.n_mx_targets > 0) && (P.work_mp.count == 0);
-    o->launches_fused = up + (m2l - 1) - (P.n_mx_targets > 0) + mx_alone + (P.leaves.count > 0) +
-                        (P.refined.count > 0) + refined_levels + (P.leaves.count > 0) + 2;
+    const int downward = t->tuning.dataflow ? 1 : refined_levels + (P.leaves.count > 0);
+    o->launches_fused = up + (m2l - 1) - (P.n_mx_targets > 0) + mx_alone + (P.refined.count > 0) +
+                        downward + 2;
     if ((t->cfg.flags & FMM_FLAG_TIMING) && !t->host_only) {
         o->timing = 1;
         timing_fold(t);
@@ -982,13 +985,13 @@ int fmm_step(fmm_tree_t t, const double *rho, double *M, double *com, void *L, f
     if ((e = (call)) != cudaSuccess) return cuda_fail(e, what)
     // main: reset the work queues, P2M, fork
     FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, s, &nl, M2L_RESET), "queue reset");
-    FMM_STEP_TRY(launch_p2m(t, rho, M, s), "p2m launch");
+    FMM_STEP_TRY(launch_p2m(t, rho, M, s, true), "p2m launch");
     FMM_STEP_TRY(cudaEventRecord(ev[0], s), "cudaEventRecord");
     // Events: 0 P2M done, 1 refined sources packed, 2 refined shifts done,
     // 3 second stream done, 4 roots done, 5 monopole kernel done.
     // aux: leaf masses, monopole<-monopole
+    // (P2M has stored the leaf masses in their packed form)
     FMM_STEP_TRY(cudaStreamWaitEvent(a, ev[0], 0), "cudaStreamWaitEvent");
-    FMM_STEP_TRY(launch_pack(t, M, com, a, PACK_LEAVES), "pack launch");
     FMM_STEP_TRY(launch_m2l(t, L, L_comp, dL1, a, &nl, M2L_MONO), "m2l launch");
     FMM_STEP_TRY(cudaEventRecord(ev[5], a), "cudaEventRecord");
     // main: M2M, refined sources, multipole targets

@@ -193,7 +193,10 @@ struct fmm_tree_s {
 namespace fmm {
 
 // kernels (each returns a cudaError_t from the launch)
-cudaError_t launch_p2m(const fmm_tree_s *t, const double *rho, double *M, cudaStream_t s);
+// pack_leaves: also store the leaf masses in the same-level pass's packed
+// form (what launch_pack does for the leaves)
+cudaError_t launch_p2m(const fmm_tree_s *t, const double *rho, double *M, cudaStream_t s,
+                       bool pack_leaves = false);
 cudaError_t launch_m2m_level(const fmm_tree_s *t, int level, double *M, double *com,
                              cudaStream_t s);
 // which nodes a pack launch covers

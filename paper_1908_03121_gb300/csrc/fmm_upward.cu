@@ -9,6 +9,8 @@
 // cell centre are exactly (+-h/2, +-h/2, +-h/2), so the raw moments about
 // that centre are signed sums of the eight masses (a 3-D Hadamard transform),
 // shifted to the centre of mass afterwards.
+#include <type_traits>
+
 #include "fmm_convert.cuh"
 #include "fmm_internal.h"
 #include "fmm_tensor.cuh"
@@ -17,18 +19,36 @@ namespace fmm {
 
 namespace {
 
+// the packed same-level mass of a leaf cell, as the pack kernel stores it
+template <typename T>
+__device__ __forceinline__ T packed_mass(double m)
+{
+    if constexpr (std::is_same<T, float>::value) {
+        return d2f_rn(m);
+    } else if constexpr (std::is_same<T, dfloat>::value) {
+        return df_from_double(m);
+    } else {
+        return m;
+    }
+}
+
 // P2M: leaf cells hold m = rho h^3 at their centre (point-mass reading of a
 // locally homogeneous density).  Two cells per thread, cells x-fastest, as
 // 16-byte loads and stores: the density may sit in pinned host memory, and
 // wider requests keep more of it in flight over the host link.  A density
 // that is not positive (zero, negative, NaN) sets FMM_STATUS_BAD_DENSITY in
-// the status word: the centres of mass divide by masses.
+// the status word: the centres of mass divide by masses.  With a packed-mass
+// array (T not void), the kernel also stores the masses in the same-level
+// pass's parity-split order and element type, which the pack kernel would
+// otherwise do for the leaves in a launch of its own.
+template <typename T>
 __global__ void __launch_bounds__(NCELL / 2) p2m_kernel(const NodeInfo *__restrict__ info,
                                                         const int32_t *__restrict__ leaves,
                                                         const double *__restrict__ levels,
                                                         const double *__restrict__ rho,
                                                         double *__restrict__ M,
-                                                        int32_t *__restrict__ status)
+                                                        int32_t *__restrict__ status,
+                                                        T *__restrict__ mass)
 {
     const int node = leaves[blockIdx.x];
     const NodeInfo ni = info[node];
@@ -36,8 +56,15 @@ __global__ void __launch_bounds__(NCELL / 2) p2m_kernel(const NodeInfo *__restri
     const int c = 2 * threadIdx.x;
     const double2 r = *reinterpret_cast<const double2 *>(rho + size_t(ni.leaf_row) * NCELL + c);
     if (!(r.x > 0.0) || !(r.y > 0.0)) atomicOr(status, FMM_STATUS_BAD_DENSITY);
-    *reinterpret_cast<double2 *>(M + (size_t(node) * NCOMP) * NCELL + c) =
-        make_double2(r.x * h3, r.y * h3);
+    const double m0 = r.x * h3, m1 = r.y * h3;
+    *reinterpret_cast<double2 *>(M + (size_t(node) * NCOMP) * NCELL + c) = make_double2(m0, m1);
+    if constexpr (!std::is_void<T>::value) {
+        // cells c and c + 1 differ in x parity only
+        const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+        const int pi = parity_index(x, y, z);
+        mass[size_t(node) * NCELL + pi] = packed_mass<T>(m0);
+        mass[size_t(node) * NCELL + pi + 64] = packed_mass<T>(m1);
+    }
 }
 
 // Central moments about X = ref + d from raw moments S2, S3 about ref:
@@ -427,15 +454,28 @@ __global__ void __launch_bounds__(8 * kCellsPerCta) m2m_df_lanes_kernel(const No
 
 }  // namespace
 
-cudaError_t launch_p2m(const fmm_tree_s *t, const double *rho, double *M, cudaStream_t s)
+cudaError_t launch_p2m(const fmm_tree_s *t, const double *rho, double *M, cudaStream_t s,
+                       bool pack_leaves)
 {
     const ListRange &r = t->plan.leaves;
     if (r.count == 0) return cudaSuccess;
     // 16-byte accesses: rho and M must be 16-byte aligned (checked by the
     // public calls)
-    p2m_kernel<<<unsigned(r.count), NCELL / 2, 0, s>>>(t->dev.info, t->dev.lists + r.off,
-                                                       t->dev.levels, rho, M,
-                                                       t->dev.counters + kStatusSlot);
+    const unsigned grid = unsigned(r.count);
+    const int32_t *leaves = t->dev.lists + r.off;
+    int32_t *status = t->dev.counters + kStatusSlot;
+    if (!pack_leaves)
+        p2m_kernel<void><<<grid, NCELL / 2, 0, s>>>(t->dev.info, leaves, t->dev.levels, rho, M,
+                                                   status, nullptr);
+    else if (t->cfg.precision == FMM_MIXED)
+        p2m_kernel<float><<<grid, NCELL / 2, 0, s>>>(t->dev.info, leaves, t->dev.levels, rho, M,
+                                                    status, static_cast<float *>(t->dev.mass));
+    else if (t->cfg.precision == FMM_DFLOAT)
+        p2m_kernel<dfloat><<<grid, NCELL / 2, 0, s>>>(t->dev.info, leaves, t->dev.levels, rho, M,
+                                                     status, static_cast<dfloat *>(t->dev.mass));
+    else
+        p2m_kernel<double><<<grid, NCELL / 2, 0, s>>>(t->dev.info, leaves, t->dev.levels, rho, M,
+                                                     status, static_cast<double *>(t->dev.mass));
     return cudaGetLastError();
 }
 

@@ -633,3 +633,25 @@ def test_order2_same_level_fp64():
     h = widths(c["desc"])[:, None, None]
     assert rel_err(host(s.dL1) * h ** -2, ref["dL1"]) <= FP64_TOL
     s.close()
+
+
+@pytest.mark.parametrize("dataflow", [0, 1])
+@pytest.mark.parametrize("name", ["adaptive4", "batch3", "single"])
+def test_step_launch_count_matches_stats(name, dataflow):
+    """The library kernels one fmm_step launches, as the CUDA profiler
+    counts them, equal fmm_get_stats' launches_fused under the same tuning
+    (the figure the benchmark reports as gpu_launches)."""
+    prof = pytest.importorskip("torch.profiler")
+    c = small_case(name)
+    s = solve_gpu(c, "mixed")
+    F.fmm_set_tuning(s.tree, dataflow=dataflow)
+    s.step()
+    torch.cuda.synchronize()
+    with prof.profile(activities=[prof.ProfilerActivity.CUDA]) as p:
+        s.step()
+        torch.cuda.synchronize()
+    names = [e.name for e in p.events() if "fmm::" in e.name]
+    if not names:
+        pytest.skip("the profiler recorded no device kernels here")
+    assert len(names) == F.fmm_get_stats(s.tree)["launches_fused"], sorted(set(names))
+    s.close()

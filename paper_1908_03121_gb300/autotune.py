@@ -6,10 +6,11 @@ caller's tree for every candidate of
 ``fmm_tuning`` (sub-grids per pass of the monopole kernel, persistent CTAs per
 SM, the dataflow downward pass or the level-by-level one, one or two multipole
 target cells per thread in flight, whole or half sub-grids per multipole work
-item) with CUDA events on the current stream, keeps the fastest and leaves it
-set on the tree.  Each candidate is run ``reps`` times after one warm-up; the
-four fastest are then timed again, round-robin, with about 100 ms of steps
-each, and the median decides.  Results are cached per tree size and precision for the
+item), each captured as a CUDA graph and replayed, with CUDA events on the
+current stream; keeps the fastest and leaves it set on the tree.  Each
+candidate is replayed ``reps`` times after one warm-up; the four fastest are
+then timed again, round-robin, with about 100 ms of steps each, and the
+median decides.  Results are cached per tree size and precision for the
 process.
 """
 
@@ -33,10 +34,13 @@ def _key(solver):
             int(solver.tree.stats["stencil_union"]), getattr(solver, "order", 3))
 
 
-def tune(solver, reps=5, verbose=False, flush=None):
+def tune(solver, reps=5, verbose=False, flush=None, graph=True):
     """Pick and set the fastest tuning for ``solver`` (an ``fmm.Solver``).
     ``flush``, if given, is called before every timed step (the benchmark's
-    L2 flush, so that candidates are compared as the benchmark times them)."""
+    L2 flush, so that candidates are compared as the benchmark times them).
+    ``graph``: time replays of the step captured as a CUDA graph under each
+    candidate (as the benchmark and ``Solver.replay`` run it), else eager
+    steps.  Leaves ``solver.graph`` unset: capture again after tuning."""
     import torch
     key = _key(solver)
     if key in _CACHE:
@@ -51,21 +55,34 @@ def tune(solver, reps=5, verbose=False, flush=None):
                                                                DATAFLOW, PAIR_TARGETS, items)
                   if (mixed or (nb != 4 and pt == 0)) and not (pt and it == 2)]
     stream = torch.cuda.current_stream()
+
+    def runner(cand):
+        # the step as the caller will run it: one CUDA graph captured under
+        # this tuning (launch shapes are fixed at capture), replayed; eager
+        # steps would add launch costs that a replay does not pay, which
+        # favours the shapes with fewer launches
+        B.fmm_set_tuning(solver.tree, **cand)
+        g = solver.capture() if graph else None
+        run = g.replay if g is not None else solver.step
+        run()
+        return g, run
+
+    def timed(run):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
     results = []
     for cand in candidates:
-        B.fmm_set_tuning(solver.tree, **cand)
-        solver.step()
-        times = []
-        for _ in range(reps):
-            if flush is not None:
-                flush()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            solver.step()
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b))
+        g, run = runner(cand)
+        times = [timed(run) for _ in range(reps)]
+        del g
         results.append((float(np.median(times)), cand))
         if verbose:
             print(f"  {cand}: {np.median(times):.3f} ms")
@@ -74,25 +91,19 @@ def tune(solver, reps=5, verbose=False, flush=None):
     # falls on all of them alike), with about 100 ms of steps each: the first
     # pass's few steps cannot tell shapes within a percent apart.
     top = [c for _, c in results[:4]]
+    runs = [runner(c) for c in top]
     more = max(reps, min(200, int(100.0 / max(results[0][0], 1e-3))))
     again = [[] for _ in top]
     for _ in range(more):
-        for i, cand in enumerate(top):
-            B.fmm_set_tuning(solver.tree, **cand)
-            if flush is not None:
-                flush()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            solver.step()
-            b.record(stream)
-            b.synchronize()
-            again[i].append(a.elapsed_time(b))
+        for i, (_, run) in enumerate(runs):
+            again[i].append(timed(run))
+    del runs
     final = sorted(((float(np.median(t)), c) for t, c in zip(again, top)), key=lambda r: r[0])
     if verbose:
         for ms, c in final:
             print(f"  again {c}: {ms:.3f} ms")
     best = final[0][1]
     B.fmm_set_tuning(solver.tree, **best)
+    solver.graph = None
     _CACHE[key] = (best, final + results[len(top):])
     return _CACHE[key]

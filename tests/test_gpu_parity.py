@@ -647,10 +647,14 @@ def test_step_launch_count_matches_stats(name, dataflow):
     F.fmm_set_tuning(s.tree, dataflow=dataflow)
     s.step()
     torch.cuda.synchronize()
-    with prof.profile(activities=[prof.ProfilerActivity.CUDA]) as p:
-        s.step()
-        torch.cuda.synchronize()
-    names = [e.name for e in p.events() if "fmm::" in e.name]
+    names = []
+    for _ in range(2):      # the first session can start its device tracing late
+        with prof.profile(activities=[prof.ProfilerActivity.CUDA]) as p:
+            s.step()
+            torch.cuda.synchronize()
+        names = [e.name for e in p.events() if "fmm::" in e.name]
+        if names:
+            break
     if not names:
         pytest.skip("the profiler recorded no device kernels here")
     assert len(names) == F.fmm_get_stats(s.tree)["launches_fused"], sorted(set(names))

@@ -5,10 +5,12 @@
 // final expansion re-centred at its own centre of mass,
 //   L^(n) += sum_{k=0}^{3-n} (1/k!) L_parent^(n+k) . d^k,  d = X - X_parent,
 // and inherits the parent's accumulated angular-momentum correction.  The
-// accumulation is FP64 in both precisions; in the mixed precision the shift
-// increments (the k >= 1 terms, small next to the parent's own coefficient)
-// are formed in float, which keeps GB300's slow FP64 pipe to a few adds per
-// component.
+// FP64 precision accumulates in FP64 and the double-float one with one FP64
+// operation per component; in the mixed precision the shift increments (the
+// k >= 1 terms, small next to the parent's own coefficient) are formed in
+// float and the final expansion in double-float from the parent's
+// double-float copy, so GB300's slow FP64 pipe does one add per component
+// (forming L64).  The correction is carried in FP64 in every precision.
 // forces_kernel: phi = L0, g = -(L1 + dL1), f = m g, and fixed-order FP64
 // block sums of f and x cross f (plus the |f|, |x cross f| normalisers) per
 // leaf node; reduce_chunk_kernel and reduce_final_kernel fold those per tree.
@@ -126,18 +128,20 @@ template <int NMAX>
 __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int c,
                                                const NodeInfo *__restrict__ info,
                                                const double *__restrict__ lv,
+                                               const dfloat *__restrict__ lvdf,
                                                const float *__restrict__ Lhi,
                                                const float *__restrict__ Llo, const double *dL1,
                                                const double *__restrict__ com,
                                                double *__restrict__ L64, double *dacc,
-                                               float *__restrict__ down, double lo_x,
+                                               dfloat *__restrict__ down, double lo_x,
                                                double lo_y, double lo_z, double (&out)[20],
                                                double (&corr)[3])
 {
     constexpr int NK = NMAX == 1 ? 4 : 20;
     const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
     const double *L = lv + ni.level * LEVEL_FIELDS;
-    const double sc[4] = {L[LV_S0], L[LV_S1], L[LV_S2], L[LV_S3]};
+    const dfloat *Ld = lvdf + ni.level * LEVEL_DF_FIELDS;
+    const double sc1 = L[LV_S1];
     float hi[20], lo[20];
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
@@ -152,18 +156,27 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
         offc[1] = d2f_trunc(com[(size_t(node) * 3 + 1) * NCELL + c] - (lo_y + (8.0 * ni.iy + y + 0.5) * h));
         offc[2] = d2f_trunc(com[(size_t(node) * 3 + 2) * NCELL + c] - (lo_z + (8.0 * ni.iz + z + 0.5) * h));
     }
+    // the cell's final expansion in double-float: own (level units) x scale
+    // + the parent's final expansion, which the parent level left in `down`
+    // as (hi, lo) pairs; one FP64 add per component then forms L64
+    dfloat res[20];
     if (ni.parent >= 0) {
         const int pc = (4 * (ni.ix & 1) + (x >> 1)) + 8 * (4 * (ni.iy & 1) + (y >> 1)) +
                        64 * (4 * (ni.iz & 1) + (z >> 1));
         const int prow = info[ni.parent].mp_row;
-        const float *pd = down + size_t(prow) * 23 * NCELL + pc;
+        const dfloat *pd = down + size_t(prow) * 23 * NCELL + pc;
         float Pf[20];
+        dfloat Pb[20];
 #pragma unroll
-        for (int k = 0; k < 20; ++k) Pf[k] = pd[k * NCELL];
+        for (int k = 0; k < 20; ++k) {
+            const dfloat v = pd[k * NCELL];
+            Pf[k] = v.hi;
+            if (k < NK) Pb[k] = v;
+        }
         const float hc = d2f_trunc(L[LV_H]);
-        const float d[3] = {(float(x & 1) - 0.5f) * hc + offc[0] - pd[20 * NCELL],
-                            (float(y & 1) - 0.5f) * hc + offc[1] - pd[21 * NCELL],
-                            (float(z & 1) - 0.5f) * hc + offc[2] - pd[22 * NCELL]};
+        const float d[3] = {(float(x & 1) - 0.5f) * hc + offc[0] - pd[20 * NCELL].hi,
+                            (float(y & 1) - 0.5f) * hc + offc[1] - pd[21 * NCELL].hi,
+                            (float(z & 1) - 0.5f) * hc + offc[2] - pd[22 * NCELL].hi};
         float inc[20];
         shift_increments<float, NMAX>(Pf, d, inc);
         const float rs[4] = {d2f_trunc(L[LV_R0]), d2f_trunc(L[LV_R1]), d2f_trunc(L[LV_R2]),
@@ -177,29 +190,32 @@ __device__ __forceinline__ void l2l_cell_mixed(const NodeInfo &ni, int node, int
         }
 #pragma unroll
         for (int k = 0; k < NK; ++k)
-            out[k] = fma(pair_to_double(hi[k], lo[k]), sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3],
-                         L64[(size_t(ni.parent) * NCOMP + k) * NCELL + pc]);
+            res[k] = fmadd(dfloat(hi[k], lo[k]), Ld[5 + (k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3)],
+                           Pb[k]);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            corr[a] = fma(dL1[(size_t(node) * 3 + a) * NCELL + c], sc[1],
+            corr[a] = fma(dL1[(size_t(node) * 3 + a) * NCELL + c], sc1,
                           dacc[(size_t(ni.parent) * 3 + a) * NCELL + pc]);
     } else {
 #pragma unroll
         for (int k = 0; k < NK; ++k)
-            out[k] = pair_to_double(hi[k], lo[k]) * sc[k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3];
+            res[k] = dfloat(hi[k], lo[k]) * Ld[5 + (k == 0 ? 0 : k < 4 ? 1 : k < 10 ? 2 : 3)];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc[1];
+        for (int a = 0; a < 3; ++a) corr[a] = dL1[(size_t(node) * 3 + a) * NCELL + c] * sc1;
     }
 #pragma unroll
-    for (int k = 0; k < NK; ++k) L64[(size_t(node) * NCOMP + k) * NCELL + c] = out[k];
+    for (int k = 0; k < NK; ++k) {
+        out[k] = df_to_double(res[k]);
+        L64[(size_t(node) * NCOMP + k) * NCELL + c] = out[k];
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) dacc[(size_t(node) * 3 + a) * NCELL + c] = corr[a];
     if (NMAX == 3) {
-        float *od = down + size_t(ni.mp_row) * 23 * NCELL + c;
+        dfloat *od = down + size_t(ni.mp_row) * 23 * NCELL + c;
 #pragma unroll
-        for (int k = 0; k < 20; ++k) od[k * NCELL] = d2f_trunc(out[k]);
+        for (int k = 0; k < 20; ++k) od[k * NCELL] = res[k];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) od[(20 + a) * NCELL] = offc[a];
+        for (int a = 0; a < 3; ++a) od[(20 + a) * NCELL] = dfloat(offc[a]);
     }
 }
 
@@ -299,8 +315,9 @@ __device__ __forceinline__ void l2l_cell(const NodeInfo *__restrict__ info, cons
                                          double (&corr)[3])
 {
     if constexpr (MODE == FMM_MIXED)
-        l2l_cell_mixed<NMAX>(ni, node, c, info, levels, static_cast<const float *>(Lv), Lc, dL1,
-                             com, L64, dacc, down, lo_x, lo_y, lo_z, out, corr);
+        l2l_cell_mixed<NMAX>(ni, node, c, info, levels, levels_df, static_cast<const float *>(Lv),
+                             Lc, dL1, com, L64, dacc, reinterpret_cast<dfloat *>(down), lo_x, lo_y,
+                             lo_z, out, corr);
     else if constexpr (MODE == FMM_DFLOAT)
         l2l_cell_df<NMAX>(ni, node, c, info, levels, levels_df, static_cast<const float *>(Lv), Lc,
                           dL1, com, L64, dacc, reinterpret_cast<dfloat *>(down), lo_x, lo_y, lo_z,

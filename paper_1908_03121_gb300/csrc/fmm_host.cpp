@@ -646,9 +646,8 @@ static int upload_tree(fmm_tree_s *t)
         d.workspace_bytes += up_b;
     }
     if (t->cfg.precision != FMM_FP64) {
-        // float copies (mixed) or (hi, lo) pairs (double-float)
-        size_t down_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 23 * NCELL * sizeof(float) *
-                        (t->cfg.precision == FMM_DFLOAT ? 2 : 1);
+        // (hi, lo) float pairs
+        size_t down_b = size_t(std::max<int64_t>(t->n_refined, 1)) * 23 * NCELL * 2 * sizeof(float);
         if ((e = cudaMalloc(reinterpret_cast<void **>(&d.down), down_b)) != cudaSuccess)
             return fail(FMM_ERR_NOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
         d.workspace_bytes += down_b;
@@ -767,11 +766,12 @@ int fmm_build_tree(const fmm_node_desc *nodes, int64_t n_nodes, const fmm_config
         L[LV_S3] = L[LV_S2] / h;
         for (int k = 0; k < 4; ++k) L[LV_R0 + k] = 1.0 / L[LV_S0 + k];
     }
-    // the same h and inverse scales as (hi, lo) float pairs
+    // the same h, inverse scales and scales as (hi, lo) float pairs
     t->levels_df.assign(size_t(t->max_level + 1) * LEVEL_DF_FIELDS * 2, 0.f);
     for (int lev = 1; lev <= t->max_level; ++lev) {
         const double *L = &t->levels[size_t(lev) * LEVEL_FIELDS];
-        const double v[LEVEL_DF_FIELDS] = {L[LV_H], L[LV_R0], L[LV_R1], L[LV_R2], L[LV_R3]};
+        const double v[LEVEL_DF_FIELDS] = {L[LV_H],  L[LV_R0], L[LV_R1], L[LV_R2], L[LV_R3],
+                                           L[LV_S0], L[LV_S1], L[LV_S2], L[LV_S3]};
         for (int k = 0; k < LEVEL_DF_FIELDS; ++k) {
             float *o = &t->levels_df[(size_t(lev) * LEVEL_DF_FIELDS + k) * 2];
             o[0] = float(v[k]);

@@ -48,9 +48,9 @@ __host__ __device__ constexpr int pad_to(int min_value, int want)
 // physical scales G h^-(n+1) of orders n = 0..3 and their inverses
 constexpr int LEVEL_FIELDS = 12;
 enum { LV_H = 0, LV_IH, LV_H3, LV_S0, LV_S1, LV_S2, LV_S3, LV_R0, LV_R1, LV_R2, LV_R3 };
-// the same h and inverse scales R0..R3 as double-float (hi, lo) pairs,
-// [level][LEVEL_DF_FIELDS][2] floats
-constexpr int LEVEL_DF_FIELDS = 5;
+// the same h, inverse scales R0..R3 and scales S0..S3 as double-float
+// (hi, lo) pairs, [level][LEVEL_DF_FIELDS][2] floats
+constexpr int LEVEL_DF_FIELDS = 9;
 
 // per-node table row (device and host)
 struct NodeInfo {
@@ -99,10 +99,10 @@ struct DeviceTables {
                                      // node * 8 + slice, root level first, then leaf nodes
                                      // by level
     int32_t *dflow_ready = nullptr;  // [n]: slices of the node's shift completed this step
-    float *down = nullptr;           // mixed: [n_refined][23][512] float copy, double-
-                                     // float: the same as (hi, lo) pairs, of each refined
-                                     // cell's final expansion (20) and centre-of-mass
-                                     // offset from its centre (3)
+    float *down = nullptr;           // mixed and double-float: [n_refined][23][512]
+                                     // (hi, lo) pairs of each refined cell's final
+                                     // expansion (20) and centre-of-mass offset from
+                                     // its centre (3)
     size_t workspace_bytes = 0;
 };
 
